@@ -1,0 +1,408 @@
+#!/usr/bin/env python
+"""Benchmark: image pairs matched per second by Cascade Hashing on GB300.
+
+One step = the whole matching path over one synthetic image set already
+resident in HBM: centre, projection + signs (+ exact double re-evaluation),
+lookup tables, and matching of every pair (lookup, Hamming ranking, exact
+distances, ratio test, compaction of the match lists).  Default workload:
+100 images of 4,000..12,000 SIFT-like uint8 descriptors (mean 8k) with all
+4,950 pairs matched exhaustively.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank matches its own independent image set (weak
+scaling, no data-path collective); rank 0 prints one JSON line.
+--impl reference times the CPU oracle on a bounded sample of the same
+workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "image pairs matched/sec (8k x 8k SIFT) on 1 GB300 at bit-exact matches; % HBM roofline"
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}
+N_SM = 152
+POPC_PER_CLK_SM = 16          # 32-bit population counts per clock per SM (measured 15.96)
+L2_FLUSH_BYTES = 256 << 20
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        d["source"] = "measured"
+        return d
+    except Exception:
+        d = dict(FALLBACK_PEAKS)
+        d["source"] = "fallback"
+        return d
+
+
+def workload(name: str, rank: int):
+    import synth
+    if name == "config1":
+        s = synth.config1(seed=1 + 1000 * rank)
+        desc = "config1: 100 images x U{4000..12000} SIFT-like uint8 descriptors (30%% noisy copies of " \
+               "index-neighbours), all 4950 pairs, seed %d" % (1 + 1000 * rank)
+    elif name == "config0":
+        s = synth.config0(seed=1000 * rank)
+        desc = "config0: one pair, 2000 x 2000 descriptors, seed %d" % (1000 * rank)
+    elif name == "config3":
+        s = synth.config3(seed=3 + 1000 * rank)
+        desc = "config3: 2000 images log-uniform 1000..20000, 30 neighbours each, %d pairs" % len(s.pairs)
+    else:
+        raise SystemExit("unknown workload " + name)
+    return s, desc
+
+
+def lookup_entries(buckets: np.ndarray, img_off: np.ndarray, pairs: np.ndarray, T: int, m: int) -> int:
+    """Sum over pairs and tables of |A_v| * |B_v| over buckets v: the lookup-table
+    entries Step 1 visits (each needs one 128-bit Hamming distance)."""
+    nb = 1 << m
+    n_img = len(img_off) - 1
+    hist = np.zeros((n_img, T, nb), np.int64)
+    for i in range(n_img):
+        b = buckets[img_off[i]:img_off[i + 1]]
+        for t in range(T):
+            hist[i, t] = np.bincount(b[:, t], minlength=nb)
+    A = hist[pairs[:, 0].astype(np.int64)]
+    B = hist[pairs[:, 1].astype(np.int64)]
+    return int((A * B).sum())
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline leg and reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_codes_parallel(orc, desc, R, po, mu, threads):
+    n = desc.shape[0]
+    codes = np.zeros((n, 4), np.uint32)
+    buckets = np.zeros((n, po.n_tables), np.uint8)
+    step = max(1, (n + threads - 1) // threads)
+
+    def work(s):
+        c, b = orc.hash_codes(desc[s:s + step], mu, R, po)
+        codes[s:s + step] = c
+        buckets[s:s + step] = b
+
+    ts = [threading.Thread(target=work, args=(s,)) for s in range(0, n, step)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    return codes, buckets
+
+
+def oracle_sample(s, n_pairs: int, seed: int = 0):
+    """Times the oracle on a bounded sample: the centre over the whole set,
+    codes for the features of the images the sampled pairs touch, and the
+    matching of n_pairs random pairs, all host cores.  Extrapolates to the
+    whole job (codes of every feature + every pair, pair cost scaled by
+    N_A * N_B).  Returns (pairs/s, cores, sample text, seconds)."""
+    import oracle as orc
+    cores = os.cpu_count() or 1
+    po = orc.params()
+    rng = np.random.default_rng(seed)
+    P = len(s.pairs)
+    pick = np.sort(rng.choice(P, size=min(n_pairs, P), replace=False))
+    sp = s.pairs[pick]
+    imgs = np.unique(sp)
+    sizes = s.sizes()
+    t0 = time.perf_counter()
+    mu = orc.mean(s.desc)
+    t_mean = time.perf_counter() - t0
+    # sub-set of touched images, renumbered
+    sub_off = np.zeros(len(imgs) + 1, np.uint64)
+    sub_off[1:] = np.cumsum(sizes[imgs])
+    sub_desc = np.concatenate([s.image(int(i)) for i in imgs])
+    t0 = time.perf_counter()
+    codes, buckets = oracle_codes_parallel(orc, sub_desc, s.R, po, mu, cores)
+    t_hash = time.perf_counter() - t0
+    remap = {int(i): k for k, i in enumerate(imgs)}
+    sp2 = np.array([[remap[int(a)], remap[int(b)]] for a, b in sp], np.uint32)
+    t0 = time.perf_counter()
+    orc.match_pairs(sub_desc, sub_off, codes, buckets, sp2, po, n_threads=cores)
+    t_match = time.perf_counter() - t0
+    work_full = float((sizes[s.pairs[:, 0]] * sizes[s.pairs[:, 1]]).sum())
+    work_smp = float((sizes[sp[:, 0]] * sizes[sp[:, 1]]).sum())
+    job = t_mean + t_hash * (sizes.sum() / max(1, sub_desc.shape[0])) + t_match * (work_full / max(1.0, work_smp))
+    text = ("oracle (C, %d threads): centre over %d features, codes of %d features (%d images), %d of %d pairs "
+            "matched; extrapolated to codes of all %d features + all pairs by feature count and N_A*N_B"
+            % (cores, s.desc.shape[0], sub_desc.shape[0], len(imgs), len(sp), P, s.desc.shape[0]))
+    return P / job, cores, text, t_mean + t_hash + t_match
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    s, wdesc = workload(args.workload, 0)
+    sp = max(8, args.ref_pairs)
+    times = []
+    for i in range(args.warmup + args.steps):
+        v, cores, text, secs = oracle_sample(s, sp, seed=i)
+        if i >= args.warmup:
+            times.append(len(s.pairs) / v)
+    job = statistics.mean(times)
+    value = len(s.pairs) / job
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": job * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8/f64", "data": "synthetic",
+            "config": {"workload": wdesc},
+            "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle", "sample": text},
+            "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    import paper_1805_08995_gb300 as ch
+    from paper_1805_08995_gb300 import build as chbuild
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.gpus != world:
+        raise SystemExit("--gpus %d but WORLD_SIZE %d" % (args.gpus, world))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        chbuild.build()
+    if dist:
+        dist.barrier()
+    ch._load()
+
+    s, wdesc = workload(args.workload, rank)
+    prec = ch.CASHASH_BF16 if args.precision == "bf16" else ch.CASHASH_FP32
+    sched = ch.CASHASH_SCHED_PERSISTENT if args.schedule == "persistent" else ch.CASHASH_SCHED_PER_PAIR
+    p = ch.cashash_default_params(precision=prec, schedule=sched)
+    ctx = ch.cashash_create(p, s.R)
+    ds = ch.DeviceSet(p, s.img_off, s.desc)
+    plan = ch.cashash_plan_create(ctx, ds, s.pairs)
+    P = len(s.pairs)
+    cap = int(s.sizes()[s.pairs[:, 0]].sum())
+    dev = torch.device("cuda", local)
+    moff = torch.zeros(P + 1, dtype=torch.int64, device=dev)
+    mt = torch.zeros((cap, 2), dtype=torch.int32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        ch.cashash_build_codes(ctx, ds, stream=stream)
+        ch.cashash_match_plan(ctx, plan, moff, mt, cap, stream=stream)
+
+    ch.cashash_set_profiling(ctx, True)
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    if ch.cashash_sync_status(ctx) != ch.CASHASH_OK:
+        raise SystemExit("device status not OK after warm-up")
+    launches0 = ch.cashash_get_stats(ctx)["n_launches"]
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.perf_counter()
+    step_ms, stage_ms = [], {k: [] for k in ch.STAGES}
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    for _ in range(args.steps):
+        flush.zero_()
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        st = ch.cashash_get_stats(ctx)
+        for k, v in st["ms_stage"].items():
+            if v >= 0:
+                stage_ms[k].append(v)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t_wall = time.perf_counter() - t_wall0
+    clocks = sampler.stop()
+    stats = ch.cashash_get_stats(ctx)
+    launches = stats["n_launches"] - launches0
+    if ch.cashash_sync_status(ctx) != ch.CASHASH_OK:
+        raise SystemExit("device status not OK after timed steps")
+
+    t_steps = sum(step_ms) / 1e3
+    t_max = t_steps
+    if dist:
+        tt = torch.tensor([t_steps], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = P * world * args.steps / t_max
+
+    # dominant kernel: the matching kernel; its work counted by the method's
+    # lookup entries (Step 1), one 128-bit Hamming distance = 4 popcounts each
+    pk = peaks()
+    T, m = p.n_tables, p.bits_per_table
+    buckets = ds.buckets_np(T)
+    entries = lookup_entries(buckets, s.img_off, s.pairs, T, m)
+    t_match = statistics.mean(stage_ms["match"]) / 1e3
+    popc_rate = 4.0 * entries / t_match
+    popc_peak = POPC_PER_CLK_SM * N_SM * pk.get("sm_max_mhz", 2070.0) * 1e6
+    # touched-bytes view (per query: candidate codes + indices, k rows, query, offsets)
+    touched = 20.0 * entries + float(s.sizes()[s.pairs[:, 0]].sum()) * (10 * 128 + 128 + 16 + 8 + 48)
+    roofline = {"bound": "alu", "achieved": popc_rate / 1e12, "peak": popc_peak / 1e12, "unit": "Tpopc/s",
+                "frac": popc_rate / popc_peak, "traffic": None, "kernel": "k_match",
+                "units_per_launch": entries, "unit_def": "lookup-table entries (one 128-bit Hamming each)",
+                "kernel_ms": t_match * 1e3,
+                "peak_def": "16 popc/clk/SM x 152 SMs x %.0f MHz (sm_max_mhz, %s)" % (
+                    pk.get("sm_max_mhz", 2070.0), pk["source"]),
+                "hbm_view": {"touched_gbs": touched / t_match / 1e9,
+                             "frac_of_hbm": touched / t_match / 1e9 / pk["hbm_gbs"],
+                             "note": "bytes the method touches per query, mostly served from shared memory / L2"}}
+
+    # end-to-end through the C-ABI with host buffers (pinned descriptors)
+    e2e = None
+    if not args.no_e2e:
+        pinned = torch.from_numpy(s.desc).pin_memory()
+        mo_h = np.zeros(P + 1, np.uint64)
+        mt_h = np.zeros((cap, 2), np.uint32)
+        ctx2 = ch.cashash_create(p, s.R)
+        for _ in range(max(1, args.warmup)):
+            ch.cashash_run_host(ctx2, pinned, s.img_off, s.pairs, cap, match_off=mo_h, matches=mt_h)
+        ts = []
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st, off, mth = ch.cashash_run_host(ctx2, pinned, s.img_off, s.pairs, cap, match_off=mo_h,
+                                               matches=mt_h)
+            ts.append(time.perf_counter() - t0)
+            assert st == ch.CASHASH_OK
+        n_m = int(mo_h[P])
+        e2e = {"value": P / statistics.mean(ts), "unit": "pairs/s",
+               "h2d_bytes_per_step": int(s.desc.nbytes + 8 * (len(s.img_off))),
+               "d2h_bytes_per_step": int(8 * (P + 1) + 8 * n_m)}
+        ctx2.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, cores, text, secs = oracle_sample(s, args.ref_pairs)
+        cpu = {"value": v, "unit": "pairs/s", "cores": cores, "kind": "oracle", "sample": text,
+               "seconds": secs}
+
+    if rank == 0:
+        stages = {k: (statistics.mean(v) if v else None) for k, v in stage_ms.items()}
+        line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "u8/" + ("bf16" if prec == ch.CASHASH_BF16 else "fp32") + "+f64fix",
+                "data": "synthetic",
+                "config": {"workload": wdesc, "images": int(s.n_images), "features": int(s.desc.shape[0]),
+                           "pairs": P, "precision": args.precision, "schedule": args.schedule,
+                           "l2": "flushed: 256 MiB write between timed steps (outside the events)",
+                           "params": "n=128, 6 tables x 8 bits, k=10, ratio 0.8",
+                           "matches_per_step": int(stats["n_matches"]),
+                           "reevaluated_projections": int(stats["n_reevaluated"])},
+                "features_per_s": s.desc.shape[0] * world * args.steps / t_max,
+                "stages_ms": stages, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(launches), "clocks": clocks, "wall_s_timed_region": t_wall}
+        print(json.dumps(line))
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="config1", choices=["config0", "config1", "config3"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--schedule", default="persistent", choices=["persistent", "per_pair"])
+    ap.add_argument("--ref-pairs", type=int, default=480)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

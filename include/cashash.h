@@ -1,0 +1,225 @@
+/*
+ * cashash.h -- C-ABI of the GB300 (sm_103a) Cascade Hashing image matcher.
+ *
+ * The library implements Cascade Hashing (CasHash) SIFT matching between
+ * image pairs as described in Xu, Sun and Tao, "GPU Accelerated Cascade
+ * Hashing Image Matching for Large Scale 3D Reconstruction":
+ *   Sec. 3.1 Step 1  lookup in several tables of m-bit short codes
+ *   Sec. 3.1 Step 2  remapping to an n-bit code, Hamming distance
+ *   Sec. 3.1 Step 3  ranking: the k candidates of smallest Hamming distance
+ *   Sec. 3.1 Step 4  squared Euclidean distance on those k, Lowe's ratio test
+ *   Sec. 4.1         hash bit = sign of the inner product with a random vector
+ *   Sec. 5           optional Hamming threshold tau before ranking
+ *   Sec. 6.2 Eq. 1-2 optional epipolar band before ranking
+ *
+ * Results are defined exactly (bit-exact, not approximately):
+ *   - descriptors are centred by the mean over every descriptor of the set
+ *     passed to cashash_build_codes (or by a caller-given mean);
+ *   - bit b of a feature is [v_b > 0] where v_b is the projection
+ *     sum_j R[b][j] * (x_j - mu_j) evaluated in IEEE double, j ascending,
+ *     each difference, product and sum rounded to nearest (no fused
+ *     multiply-add); the GPU computes a cheaper bounded approximation and
+ *     re-evaluates exactly that double sequence whenever the approximation
+ *     is within its rounding bound of zero;
+ *   - the candidate set of a query is the set of points of the other image
+ *     that share its bucket in at least one table (each point once);
+ *   - ranking orders candidates by (Hamming distance, candidate index);
+ *   - squared distances are exact integers; the nearest candidate (smaller
+ *     index on equal distance) matches when den^2 * d1 < num^2 * d2 and at
+ *     least two candidates were ranked.
+ *
+ * Conventions for every entry point:
+ *   - "DEVICE" pointers are CUDA device memory of the current device,
+ *     owned by the caller and left untouched by the library beyond what the
+ *     call documents; "HOST" pointers are ordinary host memory.
+ *   - Calls that take a cudaStream_t are asynchronous with respect to the
+ *     host and ordered on that stream (0 = legacy default stream).  Device
+ *     side errors (capacity exceeded, bad index) are recorded in a status
+ *     word of the context and returned by cashash_sync_status().
+ *   - Every entry point returns a cashash_status; nothing aborts, traps or
+ *     throws across the boundary.
+ *   - A context is not thread-safe: use one per host thread.
+ */
+#ifndef CASHASH_H
+#define CASHASH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* cashash_stream_t; /* ABI-identical to cudaStream_t */
+typedef struct cashash_ctx cashash_ctx;          /* opaque context */
+
+typedef enum {
+  CASHASH_OK = 0,
+  CASHASH_EINVAL = 1,     /* bad argument (null pointer, size out of range, bad parameter) */
+  CASHASH_ENOMEM = 2,     /* device or pinned host allocation failed */
+  CASHASH_ECUDA = 3,      /* a CUDA runtime call failed */
+  CASHASH_EOVERFLOW = 4,  /* match capacity too small; match_off[P] holds the total needed */
+  CASHASH_EDEVICE = 5,    /* a kernel recorded an internal error (index out of range) */
+  CASHASH_ETIMEOUT = 6,   /* a bounded device or staging wait ran out */
+  CASHASH_ENOTSUP = 7     /* parameter combination not supported by this build */
+} cashash_status;
+
+enum { CASHASH_FP32 = 0, CASHASH_BF16 = 1 };                          /* projection precision form */
+enum { CASHASH_SCHED_PER_PAIR = 0, CASHASH_SCHED_PERSISTENT = 1 };   /* matching schedule */
+
+#define CASHASH_DIM 128          /* SIFT descriptor length d (Sec. 4.1) */
+#define CASHASH_MAX_TABLES 8
+#define CASHASH_MAX_K 32
+#define CASHASH_MAX_IMAGE 16777215u   /* features per image (24-bit candidate index) */
+
+/* Method parameters.  The paper fixes none of m, n, the number of tables, k
+ * or the ratio; defaults used by the benchmarks are given in brackets. */
+typedef struct {
+  uint32_t code_bits;       /* n of Step 2: 32, 64, 96 or 128 [128] */
+  uint32_t n_tables;        /* lookup tables of Step 1: 1..8 [6] */
+  uint32_t bits_per_table;  /* m of Step 1: 0..8 [8] (0 = one bucket) */
+  uint32_t top_k;           /* k of Step 3: 1..32 [10] */
+  uint32_t ratio_num;       /* Lowe ratio num/den [4/5] */
+  uint32_t ratio_den;
+  uint32_t tau;             /* Sec. 5 threshold: candidates with Hamming > tau are dropped;
+                               tau >= code_bits turns it off [code_bits] */
+  uint32_t precision;       /* CASHASH_FP32 (CUDA-core projection) or CASHASH_BF16 (tensor cores) */
+  uint32_t schedule;        /* CASHASH_SCHED_PER_PAIR (one launch per pair) or
+                               CASHASH_SCHED_PERSISTENT (one launch over the whole pair list) */
+  uint32_t reserved;
+  double epi_px;            /* Sec. 6.2 threshold d in pixels; < 0 turns the band off [-1] */
+} cashash_params;
+
+/* Fills p with the defaults listed above. */
+void cashash_default_params(cashash_params* p);
+
+/* An image set: images stored back to back.  Feature f of image i is row
+ * img_off[i] + f.  All DEVICE arrays are caller-allocated. */
+typedef struct {
+  uint32_t n_images;
+  uint32_t reserved;
+  uint64_t n_features;       /* = img_off[n_images] */
+  const uint64_t* img_off;   /* HOST [n_images + 1], non-decreasing, img_off[0] = 0;
+                                every image has at most CASHASH_MAX_IMAGE features */
+  const uint8_t* desc;       /* DEVICE [n_features][128] uint8 descriptors, 16-byte aligned */
+  uint32_t* codes;           /* DEVICE [n_features][4] out: n-bit remapping code, bit b in
+                                word b/32 at bit b%32, unused bits 0 (Step 2) */
+  uint8_t* buckets;          /* DEVICE [n_features][8] out: byte t = short code of table t
+                                (Step 1), bit i from projection row code_bits + t*m + i;
+                                bytes >= n_tables are 0 */
+  uint32_t* sqnorm;          /* DEVICE [n_features] out: sum_j x_j^2 (used by Step 4) */
+  uint8_t* tables;           /* DEVICE out: lookup tables of Step 1, cashash_tables_bytes()
+                                bytes, 16-byte aligned; layout private to the library */
+  const float* kpts;         /* DEVICE [n_features][2] key-point (x, y) in pixels, or NULL;
+                                needed only when epi_px >= 0 */
+} cashash_set;
+
+/* Bytes of the lookup-table buffer for a set (HOST img_off).  0 on bad input. */
+uint64_t cashash_tables_bytes(const cashash_params* p, const uint64_t* img_off, uint32_t n_images);
+
+/* Creates a context on the current CUDA device.  R_host is the matrix of
+ * random vectors r_k of Sec. 4.1: [code_bits + n_tables * bits_per_table]
+ * rows of 128 doubles, row-major; rows 0..code_bits-1 give the remapping
+ * code, row code_bits + t*m + i gives bit i of table t.  The context copies
+ * R and owns its device workspace.  Errors: EINVAL, ENOTSUP, ENOMEM, ECUDA. */
+int cashash_create(cashash_ctx** out, const cashash_params* p, const double* R_host);
+
+/* Releases the context and its workspace (after synchronising its work). */
+void cashash_destroy(cashash_ctx* ctx);
+
+/* Sec. 4.1 + Steps 1-2: hash codes and lookup tables for every feature of
+ * the set.  mean_host: HOST [128] caller-given centre, or NULL to use the
+ * mean over every descriptor of the set (computed exactly from integer
+ * column sums, one correctly rounded division).  Writes set->codes,
+ * set->buckets, set->sqnorm and set->tables.  Asynchronous on `stream`.
+ * Errors: EINVAL (null pointer, bad offsets), ENOMEM, ECUDA. */
+int cashash_build_codes(cashash_ctx* ctx, const cashash_set* set, const double* mean_host,
+                        cashash_stream_t stream);
+
+/* The centre used by the last cashash_build_codes (HOST [128] out).
+ * Synchronises the context's stream.  Errors: EINVAL, ECUDA. */
+int cashash_get_mean(cashash_ctx* ctx, double* mean_out);
+
+/* A pair list prepared for matching (work items, per-pair offsets). */
+typedef struct cashash_plan cashash_plan;
+
+/* Prepares pairs_host (HOST [P][2] uint32: query image, candidate image)
+ * for matching against `set`.  The plan keeps copies; it is valid while the
+ * set's device buffers are.  Errors: EINVAL (image index out of range),
+ * ENOMEM, ECUDA. */
+int cashash_plan_create(cashash_ctx* ctx, const cashash_set* set, const uint32_t* pairs_host, uint32_t P,
+                        cashash_plan** out);
+void cashash_plan_destroy(cashash_plan* plan);
+
+/* Steps 1-4 (+ Sec. 5 tau, + Sec. 6.2 epipolar band when epi_px >= 0) for
+ * every pair of the plan.  Outputs (DEVICE, caller-allocated):
+ *   match_off [P + 1] uint64: matches of pair i are entries
+ *                             match_off[i] .. match_off[i+1]-1;
+ *   matches   [cap][2] uint32: (query feature index in the query image,
+ *                             candidate feature index in the other image),
+ *                             ascending query index within each pair.
+ * F_dev: DEVICE [P][9] row-major fundamental matrices (x_cand^T F x_query = 0)
+ * when epi_px >= 0, else ignored (may be NULL).  When the total exceeds cap,
+ * match_off is still complete, nothing beyond cap is written and
+ * cashash_sync_status() returns EOVERFLOW.  Asynchronous on `stream`.
+ * Errors: EINVAL, ECUDA. */
+int cashash_match_plan(cashash_ctx* ctx, cashash_plan* plan, const double* F_dev, uint64_t* match_off,
+                       uint32_t* matches, uint64_t cap, cashash_stream_t stream);
+
+/* Convenience: plan + match + plan release in one call (same outputs). */
+int cashash_match_pairs(cashash_ctx* ctx, const cashash_set* set, const uint32_t* pairs_host, uint32_t P,
+                        const double* F_dev, uint64_t* match_off, uint32_t* matches, uint64_t cap,
+                        cashash_stream_t stream);
+
+/* Synchronises `stream` and returns (then clears) the first device-side
+ * error recorded since the last call: OK, EOVERFLOW or EDEVICE. */
+int cashash_sync_status(cashash_ctx* ctx, cashash_stream_t stream);
+
+/* End-to-end from HOST buffers: stages descriptors host -> device through
+ * pinned buffers on a side stream (chunks of at most stage_bytes, 0 = 4 GiB),
+ * builds codes and tables, matches every pair, and copies match_off and the
+ * matches back.  desc_host: HOST [img_off[n_images]][128]; kpts_host /
+ * F_host may be NULL unless epi_px >= 0.  match_off_host: HOST [P + 1];
+ * matches_host: HOST [cap][2].  Synchronous.  Errors: EINVAL, ENOMEM, ECUDA,
+ * EOVERFLOW (match_off_host complete, matches truncated to cap), EDEVICE. */
+int cashash_run_host(cashash_ctx* ctx, const uint8_t* desc_host, const uint64_t* img_off, uint32_t n_images,
+                     const float* kpts_host, const uint32_t* pairs_host, uint32_t P, const double* F_host,
+                     uint64_t* match_off_host, uint32_t* matches_host, uint64_t cap, uint64_t stage_bytes);
+
+/* Stage ids of cashash_stats.ms_stage. */
+enum {
+  CASHASH_STAGE_CENTRE = 0,     /* column sums, centre and per-row constants */
+  CASHASH_STAGE_PROJECT = 1,    /* projection, signs, rounding-bound test */
+  CASHASH_STAGE_REEVAL = 2,     /* exact double re-evaluation of flagged projections */
+  CASHASH_STAGE_TABLES = 3,     /* lookup tables of Step 1 */
+  CASHASH_STAGE_MATCH = 4,      /* matching kernel(s): Steps 1-4 */
+  CASHASH_STAGE_COMPACT = 5,    /* per-pair offsets and compaction of the match lists */
+  CASHASH_N_STAGES = 8
+};
+
+/* Counters of the last build/match calls (host copies after the call's stream sync). */
+typedef struct {
+  uint64_t n_features;        /* features hashed by the last build */
+  uint64_t n_reevaluated;     /* projections re-evaluated in double (|approx| under the bound) */
+  uint64_t n_pairs;           /* pairs in the last match */
+  uint64_t n_matches;         /* matches found by the last match */
+  uint64_t n_work_items;      /* (pair, query tile) items of the last match */
+  uint64_t n_launches;        /* kernels launched by this context since it was created */
+  double ms_stage[CASHASH_N_STAGES];  /* with profiling on: device milliseconds of each stage of
+                                         the last build/match (CUDA events recorded on the
+                                         launching stream); -1 when not measured */
+} cashash_stats;
+
+/* Turns per-stage CUDA-event timing on (1) or off (0).  Off by default. */
+int cashash_set_profiling(cashash_ctx* ctx, int on);
+
+/* Synchronises the context's last stream and fills *out.  Errors: EINVAL, ECUDA. */
+int cashash_get_stats(cashash_ctx* ctx, cashash_stats* out);
+
+/* Static text for a status code. */
+const char* cashash_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

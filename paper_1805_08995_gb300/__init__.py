@@ -1,0 +1,302 @@
+"""Python binding of the GB300 Cascade Hashing library (libcashash.so).
+
+Argument marshalling only: every step of the matching path runs in the CUDA
+kernels of ``csrc/`` behind the C-ABI declared in ``include/cashash.h``.  The
+functions carry the C names.  PyTorch supplies device memory and streams.
+
+There is no CPU fallback: importing this package without a built library,
+or calling it without a CUDA device, raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcashash.so")
+DIM = 128
+
+CASHASH_OK, CASHASH_EINVAL, CASHASH_ENOMEM, CASHASH_ECUDA = 0, 1, 2, 3
+CASHASH_EOVERFLOW, CASHASH_EDEVICE, CASHASH_ETIMEOUT, CASHASH_ENOTSUP = 4, 5, 6, 7
+CASHASH_FP32, CASHASH_BF16 = 0, 1
+CASHASH_SCHED_PER_PAIR, CASHASH_SCHED_PERSISTENT = 0, 1
+
+
+class CashashError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__("%s: %s (status %d)" % (what, cashash_strerror(status), status))
+
+
+class cashash_params(C.Structure):
+    _fields_ = [("code_bits", C.c_uint32), ("n_tables", C.c_uint32), ("bits_per_table", C.c_uint32),
+                ("top_k", C.c_uint32), ("ratio_num", C.c_uint32), ("ratio_den", C.c_uint32),
+                ("tau", C.c_uint32), ("precision", C.c_uint32), ("schedule", C.c_uint32),
+                ("reserved", C.c_uint32), ("epi_px", C.c_double)]
+
+
+class cashash_set(C.Structure):
+    _fields_ = [("n_images", C.c_uint32), ("reserved", C.c_uint32), ("n_features", C.c_uint64),
+                ("img_off", C.c_void_p), ("desc", C.c_void_p), ("codes", C.c_void_p), ("buckets", C.c_void_p),
+                ("sqnorm", C.c_void_p), ("tables", C.c_void_p), ("kpts", C.c_void_p)]
+
+
+N_STAGES = 8
+STAGES = ("centre", "project", "reeval", "tables", "match", "compact")
+
+
+class cashash_stats(C.Structure):
+    _fields_ = [("n_features", C.c_uint64), ("n_reevaluated", C.c_uint64), ("n_pairs", C.c_uint64),
+                ("n_matches", C.c_uint64), ("n_work_items", C.c_uint64), ("n_launches", C.c_uint64),
+                ("ms_stage", C.c_double * N_STAGES)]
+
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libcashash.so is not built (run __graft_entry__.build() or "
+                              "python paper_1805_08995_gb300/build.py)")
+        lib = C.CDLL(LIB_PATH)
+        vp, u32, u64 = C.c_void_p, C.c_uint32, C.c_uint64
+        P = C.POINTER
+        sig = {
+            "cashash_strerror": ([C.c_int], C.c_char_p),
+            "cashash_default_params": ([P(cashash_params)], None),
+            "cashash_tables_bytes": ([P(cashash_params), vp, u32], u64),
+            "cashash_create": ([P(vp), P(cashash_params), vp], C.c_int),
+            "cashash_destroy": ([vp], None),
+            "cashash_build_codes": ([vp, P(cashash_set), vp, vp], C.c_int),
+            "cashash_get_mean": ([vp, vp], C.c_int),
+            "cashash_plan_create": ([vp, P(cashash_set), vp, u32, P(vp)], C.c_int),
+            "cashash_plan_destroy": ([vp], None),
+            "cashash_match_plan": ([vp, vp, vp, vp, vp, u64, vp], C.c_int),
+            "cashash_match_pairs": ([vp, P(cashash_set), vp, u32, vp, vp, vp, u64, vp], C.c_int),
+            "cashash_sync_status": ([vp, vp], C.c_int),
+            "cashash_run_host": ([vp, vp, vp, u32, vp, vp, u32, vp, vp, vp, u64, u64], C.c_int),
+            "cashash_get_stats": ([vp, P(cashash_stats)], C.c_int),
+            "cashash_set_profiling": ([vp, C.c_int], C.c_int),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = lib
+    return _lib
+
+
+def exported_symbols():
+    """Names of the C-ABI entry points this binding expects."""
+    return ["cashash_strerror", "cashash_default_params", "cashash_tables_bytes", "cashash_create",
+            "cashash_destroy", "cashash_build_codes", "cashash_get_mean", "cashash_plan_create",
+            "cashash_plan_destroy", "cashash_match_plan", "cashash_match_pairs", "cashash_sync_status",
+            "cashash_run_host", "cashash_get_stats", "cashash_set_profiling"]
+
+
+def _check(st, what):
+    if st != CASHASH_OK:
+        raise CashashError(st, what)
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _dptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _hptr(a):
+    return None if a is None else C.c_void_p(a.ctypes.data)
+
+
+# ---------------------------------------------------------------------------
+# C-ABI wrappers (same names)
+# ---------------------------------------------------------------------------
+
+def cashash_strerror(status: int) -> str:
+    return _load().cashash_strerror(int(status)).decode()
+
+
+def cashash_default_params(**over) -> cashash_params:
+    p = cashash_params()
+    _load().cashash_default_params(C.byref(p))
+    for k, v in over.items():
+        setattr(p, k, v)
+    return p
+
+
+def cashash_tables_bytes(params: cashash_params, img_off: np.ndarray) -> int:
+    img_off = np.ascontiguousarray(img_off, np.uint64)
+    return int(_load().cashash_tables_bytes(C.byref(params), _hptr(img_off), len(img_off) - 1))
+
+
+class Context:
+    """Owns a cashash_ctx (projection matrix, centre, workspace)."""
+
+    def __init__(self, params: cashash_params, R: np.ndarray):
+        self.params = params
+        R = np.ascontiguousarray(R, np.float64)
+        rows = params.code_bits + params.n_tables * params.bits_per_table
+        if R.ndim != 2 or R.shape[1] != DIM or R.shape[0] < rows:
+            raise ValueError("R must have at least %d rows of 128" % rows)
+        R = np.ascontiguousarray(R[:rows])
+        h = C.c_void_p()
+        _check(_load().cashash_create(C.byref(h), C.byref(params), _hptr(R)), "cashash_create")
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _load().cashash_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cashash_create(params: cashash_params, R: np.ndarray) -> Context:
+    return Context(params, R)
+
+
+def cashash_destroy(ctx: Context):
+    ctx.close()
+
+
+class DeviceSet:
+    """A cashash_set whose device arrays are torch tensors on the current device."""
+
+    def __init__(self, params: cashash_params, img_off: np.ndarray, desc, kpts=None):
+        import torch
+        self.img_off = np.ascontiguousarray(img_off, np.uint64)
+        n = int(self.img_off[-1]) if len(self.img_off) else 0
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if not isinstance(desc, torch.Tensor):
+            desc = torch.from_numpy(np.ascontiguousarray(desc, np.uint8).reshape(-1, DIM)).to(dev)
+        assert desc.dtype == torch.uint8 and desc.is_cuda and desc.is_contiguous() and desc.shape == (n, DIM)
+        self.desc = desc
+        self.codes = torch.empty((max(n, 1), 4), dtype=torch.int32, device=dev)
+        self.buckets = torch.empty((max(n, 1), 8), dtype=torch.uint8, device=dev)
+        self.sqnorm = torch.empty((max(n, 1),), dtype=torch.int32, device=dev)
+        tb = cashash_tables_bytes(params, self.img_off)
+        self.tables = torch.empty((max(tb, 16),), dtype=torch.uint8, device=dev)
+        if kpts is not None and not isinstance(kpts, torch.Tensor):
+            kpts = torch.from_numpy(np.ascontiguousarray(kpts, np.float32).reshape(-1, 2)).to(dev)
+        self.kpts = kpts
+        self.n = n
+        self.c = cashash_set(len(self.img_off) - 1, 0, n, self.img_off.ctypes.data, desc.data_ptr(),
+                             self.codes.data_ptr(), self.buckets.data_ptr(), self.sqnorm.data_ptr(),
+                             self.tables.data_ptr(), kpts.data_ptr() if kpts is not None else None)
+
+    def codes_np(self):
+        return self.codes[:self.n].cpu().numpy().view(np.uint32)
+
+    def buckets_np(self, n_tables):
+        return self.buckets[:self.n, :n_tables].cpu().numpy()
+
+
+def cashash_build_codes(ctx: Context, dset: DeviceSet, mean=None, stream=None):
+    m = None if mean is None else np.ascontiguousarray(mean, np.float64)
+    _check(_load().cashash_build_codes(ctx.handle, C.byref(dset.c), _hptr(m), _stream(stream)),
+           "cashash_build_codes")
+
+
+def cashash_get_mean(ctx: Context) -> np.ndarray:
+    out = np.zeros(DIM, np.float64)
+    _check(_load().cashash_get_mean(ctx.handle, _hptr(out)), "cashash_get_mean")
+    return out
+
+
+class Plan:
+    def __init__(self, ctx: Context, dset: DeviceSet, pairs: np.ndarray):
+        self.ctx = ctx
+        self.pairs = np.ascontiguousarray(pairs, np.uint32).reshape(-1, 2)
+        self.P = self.pairs.shape[0]
+        h = C.c_void_p()
+        _check(_load().cashash_plan_create(ctx.handle, C.byref(dset.c), _hptr(self.pairs), self.P, C.byref(h)),
+               "cashash_plan_create")
+        self.handle = h
+        self.dset = dset
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _load().cashash_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cashash_plan_create(ctx: Context, dset: DeviceSet, pairs) -> Plan:
+    return Plan(ctx, dset, pairs)
+
+
+def cashash_plan_destroy(plan: Plan):
+    plan.close()
+
+
+def cashash_match_plan(ctx: Context, plan: Plan, match_off, matches, cap: int, F=None, stream=None):
+    _check(_load().cashash_match_plan(ctx.handle, plan.handle, _dptr(F), _dptr(match_off), _dptr(matches), int(cap),
+                                      _stream(stream)), "cashash_match_plan")
+
+
+def cashash_match_pairs(ctx: Context, dset: DeviceSet, pairs, match_off, matches, cap: int, F=None, stream=None):
+    pairs = np.ascontiguousarray(pairs, np.uint32).reshape(-1, 2)
+    _check(_load().cashash_match_pairs(ctx.handle, C.byref(dset.c), _hptr(pairs), pairs.shape[0], _dptr(F),
+                                       _dptr(match_off), _dptr(matches), int(cap), _stream(stream)),
+           "cashash_match_pairs")
+
+
+def cashash_sync_status(ctx: Context, stream=None) -> int:
+    return int(_load().cashash_sync_status(ctx.handle, _stream(stream)))
+
+
+def cashash_get_stats(ctx: Context) -> dict:
+    s = cashash_stats()
+    _check(_load().cashash_get_stats(ctx.handle, C.byref(s)), "cashash_get_stats")
+    out = {k: int(getattr(s, k)) for k, _ in cashash_stats._fields_ if k != "ms_stage"}
+    out["ms_stage"] = {name: float(s.ms_stage[i]) for i, name in enumerate(STAGES)}
+    return out
+
+
+def cashash_set_profiling(ctx: Context, on: bool = True):
+    _check(_load().cashash_set_profiling(ctx.handle, 1 if on else 0), "cashash_set_profiling")
+
+
+def cashash_run_host(ctx: Context, desc: np.ndarray, img_off: np.ndarray, pairs: np.ndarray, cap: int,
+                     kpts=None, F=None, stage_bytes: int = 0, match_off=None, matches=None):
+    """End-to-end from host arrays.  desc may be a pinned torch CPU tensor or a
+    numpy array.  Returns (status, match_off[P+1], matches[M][2])."""
+    img_off = np.ascontiguousarray(img_off, np.uint64)
+    pairs = np.ascontiguousarray(pairs, np.uint32).reshape(-1, 2)
+    P = pairs.shape[0]
+    if hasattr(desc, "data_ptr"):
+        dptr = C.c_void_p(desc.data_ptr())
+    else:
+        desc = np.ascontiguousarray(desc, np.uint8)
+        dptr = _hptr(desc)
+    kp = None if kpts is None else np.ascontiguousarray(kpts, np.float32)
+    Fh = None if F is None else np.ascontiguousarray(F, np.float64)
+    if match_off is None:
+        match_off = np.zeros(P + 1, np.uint64)
+    if matches is None:
+        matches = np.zeros((max(int(cap), 1), 2), np.uint32)
+    st = _load().cashash_run_host(ctx.handle, dptr, _hptr(img_off), len(img_off) - 1, _hptr(kp), _hptr(pairs), P,
+                                  _hptr(Fh), _hptr(match_off), _hptr(matches), int(cap), int(stage_bytes))
+    if st not in (CASHASH_OK, CASHASH_EOVERFLOW):
+        raise CashashError(st, "cashash_run_host")
+    total = int(match_off[P])
+    return st, match_off, matches[:min(total, int(cap))]

@@ -1,0 +1,728 @@
+// Host runtime behind the C-ABI of include/cashash.h: argument checks, the
+// context (projection matrix, centre, workspace), pair plans, the launch
+// sequences of cashash_build_codes / cashash_match_plan, and the end-to-end
+// host path with pinned staging on a side stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.h"
+
+using namespace chx;
+
+namespace {
+
+struct HostWS {  // device buffers of the end-to-end host path, grown on demand
+  uint8_t* desc = nullptr;       uint64_t cap_desc = 0;
+  uint32_t* codes = nullptr;     uint64_t cap_codes = 0;
+  uint8_t* buckets = nullptr;    uint64_t cap_buckets = 0;
+  uint32_t* sqnorm = nullptr;    uint64_t cap_sq = 0;
+  uint8_t* tables = nullptr;     uint64_t cap_tables = 0;
+  float* kpts = nullptr;         uint64_t cap_kpts = 0;
+  double* F = nullptr;           uint64_t cap_F = 0;
+  uint64_t* moff = nullptr;      uint64_t cap_moff = 0;
+  uint32_t* matches = nullptr;   uint64_t cap_matches = 0;
+  uint8_t* pin[2] = {nullptr, nullptr};
+  uint64_t pin_cap = 0;
+  cudaStream_t copy = nullptr, comp = nullptr;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  cudaEvent_t staged = nullptr;
+  std::vector<uint32_t> plan_pairs;  // pair list of the cached plan
+  std::vector<uint64_t> plan_off;    // image offsets of the cached plan
+  cashash_plan* plan = nullptr;
+};
+
+}  // namespace
+
+struct cashash_ctx {
+  cashash_params p{};
+  KParams kp{};
+  int device = 0;
+  int nsm = 0;
+  uint32_t rows = 0;
+  double* d_R = nullptr;        // [rows][128]
+  double* d_nrmR = nullptr;     // [rows]
+  float* d_R32T = nullptr;      // [128][192] FP32 R, transposed, zero padded
+  void* d_Rbf = nullptr;        // BF16 form operands (hi/lo split)
+  double* d_mu = nullptr;       // [128]
+  RowConst* d_rc = nullptr;     // [192]
+  unsigned long long* d_colsum = nullptr;  // [128]
+  unsigned long long* d_cnt = nullptr;     // [0] flagged features [1] re-evaluated rows [2] matches
+  uint32_t* d_status = nullptr;
+  uint32_t* d_flagmask = nullptr;   // [n][6] rows flagged for re-evaluation
+  uint32_t* d_flaglist = nullptr;   // [n] features with flagged rows
+  uint64_t cap_flagmask = 0, cap_flaglist = 0;
+  uint64_t* d_chunk_feat0 = nullptr;
+  uint32_t* d_chunk_len = nullptr;
+  uint64_t cap_cf0 = 0, cap_clen = 0;
+  cudaStream_t last_stream = nullptr;
+  uint64_t last_n_features = 0;
+  uint64_t last_pairs = 0;
+  uint64_t last_items = 0;
+  uint64_t n_launches = 0;
+  int profiling = 0;
+  cudaEvent_t ev[CASHASH_N_STAGES][2] = {};
+  int ev_used[CASHASH_N_STAGES] = {};
+  HostWS hw;
+};
+
+struct cashash_plan {
+  cashash_ctx* ctx = nullptr;
+  uint32_t P = 0;
+  int persistent = 0;
+  PairInfo* d_pairs = nullptr;
+  uint2* d_items = nullptr;
+  uint32_t n_items = 0;
+  uint32_t* d_res = nullptr;
+  uint64_t n_res = 0;
+  unsigned long long* d_pair_cnt = nullptr;
+  unsigned int* d_item_ctr = nullptr;
+  std::vector<uint32_t> first, count;  // per-pair item ranges (per-pair schedule)
+  const uint8_t* desc = nullptr;
+  const uint32_t* codes = nullptr;
+  const uint8_t* buckets = nullptr;
+  const uint32_t* sqnorm = nullptr;
+  const uint8_t* tables = nullptr;
+  const float* kpts = nullptr;
+};
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+namespace {
+
+int cuda_err(cudaError_t e) {
+  if (e == cudaSuccess) return CASHASH_OK;
+  if (e == cudaErrorMemoryAllocation) return CASHASH_ENOMEM;
+  return CASHASH_ECUDA;
+}
+
+#define CK(x)                              \
+  do {                                     \
+    const int _st = cuda_err((x));         \
+    if (_st != CASHASH_OK) return _st;     \
+  } while (0)
+
+int params_ok(const cashash_params* p) {
+  if (!p) return 0;
+  if (p->code_bits != 32 && p->code_bits != 64 && p->code_bits != 96 && p->code_bits != 128) return 0;
+  if (p->n_tables < 1 || p->n_tables > CASHASH_MAX_TABLES) return 0;
+  if (p->bits_per_table > 8) return 0;
+  if (p->top_k < 1 || p->top_k > CASHASH_MAX_K) return 0;
+  if (p->ratio_den < 1 || p->ratio_den > 65535 || p->ratio_num > 65535) return 0;
+  if (p->precision > CASHASH_BF16 || p->schedule > CASHASH_SCHED_PERSISTENT) return 0;
+  if (std::isnan(p->epi_px) || std::isinf(p->epi_px)) return 0;
+  return 1;
+}
+
+template <class T>
+int grow(T*& ptr, uint64_t& cap, uint64_t need) {
+  if (need <= cap && ptr) return CASHASH_OK;
+  if (ptr) {
+    cudaDeviceSynchronize();
+    cudaFree(ptr);
+  }
+  ptr = nullptr;
+  cap = 0;
+  if (need == 0) need = 1;
+  if (cudaMalloc(reinterpret_cast<void**>(&ptr), need * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    ptr = nullptr;
+    return CASHASH_ENOMEM;
+  }
+  cap = need;
+  return CASHASH_OK;
+}
+
+template <class T>
+void dfree(T*& ptr) {
+  if (ptr) cudaFree(ptr);
+  ptr = nullptr;
+}
+
+// Validates a set; returns number of lookup-table chunks through *n_chunks.
+int set_ok(const cashash_set* s, uint64_t* n_chunks) {
+  if (!s || (s->n_images > 0 && !s->img_off)) return 0;
+  if (s->n_images == 0) {
+    if (n_chunks) *n_chunks = 0;
+    return s->n_features == 0;
+  }
+  if (s->img_off[0] != 0 || s->img_off[s->n_images] != s->n_features) return 0;
+  if (s->n_features >= (1ull << 32)) return 0;
+  uint64_t ch = 0;
+  for (uint32_t i = 0; i < s->n_images; ++i) {
+    if (s->img_off[i + 1] < s->img_off[i]) return 0;
+    const uint64_t n = s->img_off[i + 1] - s->img_off[i];
+    if (n > CASHASH_MAX_IMAGE) return 0;
+    ch += (n + JC - 1) / JC;
+  }
+  if (s->n_features > 0) {
+    if (!s->desc || !s->codes || !s->buckets || !s->sqnorm || !s->tables) return 0;
+    if ((reinterpret_cast<uintptr_t>(s->desc) & 15) || (reinterpret_cast<uintptr_t>(s->codes) & 15) ||
+        (reinterpret_cast<uintptr_t>(s->buckets) & 7) || (reinterpret_cast<uintptr_t>(s->sqnorm) & 3) ||
+        (reinterpret_cast<uintptr_t>(s->tables) & 15) || (reinterpret_cast<uintptr_t>(s->kpts) & 7))
+      return 0;
+  }
+  if (n_chunks) *n_chunks = ch;
+  return 1;
+}
+
+void chunk_layout(const uint64_t* img_off, uint32_t n_images, std::vector<uint64_t>& f0, std::vector<uint32_t>& len,
+                  std::vector<uint32_t>* first_chunk) {
+  f0.clear();
+  len.clear();
+  if (first_chunk) first_chunk->assign(n_images, 0);
+  for (uint32_t i = 0; i < n_images; ++i) {
+    if (first_chunk) (*first_chunk)[i] = (uint32_t)f0.size();
+    const uint64_t n = img_off[i + 1] - img_off[i];
+    for (uint64_t c = 0; c * JC < n; ++c) {
+      f0.push_back(img_off[i] + c * JC);
+      len.push_back((uint32_t)std::min<uint64_t>(JC, n - c * JC));
+    }
+  }
+}
+
+// Stage timing: events recorded on the launching stream around a stage.
+struct StageTimer {
+  cashash_ctx* c;
+  int id;
+  cudaStream_t s;
+  StageTimer(cashash_ctx* c_, int id_, cudaStream_t s_) : c(c_), id(id_), s(s_) {
+    if (c->profiling && c->ev[id][0]) cudaEventRecord(c->ev[id][0], s);
+  }
+  ~StageTimer() {
+    if (c->profiling && c->ev[id][1]) {
+      cudaEventRecord(c->ev[id][1], s);
+      c->ev_used[id] = 1;
+    }
+  }
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C-ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* cashash_strerror(int st) {
+  switch (st) {
+    case CASHASH_OK: return "ok";
+    case CASHASH_EINVAL: return "invalid argument";
+    case CASHASH_ENOMEM: return "out of memory";
+    case CASHASH_ECUDA: return "CUDA runtime error";
+    case CASHASH_EOVERFLOW: return "match capacity exceeded";
+    case CASHASH_EDEVICE: return "device-side error recorded";
+    case CASHASH_ETIMEOUT: return "bounded wait timed out";
+    case CASHASH_ENOTSUP: return "not supported by this build";
+    default: return "unknown status";
+  }
+}
+
+void cashash_default_params(cashash_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof *p);
+  p->code_bits = 128;
+  p->n_tables = 6;
+  p->bits_per_table = 8;
+  p->top_k = 10;
+  p->ratio_num = 4;
+  p->ratio_den = 5;
+  p->tau = 128;
+  p->precision = CASHASH_FP32;
+  p->schedule = CASHASH_SCHED_PERSISTENT;
+  p->epi_px = -1.0;
+}
+
+uint64_t cashash_tables_bytes(const cashash_params* p, const uint64_t* img_off, uint32_t n_images) {
+  if (!params_ok(p) || (n_images > 0 && !img_off)) return 0;
+  uint64_t ch = 0;
+  for (uint32_t i = 0; i < n_images; ++i) {
+    if (img_off[i + 1] < img_off[i]) return 0;
+    ch += (img_off[i + 1] - img_off[i] + JC - 1) / JC;
+  }
+  return std::max<uint64_t>(ch, 1) * chunk_bytes(p->n_tables);
+}
+
+void cashash_destroy(cashash_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  cudaDeviceSynchronize();
+  if (c->hw.plan) cashash_plan_destroy(c->hw.plan);
+  HostWS& h = c->hw;
+  dfree(h.desc); dfree(h.codes); dfree(h.buckets); dfree(h.sqnorm); dfree(h.tables); dfree(h.kpts);
+  dfree(h.F); dfree(h.moff); dfree(h.matches);
+  for (int i = 0; i < 2; ++i) {
+    if (h.pin[i]) cudaFreeHost(h.pin[i]);
+    if (h.ev[i]) cudaEventDestroy(h.ev[i]);
+  }
+  if (h.staged) cudaEventDestroy(h.staged);
+  if (h.copy) cudaStreamDestroy(h.copy);
+  if (h.comp) cudaStreamDestroy(h.comp);
+  dfree(c->d_R); dfree(c->d_nrmR); dfree(c->d_R32T); dfree(c->d_Rbf); dfree(c->d_mu); dfree(c->d_rc);
+  dfree(c->d_colsum); dfree(c->d_cnt); dfree(c->d_status); dfree(c->d_flagmask); dfree(c->d_flaglist);
+  dfree(c->d_chunk_feat0); dfree(c->d_chunk_len);
+  for (int i = 0; i < CASHASH_N_STAGES; ++i)
+    for (int k = 0; k < 2; ++k)
+      if (c->ev[i][k]) cudaEventDestroy(c->ev[i][k]);
+  delete c;
+}
+
+int cashash_create(cashash_ctx** out, const cashash_params* p, const double* R_host) {
+  if (!out || !params_ok(p) || !R_host) return CASHASH_EINVAL;
+  *out = nullptr;
+  const uint32_t rows = p->code_bits + p->n_tables * p->bits_per_table;
+  for (uint64_t i = 0; i < (uint64_t)rows * DIM; ++i)
+    if (!std::isfinite(R_host[i])) return CASHASH_EINVAL;
+  if (p->precision == CASHASH_BF16) return CASHASH_ENOTSUP;
+  cashash_ctx* c = new (std::nothrow) cashash_ctx();
+  if (!c) return CASHASH_ENOMEM;
+  c->p = *p;
+  c->rows = rows;
+  c->kp.code_bits = p->code_bits;
+  c->kp.n_tables = p->n_tables;
+  c->kp.bits_per_table = p->bits_per_table;
+  c->kp.top_k = p->top_k;
+  c->kp.ratio_num = p->ratio_num;
+  c->kp.ratio_den = p->ratio_den;
+  c->kp.tau = std::min(p->tau, p->code_bits);
+  c->kp.rows = rows;
+  c->kp.epi_px = p->epi_px;
+  int st = cuda_err(cudaGetDevice(&c->device));
+  if (st == CASHASH_OK) st = cuda_err(cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device));
+  // host-side constants: FP32 transposed copy of R and row norms (rounded up)
+  std::vector<float> r32t((size_t)DIM * 192, 0.f);
+  std::vector<double> nrm(rows, 0.0);
+  for (uint32_t b = 0; b < rows; ++b) {
+    long double s = 0.0L;
+    for (int j = 0; j < DIM; ++j) {
+      const double v = R_host[(size_t)b * DIM + j];
+      r32t[(size_t)j * 192 + b] = (float)v;
+      s += (long double)v * (long double)v;
+    }
+    nrm[b] = (double)sqrtl(s) * (1.0 + 1e-12);
+  }
+  uint64_t cap = 0;
+  if (st == CASHASH_OK) st = grow(c->d_R, cap, (uint64_t)rows * DIM);
+  cap = 0;
+  if (st == CASHASH_OK) st = grow(c->d_nrmR, cap, rows);
+  cap = 0;
+  if (st == CASHASH_OK) st = grow(c->d_R32T, cap, (uint64_t)DIM * 192);
+  cap = 0;
+  if (st == CASHASH_OK) st = grow(c->d_mu, cap, DIM);
+  cap = 0;
+  if (st == CASHASH_OK) st = grow(c->d_rc, cap, 192);
+  cap = 0;
+  if (st == CASHASH_OK) st = grow(c->d_colsum, cap, DIM);
+  cap = 0;
+  if (st == CASHASH_OK) st = grow(c->d_cnt, cap, 8);
+  cap = 0;
+  if (st == CASHASH_OK) st = grow(c->d_status, cap, 1);
+  if (st == CASHASH_OK) st = cuda_err(cudaMemcpy(c->d_R, R_host, sizeof(double) * rows * DIM, cudaMemcpyHostToDevice));
+  if (st == CASHASH_OK) st = cuda_err(cudaMemcpy(c->d_nrmR, nrm.data(), sizeof(double) * rows, cudaMemcpyHostToDevice));
+  if (st == CASHASH_OK)
+    st = cuda_err(cudaMemcpy(c->d_R32T, r32t.data(), sizeof(float) * r32t.size(), cudaMemcpyHostToDevice));
+  if (st == CASHASH_OK) st = cuda_err(cudaMemset(c->d_cnt, 0, 8 * sizeof(unsigned long long)));
+  if (st == CASHASH_OK) st = cuda_err(cudaMemset(c->d_status, 0, sizeof(uint32_t)));
+  if (st == CASHASH_OK) st = cuda_err(cudaMemset(c->d_mu, 0, DIM * sizeof(double)));
+  if (st != CASHASH_OK) {
+    cashash_destroy(c);
+    return st;
+  }
+  *out = c;
+  return CASHASH_OK;
+}
+
+int cashash_build_codes(cashash_ctx* c, const cashash_set* s, const double* mean_host, cashash_stream_t stream_) {
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+  uint64_t n_chunks = 0;
+  if (!c || !set_ok(s, &n_chunks)) return CASHASH_EINVAL;
+  if (mean_host)
+    for (int j = 0; j < DIM; ++j)
+      if (!std::isfinite(mean_host[j])) return CASHASH_EINVAL;
+  const uint64_t n = s->n_features;
+  CK(cudaSetDevice(c->device));
+  int st = grow(c->d_flagmask, c->cap_flagmask, std::max<uint64_t>(n, 1) * 6);
+  if (st == CASHASH_OK) st = grow(c->d_flaglist, c->cap_flaglist, std::max<uint64_t>(n, 1));
+  if (st == CASHASH_OK) st = grow(c->d_chunk_feat0, c->cap_cf0, std::max<uint64_t>(n_chunks, 1));
+  if (st == CASHASH_OK) st = grow(c->d_chunk_len, c->cap_clen, std::max<uint64_t>(n_chunks, 1));
+  if (st != CASHASH_OK) return st;
+  std::vector<uint64_t> f0;
+  std::vector<uint32_t> len;
+  chunk_layout(s->img_off, s->n_images, f0, len, nullptr);
+  if (n_chunks) {
+    CK(cudaMemcpyAsync(c->d_chunk_feat0, f0.data(), n_chunks * sizeof(uint64_t), cudaMemcpyHostToDevice, stream));
+    CK(cudaMemcpyAsync(c->d_chunk_len, len.data(), n_chunks * sizeof(uint32_t), cudaMemcpyHostToDevice, stream));
+  }
+  for (int i = 0; i < 4; ++i) c->ev_used[i] = 0;
+  {  // centre (reading: mean over the whole set) and per-row constants
+    StageTimer tm(c, CASHASH_STAGE_CENTRE, stream);
+    if (mean_host) {
+      CK(cudaMemcpyAsync(c->d_mu, mean_host, DIM * sizeof(double), cudaMemcpyHostToDevice, stream));
+    } else {
+      CK(launch_colsum(s->desc, n, c->d_colsum, stream));
+      c->n_launches += n ? 1 : 0;
+    }
+    const float alpha_scale = 0x1p-16f;
+    CK(launch_row_consts(c->d_colsum, n, mean_host ? 1 : 0, c->d_mu, c->d_R, c->d_nrmR, c->rows, alpha_scale,
+                         c->d_rc, stream));
+    c->n_launches += 1;
+    CK(cudaMemsetAsync(c->d_cnt, 0, 2 * sizeof(unsigned long long), stream));
+  }
+  if (n) {
+    {
+      StageTimer tm(c, CASHASH_STAGE_PROJECT, stream);
+      CK(launch_project_fp32(s->desc, n, c->d_R32T, c->d_rc, c->kp, s->codes, s->buckets, s->sqnorm, c->d_flagmask,
+                             c->d_flaglist, c->d_cnt + 0, stream));
+    }
+    {
+      StageTimer tm(c, CASHASH_STAGE_REEVAL, stream);
+      CK(launch_fix_fp64(s->desc, c->d_mu, c->d_R, c->kp, c->d_flagmask, c->d_flaglist, c->d_cnt + 0, n, s->codes,
+                         s->buckets, c->d_cnt + 1, stream));
+    }
+    {
+      StageTimer tm(c, CASHASH_STAGE_TABLES, stream);
+      CK(launch_build_tables(s->buckets, c->d_chunk_feat0, c->d_chunk_len, (uint32_t)n_chunks, c->p.n_tables,
+                             s->tables, stream));
+    }
+    c->n_launches += 3;
+  }
+  c->last_stream = stream;
+  c->last_n_features = n;
+  return CASHASH_OK;
+}
+
+int cashash_get_mean(cashash_ctx* c, double* mean_out) {
+  if (!c || !mean_out) return CASHASH_EINVAL;
+  CK(cudaSetDevice(c->device));
+  CK(cudaStreamSynchronize(c->last_stream));
+  CK(cudaMemcpy(mean_out, c->d_mu, DIM * sizeof(double), cudaMemcpyDeviceToHost));
+  return CASHASH_OK;
+}
+
+void cashash_plan_destroy(cashash_plan* pl) {
+  if (!pl) return;
+  cudaDeviceSynchronize();
+  dfree(pl->d_pairs);
+  dfree(pl->d_items);
+  dfree(pl->d_res);
+  dfree(pl->d_pair_cnt);
+  dfree(pl->d_item_ctr);
+  delete pl;
+}
+
+int cashash_plan_create(cashash_ctx* c, const cashash_set* s, const uint32_t* pairs_host, uint32_t P,
+                        cashash_plan** out) {
+  if (!c || !out || !set_ok(s, nullptr) || (P > 0 && !pairs_host)) return CASHASH_EINVAL;
+  *out = nullptr;
+  if (c->p.epi_px >= 0.0 && s->n_features > 0 && !s->kpts) return CASHASH_EINVAL;
+  for (uint32_t i = 0; i < P; ++i)
+    if (pairs_host[2 * (size_t)i] >= s->n_images || pairs_host[2 * (size_t)i + 1] >= s->n_images)
+      return CASHASH_EINVAL;
+  CK(cudaSetDevice(c->device));
+  cashash_plan* pl = new (std::nothrow) cashash_plan();
+  if (!pl) return CASHASH_ENOMEM;
+  pl->ctx = c;
+  pl->P = P;
+  pl->persistent = c->p.schedule == CASHASH_SCHED_PERSISTENT;
+  pl->desc = s->desc;
+  pl->codes = s->codes;
+  pl->buckets = s->buckets;
+  pl->sqnorm = s->sqnorm;
+  pl->tables = s->tables;
+  pl->kpts = s->kpts;
+  std::vector<uint64_t> f0;
+  std::vector<uint32_t> len, firstc;
+  chunk_layout(s->img_off, s->n_images, f0, len, &firstc);
+  std::vector<PairInfo> info(P);
+  uint64_t qbase = 0;
+  for (uint32_t i = 0; i < P; ++i) {
+    const uint32_t a = pairs_host[2 * (size_t)i], b = pairs_host[2 * (size_t)i + 1];
+    PairInfo& pi = info[i];
+    pi.a0 = s->img_off[a];
+    pi.b0 = s->img_off[b];
+    pi.nA = (uint32_t)(s->img_off[a + 1] - s->img_off[a]);
+    pi.nB = (uint32_t)(s->img_off[b + 1] - s->img_off[b]);
+    pi.bchunk0 = firstc[b];
+    pi.pad = 0;
+    pi.qbase = qbase;
+    qbase += pi.nA;
+  }
+  pl->n_res = qbase;
+  const uint32_t tile = (uint32_t)match_tile_size(c->p.top_k, pl->persistent);
+  // work items: persistent schedule groups the pairs by candidate image so
+  // that a candidate image's chunks are reused from L2 by consecutive items
+  std::vector<uint32_t> order(P);
+  for (uint32_t i = 0; i < P; ++i) order[i] = i;
+  if (pl->persistent)
+    std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
+      return pairs_host[2 * (size_t)x + 1] < pairs_host[2 * (size_t)y + 1];
+    });
+  std::vector<uint2> items;
+  pl->first.assign(P, 0);
+  pl->count.assign(P, 0);
+  for (uint32_t oi = 0; oi < P; ++oi) {
+    const uint32_t i = order[oi];
+    pl->first[i] = (uint32_t)items.size();
+    for (uint32_t q0 = 0; q0 < info[i].nA; q0 += tile) items.push_back(make_uint2(i, q0));
+    pl->count[i] = (uint32_t)items.size() - pl->first[i];
+  }
+  pl->n_items = (uint32_t)items.size();
+  uint64_t cap = 0;
+  int st = grow(pl->d_pairs, cap, std::max<uint64_t>(P, 1));
+  cap = 0;
+  if (st == CASHASH_OK) st = grow(pl->d_items, cap, std::max<uint64_t>(items.size(), 1));
+  cap = 0;
+  if (st == CASHASH_OK) st = grow(pl->d_res, cap, std::max<uint64_t>(qbase, 1));
+  cap = 0;
+  if (st == CASHASH_OK) st = grow(pl->d_pair_cnt, cap, std::max<uint64_t>(P, 1));
+  cap = 0;
+  if (st == CASHASH_OK) st = grow(pl->d_item_ctr, cap, 1);
+  if (st == CASHASH_OK && P)
+    st = cuda_err(cudaMemcpy(pl->d_pairs, info.data(), sizeof(PairInfo) * P, cudaMemcpyHostToDevice));
+  if (st == CASHASH_OK && !items.empty())
+    st = cuda_err(cudaMemcpy(pl->d_items, items.data(), sizeof(uint2) * items.size(), cudaMemcpyHostToDevice));
+  if (st != CASHASH_OK) {
+    cashash_plan_destroy(pl);
+    return st;
+  }
+  *out = pl;
+  return CASHASH_OK;
+}
+
+int cashash_match_plan(cashash_ctx* c, cashash_plan* pl, const double* F_dev, uint64_t* match_off,
+                       uint32_t* matches, uint64_t cap, cashash_stream_t stream_) {
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+  if (!c || !pl || pl->ctx != c || !match_off || (cap > 0 && !matches)) return CASHASH_EINVAL;
+  if (c->p.epi_px >= 0.0 && pl->P > 0 && !F_dev) return CASHASH_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(match_off) & 7) || (reinterpret_cast<uintptr_t>(matches) & 3)) return CASHASH_EINVAL;
+  CK(cudaSetDevice(c->device));
+  const uint32_t P = pl->P;
+  if (P) CK(cudaMemsetAsync(pl->d_pair_cnt, 0, sizeof(unsigned long long) * P, stream));
+  MatchArgs a{};
+  a.desc = pl->desc;
+  a.codes = pl->codes;
+  a.buckets = pl->buckets;
+  a.sqnorm = pl->sqnorm;
+  a.tables = pl->tables;
+  a.kpts = pl->kpts;
+  a.F = c->p.epi_px >= 0.0 ? F_dev : nullptr;
+  a.pairs = pl->d_pairs;
+  a.item_ctr = pl->d_item_ctr;
+  a.res = pl->d_res;
+  a.pair_cnt = pl->d_pair_cnt;
+  a.status = c->d_status;
+  a.kp = c->kp;
+  c->ev_used[CASHASH_STAGE_MATCH] = c->ev_used[CASHASH_STAGE_COMPACT] = 0;
+  {
+    StageTimer tm(c, CASHASH_STAGE_MATCH, stream);
+    if (pl->persistent) {
+      CK(cudaMemsetAsync(pl->d_item_ctr, 0, sizeof(unsigned int), stream));
+      a.items = pl->d_items;
+      a.n_items = pl->n_items;
+      const uint32_t grid = std::min<uint32_t>(pl->n_items, (uint32_t)c->nsm);
+      CK(launch_match(a, 1, grid, stream));
+      c->n_launches += grid ? 1 : 0;
+    } else {
+      for (uint32_t i = 0; i < P; ++i) {
+        if (!pl->count[i]) continue;
+        a.items = pl->d_items + pl->first[i];
+        a.n_items = pl->count[i];
+        CK(launch_match(a, 0, pl->count[i], stream));
+        c->n_launches += 1;
+      }
+    }
+  }
+  {
+    StageTimer tm(c, CASHASH_STAGE_COMPACT, stream);
+    CK(launch_scan_counts(pl->d_pair_cnt, P, match_off, cap, c->d_status, c->d_cnt + 2, stream));
+    CK(launch_compact(pl->d_pairs, P, pl->d_res, match_off, matches, cap, stream));
+    c->n_launches += P ? 2 : 1;
+  }
+  c->last_stream = stream;
+  c->last_pairs = P;
+  c->last_items = pl->n_items;
+  return CASHASH_OK;
+}
+
+int cashash_match_pairs(cashash_ctx* c, const cashash_set* s, const uint32_t* pairs_host, uint32_t P,
+                        const double* F_dev, uint64_t* match_off, uint32_t* matches, uint64_t cap,
+                        cashash_stream_t stream) {
+  cashash_plan* pl = nullptr;
+  int st = cashash_plan_create(c, s, pairs_host, P, &pl);
+  if (st != CASHASH_OK) return st;
+  st = cashash_match_plan(c, pl, F_dev, match_off, matches, cap, stream);
+  if (st == CASHASH_OK) st = cuda_err(cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)));
+  cashash_plan_destroy(pl);
+  return st;
+}
+
+int cashash_sync_status(cashash_ctx* c, cashash_stream_t stream) {
+  if (!c) return CASHASH_EINVAL;
+  CK(cudaSetDevice(c->device));
+  CK(cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)));
+  uint32_t s = 0;
+  CK(cudaMemcpy(&s, c->d_status, sizeof s, cudaMemcpyDeviceToHost));
+  CK(cudaMemset(c->d_status, 0, sizeof(uint32_t)));
+  if (s & DST_INDEX) return CASHASH_EDEVICE;
+  if (s & DST_OVERFLOW) return CASHASH_EOVERFLOW;
+  return CASHASH_OK;
+}
+
+int cashash_set_profiling(cashash_ctx* c, int on) {
+  if (!c) return CASHASH_EINVAL;
+  CK(cudaSetDevice(c->device));
+  if (on && !c->ev[0][0]) {
+    for (int i = 0; i < CASHASH_N_STAGES; ++i)
+      for (int k = 0; k < 2; ++k) CK(cudaEventCreate(&c->ev[i][k]));
+  }
+  c->profiling = on ? 1 : 0;
+  return CASHASH_OK;
+}
+
+int cashash_get_stats(cashash_ctx* c, cashash_stats* out) {
+  if (!c || !out) return CASHASH_EINVAL;
+  CK(cudaSetDevice(c->device));
+  CK(cudaStreamSynchronize(c->last_stream));
+  unsigned long long h[8];
+  CK(cudaMemcpy(h, c->d_cnt, sizeof h, cudaMemcpyDeviceToHost));
+  out->n_features = c->last_n_features;
+  out->n_reevaluated = h[1];
+  out->n_pairs = c->last_pairs;
+  out->n_matches = h[2];
+  out->n_work_items = c->last_items;
+  out->n_launches = c->n_launches;
+  for (int i = 0; i < CASHASH_N_STAGES; ++i) {
+    out->ms_stage[i] = -1.0;
+    if (c->ev_used[i] && c->ev[i][0]) {
+      float ms = 0.f;
+      CK(cudaEventSynchronize(c->ev[i][1]));
+      CK(cudaEventElapsedTime(&ms, c->ev[i][0], c->ev[i][1]));
+      out->ms_stage[i] = ms;
+    }
+  }
+  return CASHASH_OK;
+}
+
+int cashash_run_host(cashash_ctx* c, const uint8_t* desc_host, const uint64_t* img_off, uint32_t n_images,
+                     const float* kpts_host, const uint32_t* pairs_host, uint32_t P, const double* F_host,
+                     uint64_t* match_off_host, uint32_t* matches_host, uint64_t cap, uint64_t stage_bytes) {
+  if (!c || (n_images > 0 && !img_off) || !match_off_host || (cap > 0 && !matches_host)) return CASHASH_EINVAL;
+  const uint64_t N = n_images ? img_off[n_images] : 0;
+  if (N > 0 && !desc_host) return CASHASH_EINVAL;
+  const bool epi = c->p.epi_px >= 0.0;
+  if (epi && ((N > 0 && !kpts_host) || (P > 0 && !F_host))) return CASHASH_EINVAL;
+  if (stage_bytes == 0) stage_bytes = 4ull << 30;
+  stage_bytes = std::max<uint64_t>(stage_bytes & ~(uint64_t)15, 1u << 20);
+  CK(cudaSetDevice(c->device));
+  HostWS& h = c->hw;
+  if (!h.copy) {
+    CK(cudaStreamCreateWithFlags(&h.copy, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&h.comp, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&h.ev[0], cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&h.ev[1], cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&h.staged, cudaEventDisableTiming));
+  }
+  int st = CASHASH_OK;
+  cashash_params pp = c->p;
+  const uint64_t tb = cashash_tables_bytes(&pp, img_off, n_images);
+  if ((st = grow(h.desc, h.cap_desc, std::max<uint64_t>(N, 1) * DIM)) != CASHASH_OK) return st;
+  if ((st = grow(h.codes, h.cap_codes, std::max<uint64_t>(N, 1) * 4)) != CASHASH_OK) return st;
+  if ((st = grow(h.buckets, h.cap_buckets, std::max<uint64_t>(N, 1) * 8)) != CASHASH_OK) return st;
+  if ((st = grow(h.sqnorm, h.cap_sq, std::max<uint64_t>(N, 1))) != CASHASH_OK) return st;
+  if ((st = grow(h.tables, h.cap_tables, tb)) != CASHASH_OK) return st;
+  if ((st = grow(h.moff, h.cap_moff, (uint64_t)P + 1)) != CASHASH_OK) return st;
+  if (epi) {
+    if ((st = grow(h.kpts, h.cap_kpts, std::max<uint64_t>(N, 1) * 2)) != CASHASH_OK) return st;
+    if ((st = grow(h.F, h.cap_F, std::max<uint64_t>(P, 1) * 9)) != CASHASH_OK) return st;
+  }
+  // descriptors: host -> device on the copy stream; pinned sources are copied
+  // directly, pageable ones through two pinned bounce buffers
+  const uint64_t bytes = N * DIM;
+  if (bytes) {
+    cudaPointerAttributes attr{};
+    bool pinned = false;
+    if (cudaPointerGetAttributes(&attr, desc_host) == cudaSuccess)
+      pinned = attr.type == cudaMemoryTypeHost;
+    else
+      cudaGetLastError();
+    if (pinned) {
+      for (uint64_t o = 0; o < bytes; o += stage_bytes)
+        CK(cudaMemcpyAsync(h.desc + o, desc_host + o, std::min(stage_bytes, bytes - o), cudaMemcpyHostToDevice, h.copy));
+    } else {
+      const uint64_t chunk = std::min(stage_bytes, bytes);
+      if (h.pin_cap < chunk) {
+        for (int i = 0; i < 2; ++i) {
+          if (h.pin[i]) cudaFreeHost(h.pin[i]);
+          h.pin[i] = nullptr;
+        }
+        h.pin_cap = 0;
+        for (int i = 0; i < 2; ++i)
+          if (cudaHostAlloc(reinterpret_cast<void**>(&h.pin[i]), chunk, cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            return CASHASH_ENOMEM;
+          }
+        h.pin_cap = chunk;
+      }
+      uint64_t k = 0;
+      for (uint64_t o = 0; o < bytes; o += chunk, ++k) {
+        const int b = (int)(k & 1);
+        if (k >= 2) CK(cudaEventSynchronize(h.ev[b]));
+        const uint64_t l = std::min(chunk, bytes - o);
+        std::memcpy(h.pin[b], desc_host + o, l);
+        CK(cudaMemcpyAsync(h.desc + o, h.pin[b], l, cudaMemcpyHostToDevice, h.copy));
+        CK(cudaEventRecord(h.ev[b], h.copy));
+      }
+    }
+  }
+  CK(cudaEventRecord(h.staged, h.copy));
+  CK(cudaStreamWaitEvent(h.comp, h.staged, 0));
+  if (epi) {
+    if (N) CK(cudaMemcpyAsync(h.kpts, kpts_host, N * 2 * sizeof(float), cudaMemcpyHostToDevice, h.comp));
+    if (P) CK(cudaMemcpyAsync(h.F, F_host, (uint64_t)P * 9 * sizeof(double), cudaMemcpyHostToDevice, h.comp));
+  }
+  cashash_set S{};
+  S.n_images = n_images;
+  S.n_features = N;
+  S.img_off = img_off;
+  S.desc = h.desc;
+  S.codes = h.codes;
+  S.buckets = h.buckets;
+  S.sqnorm = h.sqnorm;
+  S.tables = h.tables;
+  S.kpts = epi ? h.kpts : nullptr;
+  st = cashash_build_codes(c, &S, nullptr, reinterpret_cast<cashash_stream_t>(h.comp));
+  if (st != CASHASH_OK) return st;
+  // plan: reused while the pair list and image sizes are unchanged
+  const bool same = h.plan && h.plan_pairs.size() == 2 * (size_t)P && h.plan_off.size() == (size_t)n_images + 1 &&
+                    (P == 0 || std::memcmp(h.plan_pairs.data(), pairs_host, 8 * (size_t)P) == 0) &&
+                    std::memcmp(h.plan_off.data(), img_off, 8 * ((size_t)n_images + 1)) == 0 &&
+                    h.plan->desc == h.desc && h.plan->tables == h.tables && h.plan->kpts == S.kpts;
+  if (!same) {
+    if (h.plan) cashash_plan_destroy(h.plan);
+    h.plan = nullptr;
+    st = cashash_plan_create(c, &S, pairs_host, P, &h.plan);
+    if (st != CASHASH_OK) return st;
+    h.plan_pairs.assign(pairs_host, pairs_host + 2 * (size_t)P);
+    h.plan_off.assign(img_off, img_off + n_images + 1);
+  }
+  const uint64_t mcap = std::min<uint64_t>(cap, std::max<uint64_t>(h.plan->n_res, 1));
+  if ((st = grow(h.matches, h.cap_matches, std::max<uint64_t>(mcap, 1) * 2)) != CASHASH_OK) return st;
+  st = cashash_match_plan(c, h.plan, epi ? h.F : nullptr, h.moff, h.matches, mcap,
+                          reinterpret_cast<cashash_stream_t>(h.comp));
+  if (st != CASHASH_OK) return st;
+  CK(cudaMemcpyAsync(match_off_host, h.moff, ((uint64_t)P + 1) * sizeof(uint64_t), cudaMemcpyDeviceToHost, h.comp));
+  CK(cudaStreamSynchronize(h.comp));
+  const uint64_t total = match_off_host[P];
+  const uint64_t ncopy = std::min(total, mcap);
+  if (ncopy) CK(cudaMemcpyAsync(matches_host, h.matches, ncopy * 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, h.comp));
+  st = cashash_sync_status(c, reinterpret_cast<cashash_stream_t>(h.comp));
+  if (st == CASHASH_OK && total > cap) st = CASHASH_EOVERFLOW;
+  return st;
+}
+
+}  // extern "C"

@@ -1,0 +1,94 @@
+// Internal declarations of the CUDA Cascade Hashing library (not part of the C-ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/cashash.h"
+
+namespace chx {
+
+constexpr int DIM = 128;
+constexpr int MAX_ROWS = 128 + CASHASH_MAX_TABLES * 8;  // projection rows: remap code + table bits
+constexpr int JC = 4096;          // features of the candidate image per lookup-table chunk
+constexpr int OFF_STRIDE = 264;   // uint16 bucket offsets per (chunk, table): 257 used, padded to 16 B
+constexpr uint32_t NO_MATCH = 0xFFFFFFFFu;
+constexpr uint32_t KEY_INF = 0xFFFFFFFFu;
+
+// device status bits (ORed into the context's status word)
+enum : uint32_t { DST_OVERFLOW = 1u, DST_INDEX = 2u };
+
+// Bytes of one lookup-table chunk: T tables x (bucket offsets + local indices), uint16.
+__host__ __device__ inline uint64_t chunk_bytes(uint32_t T) {
+  return (uint64_t)T * (uint64_t)(OFF_STRIDE + JC) * 2u;
+}
+
+// Parameters passed to kernels by value.
+struct KParams {
+  uint32_t code_bits, n_tables, bits_per_table, top_k;
+  uint32_t ratio_num, ratio_den, tau, rows;
+  double epi_px;
+};
+
+// One image pair of a plan.
+struct PairInfo {
+  uint64_t a0, b0;      // first feature of the query image / candidate image
+  uint64_t qbase;       // offset of this pair's queries in the per-query result array
+  uint32_t nA, nB;      // feature counts
+  uint32_t bchunk0;     // first lookup-table chunk of the candidate image
+  uint32_t pad;
+};
+
+// Per-row constants of the projection (Sec. 4.1) derived from R and the centre.
+struct RowConst {
+  float c32;     // fl32(c_b), c_b = sum_j R_bj mu_j
+  float alpha;   // bound factor on ||x||_2 (FP32 form) or on ||x||_2 (BF16 form)
+  float beta;    // additive bound term
+  float pad;
+};
+
+// ---- launchers (return cudaError_t of the launch) ----
+cudaError_t launch_colsum(const uint8_t* desc, uint64_t n, unsigned long long* sums, cudaStream_t s);
+cudaError_t launch_row_consts(const unsigned long long* sums, uint64_t n, int have_mean, double* mu,
+                              const double* R, const double* nrmR, uint32_t rows, float alpha_scale,
+                              RowConst* rc, cudaStream_t s);
+cudaError_t launch_project_fp32(const uint8_t* desc, uint64_t n, const float* R32T, const RowConst* rc,
+                                const KParams& kp, uint32_t* codes, uint8_t* buckets, uint32_t* sqnorm,
+                                uint32_t* flagmask, uint32_t* flaglist, unsigned long long* nflag_feat,
+                                cudaStream_t s);
+cudaError_t launch_project_bf16(const uint8_t* desc, uint64_t n, const void* Rbf, const RowConst* rc,
+                                const KParams& kp, uint32_t* codes, uint8_t* buckets, uint32_t* sqnorm,
+                                uint32_t* flagmask, uint32_t* flaglist, unsigned long long* nflag_feat,
+                                cudaStream_t s);
+cudaError_t launch_fix_fp64(const uint8_t* desc, const double* mu, const double* R, const KParams& kp,
+                            const uint32_t* flagmask, const uint32_t* flaglist,
+                            const unsigned long long* nflag_feat, uint64_t max_feat, uint32_t* codes,
+                            uint8_t* buckets, unsigned long long* n_reeval, cudaStream_t s);
+cudaError_t launch_build_tables(const uint8_t* buckets, const uint64_t* chunk_feat0, const uint32_t* chunk_len,
+                                uint32_t n_chunks, uint32_t n_tables, uint8_t* tables, cudaStream_t s);
+
+struct MatchArgs {
+  const uint8_t* desc;
+  const uint32_t* codes;
+  const uint8_t* buckets;
+  const uint32_t* sqnorm;
+  const uint8_t* tables;
+  const float* kpts;
+  const double* F;           // [P][9] or null
+  const PairInfo* pairs;
+  const uint2* items;        // (pair, first query) work items
+  uint32_t n_items;
+  unsigned int* item_ctr;    // persistent schedule counter
+  uint32_t* res;             // per-query result (candidate index or NO_MATCH)
+  unsigned long long* pair_cnt;
+  uint32_t* status;
+  KParams kp;
+};
+cudaError_t launch_match(const MatchArgs& a, int persistent, uint32_t grid_items, cudaStream_t s);
+int match_tile_size(uint32_t top_k, int persistent);
+cudaError_t launch_scan_counts(const unsigned long long* pair_cnt, uint32_t P, uint64_t* match_off,
+                               uint64_t cap, uint32_t* status, unsigned long long* total, cudaStream_t s);
+cudaError_t launch_compact(const PairInfo* pairs, uint32_t P, const uint32_t* res, const uint64_t* match_off,
+                           uint32_t* matches, uint64_t cap, cudaStream_t s);
+
+}  // namespace chx

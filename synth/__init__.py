@@ -51,8 +51,10 @@ def noisy_copy(rng: np.random.Generator, desc: np.ndarray, sigma: float = 8.0) -
     return np.clip(np.rint(desc.astype(np.float64) + noise), 0, 255).astype(np.uint8)
 
 
-def projection_matrix(seed: int, rows: int = 176) -> np.ndarray:
-    """The random vectors r_k as a [rows][128] float64 N(0,1) matrix."""
+def projection_matrix(seed: int, rows: int = 192) -> np.ndarray:
+    """The random vectors r_k as a [rows][128] float64 N(0,1) matrix (192 rows
+    cover every parameter set: 128 code rows + up to 8 tables x 8 bits; the
+    leading rows do not depend on `rows`)."""
     return np.random.default_rng(np.random.SeedSequence([seed, 0x5EED])).standard_normal((rows, DIM))
 
 
@@ -61,7 +63,7 @@ class ImageSet:
     desc: np.ndarray          # [N_total][128] uint8, images back to back
     img_off: np.ndarray       # [n_images + 1] uint64 feature offsets
     pairs: np.ndarray         # [P][2] uint32 (query image, candidate image)
-    R: np.ndarray             # [176][128] float64 projection matrix
+    R: np.ndarray             # [192][128] float64 projection matrix (leading rows used)
     name: str = ""
     F: np.ndarray | None = None      # [P][9] float64, x_B^T F x_A = 0
     kpts: np.ndarray | None = None   # [N_total][2] float32

@@ -1,0 +1,91 @@
+"""The C-ABI library builds, loads and exports every declared symbol (CPU).
+
+No compute call is made: the library is loaded with ctypes and only its
+host-side entry points that need no device are exercised.
+"""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "cashash.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1805_08995_gb300 import build
+    path = build.build()
+    return C.CDLL(path), path
+
+
+def declared_functions():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    names = re.findall(r"\b(cashash_[a-z_]+)\s*\(", txt)
+    return sorted(set(names))
+
+
+def test_every_declared_function_is_exported(lib):
+    _, path = lib
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\sT\s(cashash_\w+)", out))
+    declared = declared_functions()
+    assert len(declared) >= 14
+    missing = [n for n in declared if n not in exported]
+    assert not missing, missing
+
+
+def test_binding_names_match_header():
+    import paper_1805_08995_gb300 as ch
+    assert sorted(ch.exported_symbols()) == sorted(n for n in declared_functions())
+
+
+def test_strerror_and_defaults_without_device(lib):
+    import paper_1805_08995_gb300 as ch
+    assert ch.cashash_strerror(0) == "ok"
+    assert ch.cashash_strerror(4) == "match capacity exceeded"
+    assert ch.cashash_strerror(99) == "unknown status"
+    p = ch.cashash_default_params()
+    assert (p.code_bits, p.n_tables, p.bits_per_table, p.top_k, p.ratio_num, p.ratio_den) == (128, 6, 8, 10, 4, 5)
+    assert p.epi_px < 0
+
+
+def test_tables_bytes_host_arithmetic(lib):
+    import paper_1805_08995_gb300 as ch
+    p = ch.cashash_default_params()
+    off = np.array([0, 4096, 4097, 4097, 20000], np.uint64)
+    # chunks: 1 + 1 + 0 + 4 = 6; each chunk holds 6 tables x (264 + 4096) uint16
+    assert ch.cashash_tables_bytes(p, off) == 6 * 6 * (264 + 4096) * 2
+    bad = ch.cashash_default_params(n_tables=0)
+    assert ch.cashash_tables_bytes(bad, off) == 0
+    assert ch.cashash_tables_bytes(p, np.array([0, 5, 3], np.uint64)) == 0
+
+
+def test_create_rejects_bad_arguments_before_touching_a_device(lib):
+    import paper_1805_08995_gb300 as ch
+    R = np.zeros((256, 128))  # enough rows for any parameter set tried below
+    for kw in (dict(top_k=0), dict(code_bits=100), dict(n_tables=9), dict(bits_per_table=9),
+               dict(ratio_den=0), dict(precision=7), dict(schedule=5)):
+        with pytest.raises(ch.CashashError) as e:
+            ch.cashash_create(ch.cashash_default_params(**kw), R)
+        assert e.value.status == ch.CASHASH_EINVAL
+    Rn = R.copy()
+    Rn[3, 4] = np.nan
+    with pytest.raises(ch.CashashError) as e:
+        ch.cashash_create(ch.cashash_default_params(), Rn)
+    assert e.value.status == ch.CASHASH_EINVAL
+
+
+def test_package_fails_loudly_without_library(tmp_path):
+    """The product path has no CPU fallback: without libcashash.so it raises."""
+    import sys
+    code = ("import sys; sys.path.insert(0, %r); import paper_1805_08995_gb300 as ch; "
+            "ch.LIB_PATH = %r; ch._lib = None\n"
+            "try:\n    ch.cashash_default_params()\nexcept ImportError as e:\n    print('raised', e)\n" %
+            (ROOT, str(tmp_path / "missing.so")))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True)
+    assert "raised" in r.stdout

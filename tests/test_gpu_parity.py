@@ -1,0 +1,248 @@
+"""CUDA path vs the CPU oracle, element by element, through the C-ABI.
+
+Codes and bucket ids are compared bit for bit, lookup tables as sets per
+bucket, match lists entry for entry (the output order is defined: pairs in
+input order, ascending query index).
+"""
+import threading
+
+import numpy as np
+import pytest
+
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+JC = 4096          # features per lookup-table chunk (library layout)
+OFF_STRIDE = 264   # uint16 offsets per (chunk, table)
+
+
+@pytest.fixture(scope="module")
+def ch():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1805_08995_gb300 as m
+    torch.cuda.set_device(0)
+    return m
+
+
+def oracle_codes(orc, desc, R, po, mu=None, threads=8):
+    """Oracle codes, computed in parallel row blocks (ctypes releases the GIL)."""
+    if mu is None:
+        mu = orc.mean(desc)
+    n = desc.shape[0]
+    codes = np.zeros((n, 4), np.uint32)
+    buckets = np.zeros((n, po.n_tables), np.uint8)
+    step = max(1, (n + threads - 1) // threads)
+
+    def work(s):
+        c, b = orc.hash_codes(desc[s:s + step], mu, R, po)
+        codes[s:s + step] = c
+        buckets[s:s + step] = b
+
+    ts = [threading.Thread(target=work, args=(s,)) for s in range(0, n, step)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    return mu, codes, buckets
+
+
+def gpu_run(ch, s, pairs, **pk):
+    p = ch.cashash_default_params(**pk)
+    ctx = ch.cashash_create(p, s.R)
+    ds = ch.DeviceSet(p, s.img_off, s.desc, s.kpts)
+    ch.cashash_build_codes(ctx, ds)
+    pairs = np.asarray(pairs, np.uint32).reshape(-1, 2)
+    P = pairs.shape[0]
+    cap = int(s.sizes()[pairs[:, 0]].sum()) if P else 0
+    moff = torch.zeros(P + 1, dtype=torch.int64, device="cuda")
+    mt = torch.zeros((max(cap, 1), 2), dtype=torch.int32, device="cuda")
+    F = None if s.F is None else torch.from_numpy(np.ascontiguousarray(s.F)).cuda()
+    ch.cashash_match_pairs(ctx, ds, pairs, moff, mt, cap, F=F)
+    assert ch.cashash_sync_status(ctx) == ch.CASHASH_OK
+    off = moff.cpu().numpy().astype(np.uint64)
+    got = mt[:int(off[-1])].cpu().numpy().view(np.uint32)
+    stats = ch.cashash_get_stats(ctx)
+    return ctx, ds, off, got, stats
+
+
+def oparams(orc, pk):
+    return orc.params(code_bits=pk.get("code_bits", 128), n_tables=pk.get("n_tables", 6),
+                      bits_per_table=pk.get("bits_per_table", 8), top_k=pk.get("top_k", 10),
+                      ratio=(pk.get("ratio_num", 4), pk.get("ratio_den", 5)), tau=pk.get("tau", None),
+                      epi_px=pk.get("epi_px", -1.0))
+
+
+def check_case(ch, orc, s, pairs, **pk):
+    ctx, ds, off, got, stats = gpu_run(ch, s, pairs, **pk)
+    po = oparams(orc, pk)
+    mu, codes, buckets = oracle_codes(orc, s.desc, s.R, po)
+    assert np.array_equal(ch.cashash_get_mean(ctx), mu)
+    assert np.array_equal(ds.codes_np(), codes)
+    assert np.array_equal(ds.buckets_np(po.n_tables), buckets)
+    assert not ds.buckets[:ds.n, po.n_tables:].any().item()
+    sq = (s.desc.astype(np.int64) ** 2).sum(axis=1)
+    assert np.array_equal(ds.sqnorm[:ds.n].cpu().numpy().astype(np.int64), sq)
+    eoff, emt = orc.match_pairs(s.desc, s.img_off, codes, buckets, pairs, po, F=s.F, kpts=s.kpts)
+    assert np.array_equal(off, eoff)
+    assert np.array_equal(got, emt)
+    ctx.close()
+    return ds, codes, buckets, stats
+
+
+SIZES = [300, 1, 0, 2500, 5000, 4097, 4096, 33]
+
+
+def _pairs(sizes, extra=()):
+    n = len(sizes)
+    pr = [(i, k) for i in range(n) for k in range(n) if i != k and (i + k) % 3 != 1]
+    pr += [(i, i) for i in (3, 4) if i < n] + list(extra)
+    return np.array(pr, np.uint32)
+
+
+@pytest.mark.parametrize("sched", [0, 1])
+def test_default_parameters_ragged_images(ch, orc, sched):
+    s = synth.random_set(101, SIZES)
+    check_case(ch, orc, s, _pairs(SIZES), schedule=sched)
+
+
+@pytest.mark.parametrize("pk", [
+    dict(top_k=4), dict(top_k=16), dict(top_k=32), dict(top_k=1), dict(top_k=2),
+    dict(bits_per_table=4, n_tables=3), dict(bits_per_table=0, n_tables=1, top_k=8),
+    dict(n_tables=8, bits_per_table=8), dict(n_tables=1, bits_per_table=5),
+    dict(code_bits=64), dict(code_bits=32, n_tables=2), dict(code_bits=96, n_tables=4, bits_per_table=6),
+    dict(tau=40), dict(tau=0), dict(ratio_num=9, ratio_den=10),
+])
+@pytest.mark.parametrize("sched", [0, 1])
+def test_parameter_variants(ch, orc, pk, sched):
+    sizes = [700, 1300, 0, 260, 4500]
+    s = synth.random_set(202, sizes)
+    check_case(ch, orc, s, _pairs(sizes), schedule=sched, **pk)
+
+
+def test_lookup_tables_are_the_bucket_sets(ch, orc):
+    sizes = [5000, 10, 0, 4096, 8193]
+    s = synth.random_set(303, sizes)
+    p = ch.cashash_default_params()
+    ctx = ch.cashash_create(p, s.R)
+    ds = ch.DeviceSet(p, s.img_off, s.desc)
+    ch.cashash_build_codes(ctx, ds)
+    torch.cuda.synchronize()
+    tb = ds.tables.cpu().numpy().view(np.uint16)
+    buckets = ds.buckets_np(6)
+    chunk_u16 = 6 * (OFF_STRIDE + JC)
+    k = 0
+    for i in range(len(sizes)):
+        a0 = int(s.img_off[i])
+        n = sizes[i]
+        for c in range(0, n, JC):
+            blk = tb[k * chunk_u16:(k + 1) * chunk_u16]
+            ln = min(JC, n - c)
+            for t in range(6):
+                off = blk[t * OFF_STRIDE:t * OFF_STRIDE + 257].astype(np.int64)
+                idx = blk[6 * OFF_STRIDE + t * JC:6 * OFF_STRIDE + t * JC + ln].astype(np.int64)
+                assert off[0] == 0 and off[256] == ln and np.all(np.diff(off) >= 0)
+                bb = buckets[a0 + c:a0 + c + ln, t]
+                exp_off = np.concatenate([[0], np.cumsum(np.bincount(bb, minlength=256))])
+                assert np.array_equal(off, exp_off)
+                for v in range(0, 256, 17):
+                    got = idx[off[v]:off[v + 1]]
+                    assert np.array_equal(got, np.nonzero(bb == v)[0])
+            k += 1
+    ctx.close()
+
+
+def test_one_pair_workload_config0(ch, orc):
+    s = synth.config0()
+    for sched in (0, 1):
+        check_case(ch, orc, s, s.pairs, schedule=sched)
+
+
+def test_identical_and_degenerate_descriptors(ch, orc):
+    """Single-feature images, empty images, and a set whose descriptors are
+    all identical: the centre equals every descriptor, every projection is
+    exactly 0, every row goes through the double re-evaluation and every bit
+    is 0 (sign at exactly zero)."""
+    rng = np.random.default_rng(5)
+    one = synth.sift_like(rng, 1)
+    desc = np.concatenate([np.repeat(one, 40, axis=0), synth.sift_like(rng, 1), synth.sift_like(rng, 30)])
+    s = synth.ImageSet(desc, np.array([0, 40, 41, 41, 71], np.uint64),
+                       np.array([[0, 0], [0, 1], [1, 0], [2, 0], [0, 2], [3, 0], [0, 3], [3, 3]], np.uint32),
+                       synth.projection_matrix(5))
+    check_case(ch, orc, s, s.pairs)
+    same = synth.ImageSet(np.repeat(one, 50, axis=0), np.array([0, 20, 50], np.uint64),
+                          np.array([[0, 1], [1, 0], [0, 0]], np.uint32), synth.projection_matrix(6))
+    ds, codes, buckets, stats = check_case(ch, orc, same, same.pairs)
+    assert not codes.any() and not buckets.any()
+    assert stats["n_reevaluated"] == 50 * 176
+
+
+def test_many_pairs_medium(ch, orc):
+    s = synth.config1(seed=11, n_images=12, lo=1500, hi=4500)
+    check_case(ch, orc, s, s.pairs, schedule=1)
+
+
+def test_capacity_overflow_reports_and_truncates(ch, orc):
+    sizes = [800, 900, 700]
+    s = synth.random_set(404, sizes)
+    pairs = np.array([[0, 1], [1, 2], [2, 0]], np.uint32)
+    p = ch.cashash_default_params()
+    ctx = ch.cashash_create(p, s.R)
+    ds = ch.DeviceSet(p, s.img_off, s.desc)
+    ch.cashash_build_codes(ctx, ds)
+    moff = torch.zeros(4, dtype=torch.int64, device="cuda")
+    mt = torch.full((50, 2), -7, dtype=torch.int32, device="cuda")
+    ch.cashash_match_pairs(ctx, ds, pairs, moff, mt, 40)
+    assert ch.cashash_sync_status(ctx) == ch.CASHASH_EOVERFLOW
+    assert ch.cashash_sync_status(ctx) == ch.CASHASH_OK  # cleared
+    po = orc.params()
+    mu, codes, buckets = oracle_codes(orc, s.desc, s.R, po)
+    eoff, emt = orc.match_pairs(s.desc, s.img_off, codes, buckets, pairs, po)
+    assert np.array_equal(moff.cpu().numpy().astype(np.uint64), eoff)
+    got = mt.cpu().numpy()
+    assert np.array_equal(got[:40].view(np.uint32), emt[:40])
+    assert (got[40:] == -7).all()
+    ctx.close()
+
+
+def test_host_end_to_end_matches_device_path(ch, orc):
+    sizes = [3000, 4100, 0, 2000]
+    s = synth.random_set(505, sizes)
+    pairs = _pairs(sizes)
+    p = ch.cashash_default_params()
+    ctx = ch.cashash_create(p, s.R)
+    cap = int(s.sizes()[pairs[:, 0]].sum())
+    po = orc.params()
+    mu, codes, buckets = oracle_codes(orc, s.desc, s.R, po)
+    eoff, emt = orc.match_pairs(s.desc, s.img_off, codes, buckets, pairs, po)
+    pinned = torch.from_numpy(s.desc).pin_memory()
+    for desc, stage in ((s.desc, 0), (pinned, 0), (s.desc, 1 << 20), (pinned, 1 << 20)):
+        st, off, mt = ch.cashash_run_host(ctx, desc, s.img_off, pairs, cap, stage_bytes=stage)
+        assert st == ch.CASHASH_OK
+        assert np.array_equal(off, eoff) and np.array_equal(mt, emt)
+    st, off, mt = ch.cashash_run_host(ctx, s.desc, s.img_off, pairs, 10)
+    assert st == ch.CASHASH_EOVERFLOW and np.array_equal(off, eoff) and np.array_equal(mt, emt[:10])
+    ctx.close()
+
+
+def test_invalid_arguments_are_rejected(ch):
+    s = synth.random_set(606, [100, 50])
+    p = ch.cashash_default_params()
+    ctx = ch.cashash_create(p, s.R)
+    ds = ch.DeviceSet(p, s.img_off, s.desc)
+    ch.cashash_build_codes(ctx, ds)
+    moff = torch.zeros(2, dtype=torch.int64, device="cuda")
+    mt = torch.zeros((100, 2), dtype=torch.int32, device="cuda")
+    with pytest.raises(ch.CashashError) as e:
+        ch.cashash_match_pairs(ctx, ds, np.array([[0, 2]], np.uint32), moff, mt, 100)
+    assert e.value.status == ch.CASHASH_EINVAL
+    bad = ch.cashash_default_params(top_k=0)
+    with pytest.raises(ch.CashashError):
+        ch.cashash_create(bad, s.R)
+    with pytest.raises(ch.CashashError):
+        ch.cashash_create(ch.cashash_default_params(code_bits=100), s.R)
+    ctx.close()
