@@ -244,6 +244,10 @@ def run_ours(args):
     ch._load()
 
     s, wdesc = workload(args.workload, rank)
+    if args.max_pairs and args.max_pairs < len(s.pairs):
+        # profiling case: the whole image set stays resident, fewer pairs are matched
+        s.pairs = s.pairs[:args.max_pairs]
+        wdesc += " (first %d pairs only)" % args.max_pairs
     prec = ch.CASHASH_BF16 if args.precision == "bf16" else ch.CASHASH_FP32
     sched = ch.CASHASH_SCHED_PERSISTENT if args.schedule == "persistent" else ch.CASHASH_SCHED_PER_PAIR
     p = ch.cashash_default_params(precision=prec, schedule=sched)
@@ -394,6 +398,7 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
     ap.add_argument("--schedule", default="persistent", choices=["persistent", "per_pair"])
     ap.add_argument("--ref-pairs", type=int, default=480)
+    ap.add_argument("--max-pairs", type=int, default=0, help="match only the first N pairs (profiling case)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
