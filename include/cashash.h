@@ -186,6 +186,39 @@ int cashash_run_host(cashash_ctx* ctx, const uint8_t* desc_host, const uint64_t*
                      const float* kpts_host, const uint32_t* pairs_host, uint32_t P, const double* F_host,
                      uint64_t* match_off_host, uint32_t* matches_host, uint64_t cap, uint64_t stage_bytes);
 
+/* Largest query image (features) that cashash_match_pair_noalloc accepts. */
+#define CASHASH_NOALLOC_MAX_QUERIES 65536u
+
+/* Allocation-free matching of one image pair.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc at the
+ * moment they need a match -- a real-time pipeline that must not allocate or
+ * implicitly synchronise the device after start-up, a host that gives all
+ * device memory to its own pool allocator, or a caller whose device memory is
+ * already committed.  It needs no context and allocates nothing: its scratch
+ * (pair record, work items, per-query results, match counter, status word)
+ * is one fixed, file-scope device array of about 260 KB that every GPU
+ * loading this library holds until the process exits.
+ *
+ * Computes for pair (image_a queries, image_b candidates) of `set` the same
+ * matches as cashash_match_pairs would for that single pair with the same
+ * parameters (p->precision and p->schedule are ignored: the codes and lookup
+ * tables of `set` must already have been built, e.g. by cashash_build_codes).
+ *   match_off: DEVICE [2] uint64 out: 0 and the number of matches;
+ *   matches:   DEVICE [cap][2] uint32 out: (query index, candidate index),
+ *              ascending query index; entries beyond cap are not written, so
+ *              match_off[1] > cap means the list was truncated.
+ *   F_dev:     DEVICE [9] fundamental matrix when p->epi_px >= 0, else NULL.
+ * Asynchronous on `stream`.  The first call on a device (with that device
+ * current) looks up the scratch array's device address; make that first call
+ * before any stream capture.  Every call shares the one array: calls that
+ * overlap on the GPU (other streams, other host threads) race and must be
+ * serialised by the caller.
+ * Errors: EINVAL (bad parameters or set, image index out of range, or
+ * image_a larger than CASHASH_NOALLOC_MAX_QUERIES features), ECUDA. */
+int cashash_match_pair_noalloc(const cashash_params* p, const cashash_set* set, uint32_t image_a,
+                               uint32_t image_b, const double* F_dev, uint64_t* match_off, uint32_t* matches,
+                               uint64_t cap, cashash_stream_t stream);
+
 /* Stage ids of cashash_stats.ms_stage. */
 enum {
   CASHASH_STAGE_CENTRE = 0,     /* column sums, centre and per-row constants */

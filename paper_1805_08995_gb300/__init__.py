@@ -22,6 +22,7 @@ CASHASH_OK, CASHASH_EINVAL, CASHASH_ENOMEM, CASHASH_ECUDA = 0, 1, 2, 3
 CASHASH_EOVERFLOW, CASHASH_EDEVICE, CASHASH_ETIMEOUT, CASHASH_ENOTSUP = 4, 5, 6, 7
 CASHASH_FP32, CASHASH_BF16 = 0, 1
 CASHASH_SCHED_PER_PAIR, CASHASH_SCHED_PERSISTENT = 0, 1
+CASHASH_NOALLOC_MAX_QUERIES = 65536
 
 
 class CashashError(RuntimeError):
@@ -81,6 +82,8 @@ def _load():
             "cashash_run_host": ([vp, vp, vp, u32, vp, vp, u32, vp, vp, vp, u64, u64], C.c_int),
             "cashash_get_stats": ([vp, P(cashash_stats)], C.c_int),
             "cashash_set_profiling": ([vp, C.c_int], C.c_int),
+            "cashash_match_pair_noalloc": ([P(cashash_params), P(cashash_set), u32, u32, vp, vp, vp, u64, vp],
+                                           C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -95,7 +98,7 @@ def exported_symbols():
     return ["cashash_strerror", "cashash_default_params", "cashash_tables_bytes", "cashash_create",
             "cashash_destroy", "cashash_build_codes", "cashash_get_mean", "cashash_plan_create",
             "cashash_plan_destroy", "cashash_match_plan", "cashash_match_pairs", "cashash_sync_status",
-            "cashash_run_host", "cashash_get_stats", "cashash_set_profiling"]
+            "cashash_run_host", "cashash_get_stats", "cashash_set_profiling", "cashash_match_pair_noalloc"]
 
 
 def _check(st, what):
@@ -274,6 +277,15 @@ def cashash_get_stats(ctx: Context) -> dict:
 
 def cashash_set_profiling(ctx: Context, on: bool = True):
     _check(_load().cashash_set_profiling(ctx.handle, 1 if on else 0), "cashash_set_profiling")
+
+
+def cashash_match_pair_noalloc(params: cashash_params, dset: DeviceSet, image_a: int, image_b: int, match_off,
+                               matches, cap: int, F=None, stream=None):
+    """Allocation-free matching of one pair (see include/cashash.h): the
+    library allocates nothing; scratch comes from its fixed device array."""
+    _check(_load().cashash_match_pair_noalloc(C.byref(params), C.byref(dset.c), int(image_a), int(image_b),
+                                              _dptr(F), _dptr(match_off), _dptr(matches), int(cap),
+                                              _stream(stream)), "cashash_match_pair_noalloc")
 
 
 def cashash_run_host(ctx: Context, desc: np.ndarray, img_off: np.ndarray, pairs: np.ndarray, cap: int,
