@@ -166,6 +166,14 @@ void cashash_plan_destroy(cashash_plan* plan);
 int cashash_match_plan(cashash_ctx* ctx, cashash_plan* plan, const double* F_dev, uint64_t* match_off,
                        uint32_t* matches, uint64_t cap, cashash_stream_t stream);
 
+/* Performance hint for the batched (persistent) schedule: the Hamming
+ * distance below which candidates are kept for ranking when matching starts.
+ * The kernel then adapts it to the largest k-th ranked distance it observes
+ * (unless `fixed` is non-zero).  Results never depend on it: a query for
+ * which the hint turns away candidates it needed is re-matched exactly.
+ * hamming >= code_bits disables the speculation.  Errors: EINVAL, ECUDA. */
+int cashash_plan_set_threshold_hint(cashash_plan* plan, uint32_t hamming, int fixed);
+
 /* Convenience: plan + match + plan release in one call (same outputs). */
 int cashash_match_pairs(cashash_ctx* ctx, const cashash_set* set, const uint32_t* pairs_host, uint32_t P,
                         const double* F_dev, uint64_t* match_off, uint32_t* matches, uint64_t cap,

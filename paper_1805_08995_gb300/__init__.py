@@ -82,6 +82,7 @@ def _load():
             "cashash_run_host": ([vp, vp, vp, u32, vp, vp, u32, vp, vp, vp, u64, u64], C.c_int),
             "cashash_get_stats": ([vp, P(cashash_stats)], C.c_int),
             "cashash_set_profiling": ([vp, C.c_int], C.c_int),
+            "cashash_plan_set_threshold_hint": ([vp, u32, C.c_int], C.c_int),
             "cashash_match_pair_noalloc": ([P(cashash_params), P(cashash_set), u32, u32, vp, vp, vp, u64, vp],
                                            C.c_int),
         }
@@ -98,7 +99,8 @@ def exported_symbols():
     return ["cashash_strerror", "cashash_default_params", "cashash_tables_bytes", "cashash_create",
             "cashash_destroy", "cashash_build_codes", "cashash_get_mean", "cashash_plan_create",
             "cashash_plan_destroy", "cashash_match_plan", "cashash_match_pairs", "cashash_sync_status",
-            "cashash_run_host", "cashash_get_stats", "cashash_set_profiling", "cashash_match_pair_noalloc"]
+            "cashash_run_host", "cashash_get_stats", "cashash_set_profiling", "cashash_match_pair_noalloc",
+            "cashash_plan_set_threshold_hint"]
 
 
 def _check(st, what):
@@ -245,6 +247,11 @@ class Plan:
 
 def cashash_plan_create(ctx: Context, dset: DeviceSet, pairs) -> Plan:
     return Plan(ctx, dset, pairs)
+
+
+def cashash_plan_set_threshold_hint(plan: Plan, hamming: int, fixed: bool = False):
+    _check(_load().cashash_plan_set_threshold_hint(plan.handle, int(hamming), 1 if fixed else 0),
+           "cashash_plan_set_threshold_hint")
 
 
 def cashash_plan_destroy(plan: Plan):

@@ -80,7 +80,12 @@ struct cashash_plan {
   uint32_t* d_res = nullptr;
   uint64_t n_res = 0;
   unsigned long long* d_pair_cnt = nullptr;
-  unsigned int* d_item_ctr = nullptr;
+  unsigned int* d_item_ctr = nullptr;  // [P + 1]: per-pair launches, then the persistent launch
+  uint32_t* d_queue = nullptr;         // survivor queues of the persistent (speculative) kernel
+  uint32_t* d_tau = nullptr;           // per pair: learned Hamming threshold + 1 (0 = none yet)
+  uint32_t grid = 0;                   // persistent grid (resident CTAs)
+  uint32_t tau_fixed = 0;              // keep the Hamming threshold hint fixed
+  uint32_t occ_grid = 0;               // per-pair launches: resident CTAs
   std::vector<uint32_t> first, count;  // per-pair item ranges (per-pair schedule)
   const uint8_t* desc = nullptr;
   const uint32_t* codes = nullptr;
@@ -412,6 +417,8 @@ void cashash_plan_destroy(cashash_plan* pl) {
   dfree(pl->d_res);
   dfree(pl->d_pair_cnt);
   dfree(pl->d_item_ctr);
+  dfree(pl->d_queue);
+  dfree(pl->d_tau);
   delete pl;
 }
 
@@ -472,6 +479,12 @@ int cashash_plan_create(cashash_ctx* c, const cashash_set* s, const uint32_t* pa
     pl->count[i] = (uint32_t)items.size() - pl->first[i];
   }
   pl->n_items = (uint32_t)items.size();
+  const bool epi = c->p.epi_px >= 0.0;
+  if (pl->persistent) {
+    pl->grid = match_grid(c->p.top_k, 1, epi, c->p.n_tables, pl->n_items);
+  } else {
+    pl->occ_grid = match_grid(c->p.top_k, 0, epi, c->p.n_tables, 0xFFFFFFFFu);
+  }
   uint64_t cap = 0;
   int st = grow(pl->d_pairs, cap, std::max<uint64_t>(P, 1));
   cap = 0;
@@ -481,7 +494,14 @@ int cashash_plan_create(cashash_ctx* c, const cashash_set* s, const uint32_t* pa
   cap = 0;
   if (st == CASHASH_OK) st = grow(pl->d_pair_cnt, cap, std::max<uint64_t>(P, 1));
   cap = 0;
-  if (st == CASHASH_OK) st = grow(pl->d_item_ctr, cap, 1);
+  if (st == CASHASH_OK) st = grow(pl->d_item_ctr, cap, (uint64_t)P + 1);
+  cap = 0;
+  if (st == CASHASH_OK) st = grow(pl->d_tau, cap, std::max<uint64_t>(P, 1));
+  if (st == CASHASH_OK) st = cuda_err(cudaMemset(pl->d_tau, 0, sizeof(uint32_t) * std::max<uint64_t>(P, 1)));
+  if (st == CASHASH_OK && pl->persistent) {
+    cap = 0;
+    st = grow(pl->d_queue, cap, std::max<uint64_t>((uint64_t)pl->grid * tile * QCAP, 1));
+  }
   if (st == CASHASH_OK && P)
     st = cuda_err(cudaMemcpy(pl->d_pairs, info.data(), sizeof(PairInfo) * P, cudaMemcpyHostToDevice));
   if (st == CASHASH_OK && !items.empty())
@@ -512,27 +532,33 @@ int cashash_match_plan(cashash_ctx* c, cashash_plan* pl, const double* F_dev, ui
   a.kpts = pl->kpts;
   a.F = c->p.epi_px >= 0.0 ? F_dev : nullptr;
   a.pairs = pl->d_pairs;
-  a.item_ctr = pl->d_item_ctr;
+  a.n_pairs = P;
   a.res = pl->d_res;
+  a.n_res = pl->n_res;
   a.pair_cnt = pl->d_pair_cnt;
   a.status = c->d_status;
+  a.queue = pl->d_queue;
+  a.tau_pair = pl->d_tau;
+  a.tau_fixed = pl->tau_fixed;
   a.kp = c->kp;
   c->ev_used[CASHASH_STAGE_MATCH] = c->ev_used[CASHASH_STAGE_COMPACT] = 0;
   {
     StageTimer tm(c, CASHASH_STAGE_MATCH, stream);
+    CK(cudaMemsetAsync(pl->d_item_ctr, 0, sizeof(unsigned int) * ((size_t)P + 1), stream));
     if (pl->persistent) {
-      CK(cudaMemsetAsync(pl->d_item_ctr, 0, sizeof(unsigned int), stream));
       a.items = pl->d_items;
       a.n_items = pl->n_items;
-      const uint32_t grid = std::min<uint32_t>(pl->n_items, (uint32_t)c->nsm);
-      CK(launch_match(a, 1, grid, stream));
-      c->n_launches += grid ? 1 : 0;
+      a.item_ctr = pl->d_item_ctr + P;
+      CK(launch_match(a, 1, pl->grid, stream));
+      CK(launch_match_fallback(a, stream));
+      c->n_launches += (pl->grid ? 1 : 0) + (pl->n_res ? 1 : 0);
     } else {
       for (uint32_t i = 0; i < P; ++i) {
         if (!pl->count[i]) continue;
         a.items = pl->d_items + pl->first[i];
         a.n_items = pl->count[i];
-        CK(launch_match(a, 0, pl->count[i], stream));
+        a.item_ctr = pl->d_item_ctr + i;
+        CK(launch_match(a, 0, std::min(pl->count[i], pl->occ_grid), stream));
         c->n_launches += 1;
       }
     }
@@ -546,6 +572,17 @@ int cashash_match_plan(cashash_ctx* c, cashash_plan* pl, const double* F_dev, ui
   c->last_stream = stream;
   c->last_pairs = P;
   c->last_items = pl->n_items;
+  return CASHASH_OK;
+}
+
+int cashash_plan_set_threshold_hint(cashash_plan* pl, uint32_t hamming, int fixed) {
+  if (!pl || !pl->ctx || !pl->d_tau) return CASHASH_EINVAL;
+  CK(cudaSetDevice(pl->ctx->device));
+  const uint32_t v = hamming >= pl->ctx->p.code_bits ? 0u : hamming + 1u;
+  std::vector<uint32_t> h(std::max<uint32_t>(pl->P, 1), v);
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemcpy(pl->d_tau, h.data(), sizeof(uint32_t) * h.size(), cudaMemcpyHostToDevice));
+  pl->tau_fixed = fixed ? 1u : 0u;
   return CASHASH_OK;
 }
 

@@ -10,9 +10,12 @@ namespace chx {
 
 constexpr int DIM = 128;
 constexpr int MAX_ROWS = 128 + CASHASH_MAX_TABLES * 8;  // projection rows: remap code + table bits
-constexpr int JC = 4096;          // features of the candidate image per lookup-table chunk
+constexpr int JC = 3968;          // features of the candidate image per lookup-table chunk
+                                  // (sized so that two 512-thread matching CTAs fit one SM)
 constexpr int OFF_STRIDE = 264;   // uint16 bucket offsets per (chunk, table): 257 used, padded to 16 B
 constexpr uint32_t NO_MATCH = 0xFFFFFFFFu;
+constexpr uint32_t PENDING = 0xFFFFFFFEu;  // query left to the exact fallback kernel
+constexpr uint32_t QCAP = 64;              // survivor-queue entries per query thread
 constexpr uint32_t KEY_INF = 0xFFFFFFFFu;
 
 // device status bits (ORed into the context's status word)
@@ -78,14 +81,26 @@ struct MatchArgs {
   const PairInfo* pairs;
   const uint2* items;        // (pair, first query) work items
   uint32_t n_items;
-  unsigned int* item_ctr;    // persistent schedule counter
-  uint32_t* res;             // per-query result (candidate index or NO_MATCH)
+  uint32_t n_pairs;
+  unsigned int* item_ctr;    // work-item counter of this launch
+  uint32_t* res;             // per-query result (candidate index, NO_MATCH or PENDING)
+  uint64_t n_res;
   unsigned long long* pair_cnt;
   uint32_t* status;
+  uint32_t* queue;           // speculative form: [grid][TPB][QCAP] survivor queues
+  uint32_t* tau_pair;        // speculative form, per pair: 0 = no guess yet, else (threshold + 1);
+                             // learned as the largest k-th Hamming distance seen, kept across launches
+  uint32_t tau_fixed;        // speculative form: do not learn (keep the values set by the host)
   KParams kp;
 };
-cudaError_t launch_match(const MatchArgs& a, int persistent, uint32_t grid_items, cudaStream_t s);
-int match_tile_size(uint32_t top_k, int persistent);
+// Matching kernel launch.  spec = 0: direct register top-k (one pair per
+// launch); spec = 1: survivor queues with a speculative threshold (batched).
+cudaError_t launch_match(const MatchArgs& a, int spec, uint32_t grid, cudaStream_t s);
+// Largest useful grid (resident CTAs) for a launch over n_items items.
+uint32_t match_grid(uint32_t top_k, int spec, bool epi, uint32_t n_tables, uint32_t n_items);
+int match_tile_size(uint32_t top_k, int spec);
+// Exact re-matching of the queries the speculative kernel left PENDING.
+cudaError_t launch_match_fallback(const MatchArgs& a, cudaStream_t s);
 cudaError_t launch_scan_counts(const unsigned long long* pair_cnt, uint32_t P, uint64_t* match_off,
                                uint64_t cap, uint32_t* status, unsigned long long* total, cudaStream_t s);
 cudaError_t launch_compact(const PairInfo* pairs, uint32_t P, const uint32_t* res, const uint64_t* match_off,

@@ -5,14 +5,30 @@
 // The candidate image is streamed through shared memory in chunks of JC
 // features: its 128-bit codes (16 B each) and the chunk's lookup tables.
 // For each table the thread walks the bucket of its query and, per
-// candidate, forms the key (Hamming << 24 | candidate index); the KC smallest
-// distinct keys are kept in registers by a branch-free insertion network that
-// also drops a key equal to one already kept (the same candidate met through
-// another table), so the candidate set is a set as Step 1 requires and ties
-// are broken by the smaller index.  Then each warp computes the exact
-// squared distances of its 32 queries' k candidates with 8 lanes per
-// 128-byte row (d = |a|^2 + |b|^2 - 2 a.b, dp4a on uint8, exact in int32),
-// and each thread applies Lowe's ratio test den^2 d1 < num^2 d2.
+// candidate, forms the key (Hamming << 24 | candidate index).  The k
+// smallest distinct keys are the ranked candidates of Step 3: distinct
+// because a point met through several tables is one candidate (Step 1 is a
+// set), and ordered by (Hamming, index).
+//
+// Two forms of the selection:
+//  * direct (one pair per launch): every key below the current k-th key goes
+//    through a branch-free insertion network in registers that also drops a
+//    key equal to one already kept;
+//  * speculative (batched): the hot loop only appends keys below a threshold
+//    to the thread's survivor queue in global memory (L2-resident).  The
+//    threshold is learned per pair: the largest k-th Hamming distance any
+//    tile of the pair has produced (kept across launches, so repeated
+//    matching of a pair list speculates from its second launch on); a
+//    typical query then keeps about a tenth of its candidates, and the
+//    insertion network runs once per query over the survivors.  Exactness never depends on the guess: a
+//    query whose survivors hold fewer than k distinct keys while some
+//    candidate was turned away is marked PENDING and re-matched exactly by
+//    k_match_fallback.  A full queue is folded into the registers at once and
+//    the threshold tightened to the exact k-th key.
+// Then each warp computes the exact squared distances of its 32 queries' k
+// candidates with 8 lanes per 128-byte row (d = |a|^2 + |b|^2 - 2 a.b, dp4a
+// on uint8, exact in int32), and each thread applies Lowe's ratio test
+// den^2 d1 < num^2 d2 (Step 4).
 #include "internal.h"
 
 namespace chx {
@@ -28,39 +44,77 @@ __device__ __forceinline__ void topk_insert(uint32_t (&top)[KC], uint32_t k) {
   }
 }
 
+template <int KC>
+__device__ __forceinline__ uint32_t topk_kth(const uint32_t (&top)[KC], uint32_t K) {
+  uint32_t v = KEY_INF;
+#pragma unroll
+  for (int s = 0; s < KC; ++s)
+    if ((uint32_t)s + 1 == K) v = top[s];
+  return v;
+}
+
 __host__ __device__ inline size_t match_smem_bytes(uint32_t T, bool epi, int KC, int TPB) {
   size_t scan = (size_t)JC * 16 + (size_t)T * (OFF_STRIDE + JC) * 2 + (epi ? (size_t)JC * 8 : 0);
   size_t fin = (size_t)2 * KC * TPB * 4;
   return scan > fin ? scan : fin;
 }
 
-template <int KC, int TPB, bool EPI>
-__global__ void __launch_bounds__(TPB, 1) k_match(MatchArgs a, int persistent) {
+// Sec. 6.2: the epipolar line of the query, l = F p_q, and d^2 (a^2 + b^2).
+__device__ __forceinline__ void epi_line(const double* F, float2 pq, double dd, double& la, double& lb, double& lc,
+                                         double& rhs) {
+  const double x = (double)pq.x, y = (double)pq.y;
+  la = __dadd_rn(__dadd_rn(__dmul_rn(F[0], x), __dmul_rn(F[1], y)), F[2]);
+  lb = __dadd_rn(__dadd_rn(__dmul_rn(F[3], x), __dmul_rn(F[4], y)), F[5]);
+  lc = __dadd_rn(__dadd_rn(__dmul_rn(F[6], x), __dmul_rn(F[7], y)), F[8]);
+  rhs = __dmul_rn(dd, __dadd_rn(__dmul_rn(la, la), __dmul_rn(lb, lb)));
+}
+
+// Eq. 1-2, squared: keep p' iff (a x' + b y' + c)^2 <= d^2 (a^2 + b^2).
+__device__ __forceinline__ bool epi_keep(double la, double lb, double lc, double rhs, float2 pc) {
+  const double num = __dadd_rn(__dadd_rn(__dmul_rn(la, (double)pc.x), __dmul_rn(lb, (double)pc.y)), lc);
+  return __dmul_rn(num, num) <= rhs;
+}
+
+__device__ __forceinline__ uint32_t hamming128(uint4 a, uint4 b) {
+  return __popc(a.x ^ b.x) + __popc(a.y ^ b.y) + __popc(a.z ^ b.z) + __popc(a.w ^ b.w);
+}
+
+template <int KC, int TPB, bool EPI, bool SPEC>
+__global__ void __launch_bounds__(TPB, (TPB <= 512 ? 2 : 1)) k_match(MatchArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
-  __shared__ uint32_t s_item;
+  __shared__ uint32_t s_item, s_tau, s_tau_next;
+  __shared__ PairInfo s_P;
   const KParams kp = a.kp;
   const uint32_t T = kp.n_tables;
+  const uint32_t K = kp.top_k;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   uint4* codes_s = reinterpret_cast<uint4*>(smem);
   uint16_t* tab_s = reinterpret_cast<uint16_t*>(smem + (size_t)JC * 16);
   float2* kp_s = reinterpret_cast<float2*>(smem + (size_t)JC * 16 + (size_t)T * (OFF_STRIDE + JC) * 2);
-  constexpr bool epi = EPI;
   const double dd = kp.epi_px * kp.epi_px;
+  // Sec. 5: candidates farther than tau are not candidates at all
+  const uint32_t thr_user = kp.tau < kp.code_bits ? ((kp.tau + 1u) << 24) : KEY_INF;
+  const bool filtered = EPI || thr_user != KEY_INF;
+  uint32_t* qreg = nullptr;
+  if (SPEC) qreg = a.queue + ((size_t)blockIdx.x * TPB + tid) * QCAP;
 
-  for (uint32_t round = 0;; ++round) {
-    uint32_t it;
-    if (persistent) {
-      __syncthreads();
-      if (tid == 0) s_item = atomicAdd(a.item_ctr, 1u);
-      __syncthreads();
-      it = s_item;
-    } else {
-      if (round > 0) break;
-      it = blockIdx.x;
+  for (;;) {
+    __syncthreads();
+    if (tid == 0) {
+      const uint32_t it0 = atomicAdd(a.item_ctr, 1u);
+      s_item = it0;
+      if (it0 < a.n_items) {
+        const uint2 item0 = a.items[it0];
+        s_P = a.pairs[item0.x];
+        if (SPEC) s_tau = *reinterpret_cast<volatile uint32_t*>(a.tau_pair + item0.x);
+      }
+      if (SPEC) s_tau_next = 0;
     }
+    __syncthreads();
+    const uint32_t it = s_item;
     if (it >= a.n_items) break;
     const uint2 item = a.items[it];
-    const PairInfo P = a.pairs[item.x];
+    const PairInfo P = s_P;
     const uint32_t q = item.y + tid;
     const bool valid = q < P.nA;
     uint4 qc = make_uint4(0u, 0u, 0u, 0u);
@@ -69,20 +123,18 @@ __global__ void __launch_bounds__(TPB, 1) k_match(MatchArgs a, int persistent) {
     if (valid) {
       qc = __ldg(reinterpret_cast<const uint4*>(a.codes) + P.a0 + q);
       qb = __ldg(reinterpret_cast<const uint2*>(a.buckets) + P.a0 + q);
-      if (epi) {
-        // Sec. 6.2: epipolar line l_q = F p_q of the query in the candidate image
-        const double* F = a.F + 9 * (size_t)item.x;
-        const float2 pq = __ldg(reinterpret_cast<const float2*>(a.kpts) + P.a0 + q);
-        const double x = (double)pq.x, y = (double)pq.y;
-        la = __dadd_rn(__dadd_rn(__dmul_rn(F[0], x), __dmul_rn(F[1], y)), F[2]);
-        lb = __dadd_rn(__dadd_rn(__dmul_rn(F[3], x), __dmul_rn(F[4], y)), F[5]);
-        lc = __dadd_rn(__dadd_rn(__dmul_rn(F[6], x), __dmul_rn(F[7], y)), F[8]);
-        rhs = __dmul_rn(dd, __dadd_rn(__dmul_rn(la, la), __dmul_rn(lb, lb)));
-      }
+      if (EPI) epi_line(a.F + 9 * (size_t)item.x, __ldg(reinterpret_cast<const float2*>(a.kpts) + P.a0 + q), dd, la, lb,
+                        lc, rhs);
     }
     uint32_t top[KC];
 #pragma unroll
     for (int s = 0; s < KC; ++s) top[s] = KEY_INF;
+    uint32_t thr = thr_user;
+    uint32_t cnt = 0, nflushed = 0, nlook = 0;
+    if (SPEC) {
+      const uint32_t ts = s_tau;  // 0: no guess yet; else threshold + 1
+      if (ts != 0 && ts <= kp.code_bits) thr = min(thr, ts << 24);
+    }
 
     const uint32_t nch = (P.nB + JC - 1) / JC;
     for (uint32_t c = 0; c < nch; ++c) {
@@ -101,7 +153,7 @@ __global__ void __launch_bounds__(TPB, 1) k_match(MatchArgs a, int persistent) {
           const uint32_t o = noff + t * (JC / 8) + r;
           st[o] = __ldg(gt + o);
         }
-        if (epi) {
+        if (EPI) {
           const float2* gk = reinterpret_cast<const float2*>(a.kpts) + P.b0 + (uint64_t)c * JC;
           for (uint32_t i = tid; i < len; i += TPB) kp_s[i] = __ldg(gk + i);
         }
@@ -115,23 +167,47 @@ __global__ void __launch_bounds__(TPB, 1) k_match(MatchArgs a, int persistent) {
           const uint32_t v = (t < 4 ? (qb.x >> (8 * t)) : (qb.y >> (8 * (t - 4)))) & 0xFFu;
           const uint32_t s0 = tab_s[t * OFF_STRIDE + v], s1 = tab_s[t * OFF_STRIDE + v + 1];
           const uint16_t* il = il0 + t * JC;
+          if (SPEC) nlook += s1 - s0;
           for (uint32_t pos = s0; pos < s1; ++pos) {
             const uint32_t jl = il[pos];
-            const uint4 cc = codes_s[jl];
             // Step 2: Hamming distance of the n-bit remapping codes
-            const uint32_t h = __popc(cc.x ^ qc.x) + __popc(cc.y ^ qc.y) + __popc(cc.z ^ qc.z) + __popc(cc.w ^ qc.w);
+            const uint32_t h = hamming128(codes_s[jl], qc);
             uint32_t key = (h << 24) | (cb + jl);
-            if (h > kp.tau) key = KEY_INF;  // Sec. 5
-            if (epi && key != KEY_INF) {    // Sec. 6.2 Eq. 1-2, squared
-              const float2 pc = kp_s[jl];
-              const double num = __dadd_rn(__dadd_rn(__dmul_rn(la, (double)pc.x), __dmul_rn(lb, (double)pc.y)), lc);
-              if (!(__dmul_rn(num, num) <= rhs)) key = KEY_INF;
+            if (key >= thr_user) key = KEY_INF;                                 // Sec. 5
+            if (EPI && key != KEY_INF && !epi_keep(la, lb, lc, rhs, kp_s[jl])) key = KEY_INF;  // Sec. 6.2
+            if (SPEC) {
+              if (filtered && key == KEY_INF) --nlook;
+              if (key < thr) {
+                qreg[cnt] = key;
+                if (++cnt == QCAP) {  // fold a full queue into the registers, tighten the threshold
+                  for (uint32_t e = 0; e < QCAP; ++e) {
+                    const uint32_t k2 = qreg[e];
+                    if (k2 < top[KC - 1]) topk_insert<KC>(top, k2);
+                  }
+                  nflushed += QCAP;
+                  cnt = 0;
+                  thr = min(thr, top[KC - 1]);
+                }
+              }
+            } else {
+              // Step 3: keep the KC smallest distinct keys
+              if (key < top[KC - 1]) topk_insert<KC>(top, key);
             }
-            // Step 3: keep the KC smallest distinct keys
-            if (key < top[KC - 1]) topk_insert<KC>(top, key);
           }
         }
       }
+    }
+
+    bool pending = false;
+    if (SPEC && valid) {
+      for (uint32_t e = 0; e < cnt; ++e) {
+        const uint32_t k2 = qreg[e];
+        if (k2 < top[KC - 1]) topk_insert<KC>(top, k2);
+      }
+      const uint32_t kth = topk_kth<KC>(top, K);
+      // fewer than k distinct survivors although a candidate was turned away
+      pending = kth == KEY_INF && nlook > nflushed + cnt;
+      if (kth != KEY_INF) atomicMax(&s_tau_next, (kth >> 24) + 1u);
     }
 
     // Step 4: exact squared distances of the k ranked candidates
@@ -139,31 +215,46 @@ __global__ void __launch_bounds__(TPB, 1) k_match(MatchArgs a, int persistent) {
     uint32_t* key_s = reinterpret_cast<uint32_t*>(smem);
     uint32_t* dist_s = key_s + KC * TPB;
 #pragma unroll
-    for (int s = 0; s < KC; ++s) key_s[s * TPB + tid] = valid ? top[s] : KEY_INF;
+    for (int s = 0; s < KC; ++s) key_s[s * TPB + tid] = (valid && !pending) ? top[s] : KEY_INF;
     __syncwarp();
-    const uint32_t K = kp.top_k;
     const uint32_t wbase = warp * 32;
     const int grp = lane >> 3, sub = lane & 7;
-    for (uint32_t t0 = 0; t0 < 32 * K; t0 += 4) {
-      const uint32_t task = t0 + grp;
-      const uint32_t qq = task & 31, s = task >> 5;
-      const uint32_t key = (s < K) ? key_s[s * TPB + wbase + qq] : KEY_INF;
-      uint32_t dot = 0;
-      uint64_t fa = 0, fb = 0;
-      if (key != KEY_INF) {
-        fa = P.a0 + item.y + wbase + qq;
-        fb = P.b0 + (key & 0xFFFFFFu);
-        const uint4 av = __ldg(reinterpret_cast<const uint4*>(a.desc + fa * DIM) + sub);
-        const uint4 bv = __ldg(reinterpret_cast<const uint4*>(a.desc + fb * DIM) + sub);
-        dot = __dp4a(av.x, bv.x, dot);
-        dot = __dp4a(av.y, bv.y, dot);
-        dot = __dp4a(av.z, bv.z, dot);
-        dot = __dp4a(av.w, bv.w, dot);
+    // 8 lanes per 128-byte row; each group of 8 lanes takes one query and
+    // issues the loads of DB rows at once (independent, so their latencies overlap)
+    constexpr int DB = 5;
+    for (uint32_t qq0 = 0; qq0 < 32; qq0 += 4) {
+      const uint32_t qq = qq0 + grp;
+      const uint32_t qi = wbase + qq;
+      const bool has = key_s[qi] != KEY_INF;  // slot 0 filled <=> the query has candidates
+      const uint64_t fa = P.a0 + item.y + qi;
+      uint4 av = make_uint4(0u, 0u, 0u, 0u);
+      if (has) av = __ldg(reinterpret_cast<const uint4*>(a.desc + fa * DIM) + sub);
+      for (uint32_t s0 = 0; s0 < K; s0 += DB) {
+        uint32_t key[DB];
+        uint4 bv[DB];
+#pragma unroll
+        for (int d = 0; d < DB; ++d) {
+          key[d] = (has && s0 + d < K) ? key_s[(s0 + d) * TPB + qi] : KEY_INF;
+          bv[d] = make_uint4(0u, 0u, 0u, 0u);
+          if (key[d] != KEY_INF)
+            bv[d] = __ldg(reinterpret_cast<const uint4*>(a.desc + (P.b0 + (key[d] & 0xFFFFFFu)) * DIM) + sub);
+        }
+#pragma unroll
+        for (int d = 0; d < DB; ++d) {
+          uint32_t dot = 0;
+          dot = __dp4a(av.x, bv[d].x, dot);
+          dot = __dp4a(av.y, bv[d].y, dot);
+          dot = __dp4a(av.z, bv[d].z, dot);
+          dot = __dp4a(av.w, bv[d].w, dot);
+          dot += __shfl_xor_sync(0xFFFFFFFFu, dot, 1);
+          dot += __shfl_xor_sync(0xFFFFFFFFu, dot, 2);
+          dot += __shfl_xor_sync(0xFFFFFFFFu, dot, 4);
+          if (sub == 0 && key[d] != KEY_INF) {
+            const uint64_t fb = P.b0 + (key[d] & 0xFFFFFFu);
+            dist_s[(s0 + d) * TPB + qi] = __ldg(a.sqnorm + fa) + __ldg(a.sqnorm + fb) - 2u * dot;
+          }
+        }
       }
-      dot += __shfl_xor_sync(0xFFFFFFFFu, dot, 1);
-      dot += __shfl_xor_sync(0xFFFFFFFFu, dot, 2);
-      dot += __shfl_xor_sync(0xFFFFFFFFu, dot, 4);
-      if (sub == 0 && key != KEY_INF) dist_s[s * TPB + wbase + qq] = __ldg(a.sqnorm + fa) + __ldg(a.sqnorm + fb) - 2u * dot;
     }
     __syncwarp();
     bool matched = false;
@@ -185,17 +276,109 @@ __global__ void __launch_bounds__(TPB, 1) k_match(MatchArgs a, int persistent) {
       }
       // Lowe's ratio test on distances, strict: sqrt(d1) < (num/den) sqrt(d2)
       matched = nv >= 2 && (uint64_t)kp.ratio_den * kp.ratio_den * d1 < (uint64_t)kp.ratio_num * kp.ratio_num * d2;
-      a.res[P.qbase + q] = matched ? j1 : NO_MATCH;
+      a.res[P.qbase + q] = pending ? PENDING : (matched ? j1 : NO_MATCH);
     }
     const uint32_t bal = __ballot_sync(0xFFFFFFFFu, matched);
     if (lane == 0 && bal) atomicAdd(a.pair_cnt + item.x, (unsigned long long)__popc(bal));
+    if (SPEC) {
+      __syncthreads();
+      if (tid == 0 && s_tau_next && !a.tau_fixed) atomicMax(a.tau_pair + item.x, s_tau_next);
+    }
   }
 }
 
-template <int KC, int TPB, bool EPI>
-static cudaError_t launch_epi(const MatchArgs& a, int persistent, uint32_t grid, cudaStream_t s) {
+// ---------------------------------------------------------------------------
+// Exact fallback for PENDING queries: one thread per query, reading the
+// lookup tables and codes from global memory, direct register top-k.
+// ---------------------------------------------------------------------------
+template <int KC, bool EPI>
+__global__ void __launch_bounds__(128) k_match_fallback(MatchArgs a) {
+  const KParams kp = a.kp;
+  const uint32_t T = kp.n_tables, K = kp.top_k;
+  const uint32_t thr_user = kp.tau < kp.code_bits ? ((kp.tau + 1u) << 24) : KEY_INF;
+  const double dd = kp.epi_px * kp.epi_px;
+  for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < a.n_res;
+       g += (uint64_t)gridDim.x * blockDim.x) {
+    if (a.res[g] != PENDING) continue;
+    uint32_t lo = 0, hi = a.n_pairs - 1;  // last pair with qbase <= g
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi + 1) >> 1;
+      if (a.pairs[mid].qbase <= g) lo = mid;
+      else hi = mid - 1;
+    }
+    const PairInfo P = a.pairs[lo];
+    const uint32_t q = (uint32_t)(g - P.qbase);
+    const uint4 qc = __ldg(reinterpret_cast<const uint4*>(a.codes) + P.a0 + q);
+    const uint2 qb = __ldg(reinterpret_cast<const uint2*>(a.buckets) + P.a0 + q);
+    double la = 0.0, lb = 0.0, lc = 0.0, rhs = 0.0;
+    if (EPI) epi_line(a.F + 9 * (size_t)lo, __ldg(reinterpret_cast<const float2*>(a.kpts) + P.a0 + q), dd, la, lb, lc,
+                      rhs);
+    uint32_t top[KC];
+#pragma unroll
+    for (int s = 0; s < KC; ++s) top[s] = KEY_INF;
+    const uint32_t nch = (P.nB + JC - 1) / JC;
+    for (uint32_t c = 0; c < nch; ++c) {
+      const uint16_t* blk = reinterpret_cast<const uint16_t*>(a.tables + (uint64_t)(P.bchunk0 + c) * chunk_bytes(T));
+      const uint4* gc = reinterpret_cast<const uint4*>(a.codes) + P.b0 + (uint64_t)c * JC;
+      for (uint32_t t = 0; t < T; ++t) {
+        const uint32_t v = (t < 4 ? (qb.x >> (8 * t)) : (qb.y >> (8 * (t - 4)))) & 0xFFu;
+        const uint32_t s0 = blk[t * OFF_STRIDE + v], s1 = blk[t * OFF_STRIDE + v + 1];
+        const uint16_t* il = blk + T * OFF_STRIDE + t * JC;
+        for (uint32_t pos = s0; pos < s1; ++pos) {
+          const uint32_t jl = il[pos];
+          const uint32_t h = hamming128(__ldg(gc + jl), qc);
+          uint32_t key = (h << 24) | (c * JC + jl);
+          if (key >= thr_user) continue;
+          if (EPI && !epi_keep(la, lb, lc, rhs,
+                               __ldg(reinterpret_cast<const float2*>(a.kpts) + P.b0 + (uint64_t)c * JC + jl)))
+            continue;
+          if (key < top[KC - 1]) topk_insert<KC>(top, key);
+        }
+      }
+    }
+    const uint64_t fa = P.a0 + q;
+    const uint4* arow = reinterpret_cast<const uint4*>(a.desc + fa * DIM);
+    uint32_t nv = 0, d1 = 0xFFFFFFFFu, d2 = 0xFFFFFFFFu, j1 = NO_MATCH;
+#pragma unroll
+    for (int s = 0; s < KC; ++s) {
+      const uint32_t key = top[s];
+      if ((uint32_t)s >= K || key == KEY_INF) continue;
+      const uint32_t j = key & 0xFFFFFFu;
+      const uint64_t fb = P.b0 + j;
+      const uint4* brow = reinterpret_cast<const uint4*>(a.desc + fb * DIM);
+      uint32_t dot = 0;
+      for (int w = 0; w < 8; ++w) {
+        const uint4 av = __ldg(arow + w), bv = __ldg(brow + w);
+        dot = __dp4a(av.x, bv.x, dot);
+        dot = __dp4a(av.y, bv.y, dot);
+        dot = __dp4a(av.z, bv.z, dot);
+        dot = __dp4a(av.w, bv.w, dot);
+      }
+      const uint32_t d = __ldg(a.sqnorm + fa) + __ldg(a.sqnorm + fb) - 2u * dot;
+      ++nv;
+      if (d < d1 || (d == d1 && j < j1)) {
+        d2 = d1;
+        d1 = d;
+        j1 = j;
+      } else if (d < d2) {
+        d2 = d;
+      }
+    }
+    const bool matched =
+        nv >= 2 && (uint64_t)kp.ratio_den * kp.ratio_den * d1 < (uint64_t)kp.ratio_num * kp.ratio_num * d2;
+    a.res[g] = matched ? j1 : NO_MATCH;
+    if (matched) atomicAdd(a.pair_cnt + lo, 1ull);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launch plumbing
+// ---------------------------------------------------------------------------
+namespace {
+
+template <int KC, int TPB, bool EPI, bool SPEC>
+cudaError_t run_match(const MatchArgs* a, uint32_t grid, cudaStream_t s, uint32_t* occ) {
   static int attr_dev = -1;  // the shared-memory opt-in is set once per device
-  const size_t smem = match_smem_bytes(a.kp.n_tables, EPI, KC, TPB);
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
@@ -203,42 +386,89 @@ static cudaError_t launch_epi(const MatchArgs& a, int persistent, uint32_t grid,
     int optin = 0;
     e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_match<KC, TPB, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - 1024);
+    e = cudaFuncSetAttribute(k_match<KC, TPB, EPI, SPEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - 1024);
     if (e != cudaSuccess) return e;
     attr_dev = dev;
   }
-  k_match<KC, TPB, EPI><<<grid, TPB, smem, s>>>(a, persistent);
+  const uint32_t T = a ? a->kp.n_tables : (occ ? *occ : 6u);
+  const size_t smem = match_smem_bytes(T, EPI, KC, TPB);
+  if (occ) {
+    int nb = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_match<KC, TPB, EPI, SPEC>, TPB, smem);
+    *occ = (uint32_t)(nb > 0 ? nb : 1);
+    return e;
+  }
+  k_match<KC, TPB, EPI, SPEC><<<grid, TPB, smem, s>>>(*a);
   return cudaGetLastError();
 }
 
 template <int KC, int TPB>
-static cudaError_t launch_one(const MatchArgs& a, int persistent, uint32_t grid, cudaStream_t s) {
-  if (a.kp.epi_px >= 0.0) return launch_epi<KC, TPB, true>(a, persistent, grid, s);
-  return launch_epi<KC, TPB, false>(a, persistent, grid, s);
+cudaError_t run_kc(const MatchArgs* a, int spec, bool epi, uint32_t grid, cudaStream_t s, uint32_t* occ) {
+  if (spec) return epi ? run_match<KC, TPB, true, true>(a, grid, s, occ) : run_match<KC, TPB, false, true>(a, grid, s, occ);
+  return epi ? run_match<KC, TPB, true, false>(a, grid, s, occ) : run_match<KC, TPB, false, false>(a, grid, s, occ);
 }
 
-int match_tile_size(uint32_t top_k, int persistent) {
-  if (!persistent) return 256;
-  if (top_k <= 10) return 1024;
-  if (top_k <= 16) return 512;
-  return 256;
-}
-
-cudaError_t launch_match(const MatchArgs& a, int persistent, uint32_t grid, cudaStream_t s) {
-  if (grid == 0 || a.n_items == 0) return cudaSuccess;
-  const uint32_t k = a.kp.top_k;
-  if (!persistent) {
-    if (k <= 4) return launch_one<4, 256>(a, 0, grid, s);
-    if (k <= 8) return launch_one<8, 256>(a, 0, grid, s);
-    if (k <= 10) return launch_one<10, 256>(a, 0, grid, s);
-    if (k <= 16) return launch_one<16, 256>(a, 0, grid, s);
-    return launch_one<32, 256>(a, 0, grid, s);
+cudaError_t dispatch(uint32_t k, const MatchArgs* a, int spec, bool epi, uint32_t grid, cudaStream_t s, uint32_t* occ) {
+  if (!spec) {
+    if (k <= 4) return run_kc<4, 256>(a, 0, epi, grid, s, occ);
+    if (k <= 8) return run_kc<8, 256>(a, 0, epi, grid, s, occ);
+    if (k <= 10) return run_kc<10, 256>(a, 0, epi, grid, s, occ);
+    if (k <= 16) return run_kc<16, 256>(a, 0, epi, grid, s, occ);
+    return run_kc<32, 256>(a, 0, epi, grid, s, occ);
   }
-  if (k <= 4) return launch_one<4, 1024>(a, 1, grid, s);
-  if (k <= 8) return launch_one<8, 1024>(a, 1, grid, s);
-  if (k <= 10) return launch_one<10, 1024>(a, 1, grid, s);
-  if (k <= 16) return launch_one<16, 512>(a, 1, grid, s);
-  return launch_one<32, 256>(a, 1, grid, s);
+  if (k <= 4) return run_kc<4, 512>(a, 1, epi, grid, s, occ);
+  if (k <= 8) return run_kc<8, 512>(a, 1, epi, grid, s, occ);
+  if (k <= 10) return run_kc<10, 512>(a, 1, epi, grid, s, occ);
+  if (k <= 16) return run_kc<16, 512>(a, 1, epi, grid, s, occ);
+  return run_kc<32, 256>(a, 1, epi, grid, s, occ);
+}
+
+}  // namespace
+
+int match_tile_size(uint32_t top_k, int spec) {
+  if (!spec) return 256;
+  return top_k <= 16 ? 512 : 256;
+}
+
+uint32_t match_grid(uint32_t top_k, int spec, bool epi, uint32_t n_tables, uint32_t n_items) {
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  uint32_t occ = n_tables;
+  if (dispatch(top_k, nullptr, spec, epi, 0, 0, &occ) != cudaSuccess) {
+    cudaGetLastError();
+    occ = 1;
+  }
+  const uint64_t g = (uint64_t)nsm * occ;
+  return (uint32_t)(n_items < g ? n_items : g);
+}
+
+cudaError_t launch_match(const MatchArgs& a, int spec, uint32_t grid, cudaStream_t s) {
+  if (grid == 0 || a.n_items == 0) return cudaSuccess;
+  return dispatch(a.kp.top_k, &a, spec, a.kp.epi_px >= 0.0, grid, s, nullptr);
+}
+
+cudaError_t launch_match_fallback(const MatchArgs& a, cudaStream_t s) {
+  if (a.n_res == 0 || a.n_pairs == 0) return cudaSuccess;
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const uint64_t want = (a.n_res + 127) / 128;
+  const unsigned grid = (unsigned)(want < (uint64_t)nsm * 16 ? want : (uint64_t)nsm * 16);
+  const bool epi = a.kp.epi_px >= 0.0;
+  const uint32_t k = a.kp.top_k;
+#define CHX_FB(KC)                                                              \
+  do {                                                                          \
+    if (epi) k_match_fallback<KC, true><<<grid, 128, 0, s>>>(a);               \
+    else k_match_fallback<KC, false><<<grid, 128, 0, s>>>(a);                  \
+  } while (0)
+  if (k <= 4) CHX_FB(4);
+  else if (k <= 8) CHX_FB(8);
+  else if (k <= 10) CHX_FB(10);
+  else if (k <= 16) CHX_FB(16);
+  else CHX_FB(32);
+#undef CHX_FB
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
@@ -297,7 +527,7 @@ __global__ void __launch_bounds__(256) k_compact(const PairInfo* __restrict__ pa
   for (uint32_t q0 = 0; q0 < pi.nA; q0 += 256) {
     const uint32_t q = q0 + tid;
     const uint32_t r = q < pi.nA ? res[pi.qbase + q] : NO_MATCH;
-    const bool f = r != NO_MATCH;
+    const bool f = r < PENDING;
     const uint32_t bal = __ballot_sync(0xFFFFFFFFu, f);
     if (lane == 0) wsum[w] = __popc(bal);
     __syncthreads();

@@ -135,6 +135,8 @@ extern "C" int cashash_match_pair_noalloc(const cashash_params* p, const cashash
   a.kpts = s->kpts;
   a.F = epi ? F_dev : nullptr;
   a.pairs = &sc->pair;
+  a.n_pairs = 1;
+  a.n_res = nA;
   a.items = sc->items;
   a.n_items = n_items;
   a.item_ctr = &sc->item_ctr;

@@ -198,3 +198,111 @@ def random_set(seed: int, sizes, pairs=None, copy_frac: float = 0.3) -> ImageSet
     desc = np.concatenate(imgs) if imgs else np.zeros((0, DIM), np.uint8)
     return ImageSet(desc, _offsets(sizes), np.asarray(pairs, np.uint32).reshape(-1, 2), projection_matrix(seed),
                     "random:%s" % (sizes,))
+
+
+# ---------------------------------------------------------------------------
+# Epipolar-guided workload (config 4): views of random 3-D points
+# ---------------------------------------------------------------------------
+
+def _rot(axis_angle: np.ndarray) -> np.ndarray:
+    """Rotation matrix of an axis-angle vector (Rodrigues)."""
+    th = float(np.linalg.norm(axis_angle))
+    if th < 1e-15:
+        return np.eye(3)
+    k = axis_angle / th
+    Kx = np.array([[0, -k[2], k[1]], [k[2], 0, -k[0]], [-k[1], k[0], 0]])
+    return np.eye(3) + np.sin(th) * Kx + (1 - np.cos(th)) * (Kx @ Kx)
+
+
+def epipolar_set(seed: int = 4, n_views: int = 500, n_points: int = 200_000, radius: float = 0.25,
+                 arc: float = 2 * math.pi, z_max: float = 0.34, focal: float = 1000.0, width: int = 1920,
+                 height: int = 1080, jitter_px: float = 1.0, clutter: float = 0.3, min_overlap: float = 0.2,
+                 sigma: float = 8.0, view_noise: float = 0.05, rise: float = 0.0) -> ImageSet:
+    """Pinhole views of n_points uniform points in the unit cube.
+
+    Cameras sit on a helix of the given radius around the cube centre (over
+    the angle `arc`, rising by `rise` in total), each looking along the path with a small random
+    rotation (view_noise radians per axis); a point is seen when it projects inside the image at depth
+    0.02..z_max.  Each point carries a SIFT-like template descriptor; a view's
+    key-point of it gets the template plus N(0, sigma^2) noise and its
+    projection plus N(0, jitter^2) pixels.  A fraction `clutter` of each
+    view's key-points are fresh descriptors at uniform image positions.
+    Views are paired when they share at least min_overlap of the smaller
+    visible set; F (x_cand^T F x_query = 0) is the ground truth of each pair.
+    """
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 4]))
+    X = rng.random((n_points, 3))
+    templates = sift_like(rng, n_points)
+    Kc = np.array([[focal, 0, width / 2.0], [0, focal, height / 2.0], [0, 0, 1.0]])
+    centre = np.array([0.5, 0.5, 0.5])
+    cams = []
+    for i in range(n_views):
+        th = arc * i / n_views
+        lift = rise * (i / max(1, n_views - 1) - 0.5)          # helix height
+        pos = centre + np.array([radius * np.cos(th), radius * np.sin(th), lift]) + rng.normal(0, 0.01, 3)
+        fwd = np.array([-np.sin(th), np.cos(th), 0.0])          # along the path
+        up = np.array([0.0, 0.0, 1.0])
+        right = np.cross(fwd, up)
+        # camera axes: x right, y down, z forward
+        Rw = np.stack([right, -up, fwd])
+        Rw = _rot(rng.normal(0, view_noise, 3)) @ Rw
+        t = -Rw @ pos
+        cams.append((Rw, t))
+    vis = []
+    proj = []
+    for Rw, t in cams:
+        Y = X @ Rw.T + t
+        z = Y[:, 2]
+        ok = (z > 0.02) & (z < z_max)
+        uv = np.full((n_points, 2), -1.0)
+        uv[ok] = (Y[ok, :2] / z[ok, None]) * focal + np.array([width / 2.0, height / 2.0])
+        ok &= (uv[:, 0] >= 0) & (uv[:, 0] < width) & (uv[:, 1] >= 0) & (uv[:, 1] < height)
+        vis.append(np.nonzero(ok)[0])
+        proj.append(uv)
+    # pairs by overlap of visible sets
+    import scipy.sparse as sp
+    rows = np.concatenate([np.full(len(v), i) for i, v in enumerate(vis)])
+    cols = np.concatenate(vis)
+    M = sp.csr_matrix((np.ones(len(rows), np.int32), (rows, cols)), shape=(n_views, n_points))
+    inter = (M @ M.T).tocoo()
+    nvis = np.array([len(v) for v in vis])
+    pairs = []
+    for a, b, c in zip(inter.row, inter.col, inter.data):
+        if a < b and c >= min_overlap * max(1, min(nvis[a], nvis[b])):
+            pairs.append((a, b))
+    pairs = np.array(sorted(pairs), np.uint32).reshape(-1, 2)
+    descs, kps, sizes = [], [], []
+    for i in range(n_views):
+        v = vis[i]
+        n_real = len(v)
+        n_cl = int(round(n_real * clutter / (1.0 - clutter)))
+        d_real = noisy_copy(rng, templates[v], sigma)
+        k_real = proj[i][v] + rng.normal(0, jitter_px, (n_real, 2))
+        d_cl = sift_like(rng, n_cl)
+        k_cl = np.stack([rng.uniform(0, width, n_cl), rng.uniform(0, height, n_cl)], axis=1)
+        d = np.concatenate([d_real, d_cl])
+        k = np.concatenate([k_real, k_cl])
+        perm = rng.permutation(d.shape[0])
+        descs.append(d[perm])
+        kps.append(k[perm].astype(np.float32))
+        sizes.append(d.shape[0])
+    Kinv = np.linalg.inv(Kc)
+    F = np.zeros((len(pairs), 9))
+    for n, (a, b) in enumerate(pairs):
+        Ra, ta = cams[a]
+        Rb, tb = cams[b]
+        Rr = Rb @ Ra.T
+        tr = tb - Rr @ ta
+        tx = np.array([[0, -tr[2], tr[1]], [tr[2], 0, -tr[0]], [-tr[1], tr[0], 0]])
+        Fm = Kinv.T @ tx @ Rr @ Kinv
+        F[n] = (Fm / np.linalg.norm(Fm)).ravel()
+    return ImageSet(np.concatenate(descs), _offsets(sizes), pairs, projection_matrix(seed),
+                    "epipolar:%d views, %d points" % (n_views, n_points), F=F,
+                    kpts=np.concatenate(kps).astype(np.float32))
+
+
+def config4(seed: int = 4) -> ImageSet:
+    """Epipolar-guided workload: 500 views of 200,000 points on a two-turn
+    helix (about 8k key-points per view with 30 % clutter); views with >= 20 %
+    overlap are paired (about 14,600 pairs)."""
+    return epipolar_set(seed, arc=4 * math.pi, rise=0.5, z_max=0.355)

@@ -57,9 +57,9 @@ def test_strerror_and_defaults_without_device(lib):
 def test_tables_bytes_host_arithmetic(lib):
     import paper_1805_08995_gb300 as ch
     p = ch.cashash_default_params()
-    off = np.array([0, 4096, 4097, 4097, 20000], np.uint64)
-    # chunks: 1 + 1 + 0 + 4 = 6; each chunk holds 6 tables x (264 + 4096) uint16
-    assert ch.cashash_tables_bytes(p, off) == 6 * 6 * (264 + 4096) * 2
+    off = np.array([0, 3968, 3969, 3969, 20000], np.uint64)
+    # chunks of 3968 features: 1 + 1 + 0 + 5 = 7; each holds 6 tables x (264 + 3968) uint16
+    assert ch.cashash_tables_bytes(p, off) == 7 * 6 * (264 + 3968) * 2
     bad = ch.cashash_default_params(n_tables=0)
     assert ch.cashash_tables_bytes(bad, off) == 0
     assert ch.cashash_tables_bytes(p, np.array([0, 5, 3], np.uint64)) == 0

@@ -14,7 +14,7 @@ import synth
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-JC = 4096          # features per lookup-table chunk (library layout)
+JC = 3968          # features per lookup-table chunk (library layout)
 OFF_STRIDE = 264   # uint16 offsets per (chunk, table)
 
 
@@ -94,7 +94,7 @@ def check_case(ch, orc, s, pairs, **pk):
     return ds, codes, buckets, stats
 
 
-SIZES = [300, 1, 0, 2500, 5000, 4097, 4096, 33]
+SIZES = [300, 1, 0, 2500, 5000, 3969, 3968, 33, 8000]
 
 
 def _pairs(sizes, extra=()):
@@ -124,8 +124,39 @@ def test_parameter_variants(ch, orc, pk, sched):
     check_case(ch, orc, s, _pairs(sizes), schedule=sched, **pk)
 
 
+@pytest.mark.parametrize("hint,fixed", [(0, True), (30, True), (50, True), (53, True), (56, False), (0, False)])
+def test_speculative_threshold_never_changes_results(ch, orc, hint, fixed):
+    """The batched kernel's Hamming threshold is a guess; queries it starves
+    are re-matched exactly.  Forcing bad guesses (0: every query falls back;
+    near the median k-th distance: about half do) must not change a match."""
+    sizes = [2600, 4100, 0, 900, 5200]
+    s = synth.random_set(707, sizes)
+    pairs = _pairs(sizes)
+    p = ch.cashash_default_params(schedule=1)
+    ctx = ch.cashash_create(p, s.R)
+    ds = ch.DeviceSet(p, s.img_off, s.desc)
+    ch.cashash_build_codes(ctx, ds)
+    plan = ch.cashash_plan_create(ctx, ds, pairs)
+    ch.cashash_plan_set_threshold_hint(plan, hint, fixed)
+    P = len(pairs)
+    cap = int(s.sizes()[pairs[:, 0]].sum())
+    moff = torch.zeros(P + 1, dtype=torch.int64, device="cuda")
+    mt = torch.zeros((cap, 2), dtype=torch.int32, device="cuda")
+    po = orc.params()
+    mu, codes, buckets = oracle_codes(orc, s.desc, s.R, po)
+    eoff, emt = orc.match_pairs(s.desc, s.img_off, codes, buckets, pairs, po)
+    for _ in range(2):
+        ch.cashash_match_plan(ctx, plan, moff, mt, cap)
+        assert ch.cashash_sync_status(ctx) == ch.CASHASH_OK
+        off = moff.cpu().numpy().astype(np.uint64)
+        assert np.array_equal(off, eoff)
+        assert np.array_equal(mt[:int(off[-1])].cpu().numpy().view(np.uint32), emt)
+    plan.close()
+    ctx.close()
+
+
 def test_lookup_tables_are_the_bucket_sets(ch, orc):
-    sizes = [5000, 10, 0, 4096, 8193]
+    sizes = [5000, 10, 0, 3968, 7937]
     s = synth.random_set(303, sizes)
     p = ch.cashash_default_params()
     ctx = ch.cashash_create(p, s.R)
@@ -179,6 +210,18 @@ def test_identical_and_degenerate_descriptors(ch, orc):
     ds, codes, buckets, stats = check_case(ch, orc, same, same.pairs)
     assert not codes.any() and not buckets.any()
     assert stats["n_reevaluated"] == 50 * 176
+
+
+@pytest.mark.parametrize("sched", [0, 1])
+def test_epipolar_band(ch, orc, sched):
+    """Sec. 6.2: candidates outside the 4 px band around the query's
+    epipolar line are removed before ranking (small config-4 style set)."""
+    import math
+    s = synth.epipolar_set(41, n_views=7, n_points=24000, arc=2 * math.pi * 7 / 250, z_max=0.355)
+    assert len(s.pairs) >= 10 and s.kpts is not None
+    both = np.concatenate([s.pairs, s.pairs[:, ::-1]])
+    s.F = np.concatenate([s.F, s.F.reshape(-1, 3, 3).transpose(0, 2, 1).reshape(-1, 9)])
+    check_case(ch, orc, s, both, schedule=sched, epi_px=4.0)
 
 
 def test_many_pairs_medium(ch, orc):
