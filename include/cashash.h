@@ -162,6 +162,9 @@ void cashash_plan_destroy(cashash_plan* plan);
  * when epi_px >= 0, else ignored (may be NULL).  When the total exceeds cap,
  * match_off is still complete, nothing beyond cap is written and
  * cashash_sync_status() returns EOVERFLOW.  Asynchronous on `stream`.
+ * With the persistent schedule the launch sequence is captured once as a
+ * CUDA graph (per set of output pointers, F and profiling setting) and
+ * replayed on `stream`; calls on the same plan must not overlap.
  * Errors: EINVAL, ECUDA. */
 int cashash_match_plan(cashash_ctx* ctx, cashash_plan* plan, const double* F_dev, uint64_t* match_off,
                        uint32_t* matches, uint64_t cap, cashash_stream_t stream);

@@ -87,6 +87,15 @@ struct cashash_plan {
   uint32_t tau_fixed = 0;              // keep the Hamming threshold hint fixed
   uint32_t occ_grid = 0;               // per-pair launches: resident CTAs
   std::vector<uint32_t> first, count;  // per-pair item ranges (per-pair schedule)
+  // persistent schedule: the launch sequence captured as a CUDA graph, replayed
+  // while the outputs, F and the profiling setting stay the same
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  const double* g_F = nullptr;
+  uint64_t* g_moff = nullptr;
+  uint32_t* g_mt = nullptr;
+  uint64_t g_cap = 0;
+  int g_prof = -1;
   const uint8_t* desc = nullptr;
   const uint32_t* codes = nullptr;
   const uint8_t* buckets = nullptr;
@@ -196,12 +205,14 @@ struct StageTimer {
   cashash_ctx* c;
   int id;
   cudaStream_t s;
-  StageTimer(cashash_ctx* c_, int id_, cudaStream_t s_) : c(c_), id(id_), s(s_) {
-    if (c->profiling && c->ev[id][0]) cudaEventRecord(c->ev[id][0], s);
+  unsigned flags;  // cudaEventRecordExternal while capturing a graph
+  StageTimer(cashash_ctx* c_, int id_, cudaStream_t s_, bool capturing = false)
+      : c(c_), id(id_), s(s_), flags(capturing ? cudaEventRecordExternal : 0u) {
+    if (c->profiling && c->ev[id][0]) cudaEventRecordWithFlags(c->ev[id][0], s, flags);
   }
   ~StageTimer() {
     if (c->profiling && c->ev[id][1]) {
-      cudaEventRecord(c->ev[id][1], s);
+      cudaEventRecordWithFlags(c->ev[id][1], s, flags);
       c->ev_used[id] = 1;
     }
   }
@@ -419,6 +430,8 @@ void cashash_plan_destroy(cashash_plan* pl) {
   dfree(pl->d_item_ctr);
   dfree(pl->d_queue);
   dfree(pl->d_tau);
+  if (pl->gexec) cudaGraphExecDestroy(pl->gexec);
+  if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
   delete pl;
 }
 
@@ -514,13 +527,13 @@ int cashash_plan_create(cashash_ctx* c, const cashash_set* s, const uint32_t* pa
   return CASHASH_OK;
 }
 
-int cashash_match_plan(cashash_ctx* c, cashash_plan* pl, const double* F_dev, uint64_t* match_off,
-                       uint32_t* matches, uint64_t cap, cashash_stream_t stream_) {
-  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
-  if (!c || !pl || pl->ctx != c || !match_off || (cap > 0 && !matches)) return CASHASH_EINVAL;
-  if (c->p.epi_px >= 0.0 && pl->P > 0 && !F_dev) return CASHASH_EINVAL;
-  if ((reinterpret_cast<uintptr_t>(match_off) & 7) || (reinterpret_cast<uintptr_t>(matches) & 3)) return CASHASH_EINVAL;
-  CK(cudaSetDevice(c->device));
+namespace {
+
+// Enqueues the matching sequence of a plan on `stream`: counter resets, the
+// matching kernel(s), the exact fallback (persistent form), offsets and
+// compaction.  `capturing` marks a graph capture (events become external nodes).
+int enqueue_match(cashash_ctx* c, cashash_plan* pl, const double* F_dev, uint64_t* match_off, uint32_t* matches,
+                  uint64_t cap, cudaStream_t stream, bool capturing) {
   const uint32_t P = pl->P;
   if (P) CK(cudaMemsetAsync(pl->d_pair_cnt, 0, sizeof(unsigned long long) * P, stream));
   MatchArgs a{};
@@ -541,9 +554,8 @@ int cashash_match_plan(cashash_ctx* c, cashash_plan* pl, const double* F_dev, ui
   a.tau_pair = pl->d_tau;
   a.tau_fixed = pl->tau_fixed;
   a.kp = c->kp;
-  c->ev_used[CASHASH_STAGE_MATCH] = c->ev_used[CASHASH_STAGE_COMPACT] = 0;
   {
-    StageTimer tm(c, CASHASH_STAGE_MATCH, stream);
+    StageTimer tm(c, CASHASH_STAGE_MATCH, stream, capturing);
     CK(cudaMemsetAsync(pl->d_item_ctr, 0, sizeof(unsigned int) * ((size_t)P + 1), stream));
     if (pl->persistent) {
       a.items = pl->d_items;
@@ -551,7 +563,6 @@ int cashash_match_plan(cashash_ctx* c, cashash_plan* pl, const double* F_dev, ui
       a.item_ctr = pl->d_item_ctr + P;
       CK(launch_match(a, 1, pl->grid, stream));
       CK(launch_match_fallback(a, stream));
-      c->n_launches += (pl->grid ? 1 : 0) + (pl->n_res ? 1 : 0);
     } else {
       for (uint32_t i = 0; i < P; ++i) {
         if (!pl->count[i]) continue;
@@ -559,18 +570,72 @@ int cashash_match_plan(cashash_ctx* c, cashash_plan* pl, const double* F_dev, ui
         a.n_items = pl->count[i];
         a.item_ctr = pl->d_item_ctr + i;
         CK(launch_match(a, 0, std::min(pl->count[i], pl->occ_grid), stream));
-        c->n_launches += 1;
       }
     }
   }
   {
-    StageTimer tm(c, CASHASH_STAGE_COMPACT, stream);
+    StageTimer tm(c, CASHASH_STAGE_COMPACT, stream, capturing);
     CK(launch_scan_counts(pl->d_pair_cnt, P, match_off, cap, c->d_status, c->d_cnt + 2, stream));
     CK(launch_compact(pl->d_pairs, P, pl->d_res, match_off, matches, cap, stream));
-    c->n_launches += P ? 2 : 1;
   }
+  return CASHASH_OK;
+}
+
+uint64_t match_launches(const cashash_plan* pl) {
+  uint64_t n = pl->P ? 2 : 1;  // scan + compaction
+  if (pl->persistent) {
+    n += (pl->grid ? 1 : 0) + (pl->n_res ? 1 : 0);
+  } else {
+    for (uint32_t i = 0; i < pl->P; ++i) n += pl->count[i] ? 1 : 0;
+  }
+  return n;
+}
+
+}  // namespace
+
+int cashash_match_plan(cashash_ctx* c, cashash_plan* pl, const double* F_dev, uint64_t* match_off,
+                       uint32_t* matches, uint64_t cap, cashash_stream_t stream_) {
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+  if (!c || !pl || pl->ctx != c || !match_off || (cap > 0 && !matches)) return CASHASH_EINVAL;
+  if (c->p.epi_px >= 0.0 && pl->P > 0 && !F_dev) return CASHASH_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(match_off) & 7) || (reinterpret_cast<uintptr_t>(matches) & 3)) return CASHASH_EINVAL;
+  CK(cudaSetDevice(c->device));
+  c->ev_used[CASHASH_STAGE_MATCH] = c->ev_used[CASHASH_STAGE_COMPACT] = 0;
+  if (pl->persistent) {
+    const bool same = pl->gexec && pl->g_F == F_dev && pl->g_moff == match_off && pl->g_mt == matches &&
+                      pl->g_cap == cap && pl->g_prof == c->profiling;
+    if (!same) {
+      if (pl->gexec) cudaGraphExecDestroy(pl->gexec);
+      pl->gexec = nullptr;
+      if (!pl->cap_stream) CK(cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking));
+      CK(cudaStreamBeginCapture(pl->cap_stream, cudaStreamCaptureModeThreadLocal));
+      const int st = enqueue_match(c, pl, F_dev, match_off, matches, cap, pl->cap_stream, true);
+      cudaGraph_t g = nullptr;
+      const cudaError_t e = cudaStreamEndCapture(pl->cap_stream, &g);
+      if (st != CASHASH_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+      }
+      CK(e);
+      const cudaError_t ei = cudaGraphInstantiate(&pl->gexec, g, 0);
+      cudaGraphDestroy(g);
+      CK(ei);
+      pl->g_F = F_dev;
+      pl->g_moff = match_off;
+      pl->g_mt = matches;
+      pl->g_cap = cap;
+      pl->g_prof = c->profiling;
+    }
+    CK(cudaGraphLaunch(pl->gexec, stream));
+    if (c->profiling)  // the graph holds the stage events as external event-record nodes
+      c->ev_used[CASHASH_STAGE_MATCH] = c->ev_used[CASHASH_STAGE_COMPACT] = 1;
+  } else {
+    const int st = enqueue_match(c, pl, F_dev, match_off, matches, cap, stream, false);
+    if (st != CASHASH_OK) return st;
+  }
+  c->n_launches += match_launches(pl);
   c->last_stream = stream;
-  c->last_pairs = P;
+  c->last_pairs = pl->P;
   c->last_items = pl->n_items;
   return CASHASH_OK;
 }

@@ -1,0 +1,135 @@
+"""Full-size workloads in the launch configuration bench.py times.
+
+The oracle cannot re-match every pair at these sizes in seconds, so:
+  * hash codes and bucket ids are compared for every feature (config 1) or
+    for every feature of the sampled images (config 3);
+  * the match lists of a random sample of pairs are compared entry for entry;
+  * every pair's list is checked for properties that hold at any size.
+"""
+import threading
+
+import numpy as np
+import pytest
+
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ch():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1805_08995_gb300 as m
+    torch.cuda.set_device(0)
+    return m
+
+
+def _oracle_codes(orc, desc, R, po, mu, threads=16):
+    n = desc.shape[0]
+    codes = np.zeros((n, 4), np.uint32)
+    buckets = np.zeros((n, po.n_tables), np.uint8)
+    step = max(1, (n + threads - 1) // threads)
+
+    def work(s):
+        codes[s:s + step], buckets[s:s + step] = orc.hash_codes(desc[s:s + step], mu, R, po)
+
+    ts = [threading.Thread(target=work, args=(s,)) for s in range(0, n, step)]
+    [t.start() for t in ts]
+    [t.join() for t in ts]
+    return codes, buckets
+
+
+def _run_gpu(ch, s, precision=0, repeats=2):
+    p = ch.cashash_default_params(precision=precision, schedule=ch.CASHASH_SCHED_PERSISTENT)
+    ctx = ch.cashash_create(p, s.R)
+    ds = ch.DeviceSet(p, s.img_off, s.desc)
+    plan = ch.cashash_plan_create(ctx, ds, s.pairs)
+    P = len(s.pairs)
+    cap = int(s.sizes()[s.pairs[:, 0]].sum())
+    moff = torch.zeros(P + 1, dtype=torch.int64, device="cuda")
+    mt = torch.zeros((cap, 2), dtype=torch.int32, device="cuda")
+    outs = []
+    for _ in range(repeats):  # the second pass replays the captured graph with learned thresholds
+        ch.cashash_build_codes(ctx, ds)
+        ch.cashash_match_plan(ctx, plan, moff, mt, cap)
+        assert ch.cashash_sync_status(ctx) == ch.CASHASH_OK
+        off = moff.cpu().numpy().astype(np.uint64)
+        outs.append((off, mt[:int(off[-1])].cpu().numpy().view(np.uint32).copy()))
+    stats = ch.cashash_get_stats(ctx)
+    mu = ch.cashash_get_mean(ctx)
+    return ctx, ds, plan, outs, stats, mu
+
+
+def _properties(s, off, mt):
+    sizes = s.sizes()
+    assert off[0] == 0 and np.all(np.diff(off.astype(np.int64)) >= 0)
+    for i, (a, b) in enumerate(s.pairs):
+        seg = mt[int(off[i]):int(off[i + 1])]
+        if len(seg):
+            assert seg[:, 0].max() < sizes[a] and seg[:, 1].max() < sizes[b]
+            assert np.all(np.diff(seg[:, 0].astype(np.int64)) > 0)   # strictly ascending queries
+
+
+def _sample_check(orc, s, off, mt, codes_of, mu, n_sample, seed):
+    po = orc.params()
+    rng = np.random.default_rng(seed)
+    pick = np.sort(rng.choice(len(s.pairs), size=min(n_sample, len(s.pairs)), replace=False))
+    for i in pick:
+        a, b = (int(x) for x in s.pairs[i])
+        A = slice(int(s.img_off[a]), int(s.img_off[a + 1]))
+        B = slice(int(s.img_off[b]), int(s.img_off[b + 1]))
+        cA, bA = codes_of(a)
+        cB, bB = codes_of(b)
+        m = orc.match_pair(s.desc[A], cA, bA, s.desc[B], cB, bB, po)
+        q = np.nonzero(m >= 0)[0]
+        exp = np.stack([q, m[q]], axis=1).astype(np.uint32) if q.size else np.zeros((0, 2), np.uint32)
+        assert np.array_equal(mt[int(off[i]):int(off[i + 1])], exp), "pair %d (%d, %d)" % (i, a, b)
+
+
+def test_config1_full_size(ch, orc):
+    s = synth.config1()
+    ctx, ds, plan, outs, stats, mu = _run_gpu(ch, s)
+    po = orc.params()
+    assert np.array_equal(mu, orc.mean(s.desc))
+    codes, buckets = _oracle_codes(orc, s.desc, s.R, po, mu)
+    assert np.array_equal(ds.codes_np(), codes)
+    assert np.array_equal(ds.buckets_np(6), buckets)
+    (off1, mt1), (off2, mt2) = outs
+    assert np.array_equal(off1, off2) and np.array_equal(mt1, mt2)
+    _properties(s, off2, mt2)
+
+    def codes_of(i):
+        a, b = int(s.img_off[i]), int(s.img_off[i + 1])
+        return codes[a:b], buckets[a:b]
+
+    _sample_check(orc, s, off2, mt2, codes_of, mu, 40, 5)
+    plan.close()
+    ctx.close()
+
+
+def test_config3_full_size(ch, orc):
+    s = synth.config3()
+    ctx, ds, plan, outs, stats, mu = _run_gpu(ch, s)
+    po = orc.params()
+    assert np.array_equal(mu, orc.mean(s.desc))
+    (off1, mt1), (off2, mt2) = outs
+    assert np.array_equal(off1, off2) and np.array_equal(mt1, mt2)
+    _properties(s, off2, mt2)
+    gcodes, gbuckets = ds.codes_np(), ds.buckets_np(6)
+    cache = {}
+
+    def codes_of(i):
+        if i not in cache:
+            a, b = int(s.img_off[i]), int(s.img_off[i + 1])
+            c, bk = orc.hash_codes(s.desc[a:b], mu, s.R, po)
+            assert np.array_equal(gcodes[a:b], c) and np.array_equal(gbuckets[a:b], bk)
+            cache[i] = (c, bk)
+        return cache[i]
+
+    _sample_check(orc, s, off2, mt2, codes_of, mu, 24, 6)
+    plan.close()
+    ctx.close()

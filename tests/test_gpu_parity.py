@@ -289,3 +289,29 @@ def test_invalid_arguments_are_rejected(ch):
     with pytest.raises(ch.CashashError):
         ch.cashash_create(ch.cashash_default_params(code_bits=100), s.R)
     ctx.close()
+
+
+def test_stage_profiling_and_graph_replay(ch):
+    """Per-stage CUDA-event times are reported for direct launches and for
+    replays of the captured persistent graph (external event nodes)."""
+    s = synth.random_set(808, [3000, 3500, 1200])
+    pairs = _pairs([3000, 3500, 1200])
+    for sched in (0, 1):
+        p = ch.cashash_default_params(schedule=sched)
+        ctx = ch.cashash_create(p, s.R)
+        ch.cashash_set_profiling(ctx, True)
+        ds = ch.DeviceSet(p, s.img_off, s.desc)
+        plan = ch.cashash_plan_create(ctx, ds, pairs)
+        cap = int(s.sizes()[pairs[:, 0]].sum())
+        moff = torch.zeros(len(pairs) + 1, dtype=torch.int64, device="cuda")
+        mt = torch.zeros((cap, 2), dtype=torch.int32, device="cuda")
+        n0 = ch.cashash_get_stats(ctx)["n_launches"]
+        for _ in range(3):
+            ch.cashash_build_codes(ctx, ds)
+            ch.cashash_match_plan(ctx, plan, moff, mt, cap)
+            st = ch.cashash_get_stats(ctx)
+            assert all(v > 0 for v in st["ms_stage"].values()), st["ms_stage"]
+        assert st["n_launches"] > n0
+        assert ch.cashash_sync_status(ctx) == ch.CASHASH_OK
+        plan.close()
+        ctx.close()
