@@ -47,7 +47,8 @@ struct cashash_ctx {
   double* d_R = nullptr;        // [rows][128]
   double* d_nrmR = nullptr;     // [rows]
   float* d_R32T = nullptr;      // [128][192] FP32 R, transposed, zero padded
-  void* d_Rbf = nullptr;        // BF16 form operands (hi/lo split)
+  void* d_Rbf = nullptr;        // BF16 form operands: R hi and lo, core-matrix layout
+  uint32_t np_tc = 0;           // BF16 form: rows padded to a multiple of 16
   double* d_mu = nullptr;       // [128]
   RowConst* d_rc = nullptr;     // [192]
   unsigned long long* d_colsum = nullptr;  // [128]
@@ -156,6 +157,30 @@ template <class T>
 void dfree(T*& ptr) {
   if (ptr) cudaFree(ptr);
   ptr = nullptr;
+}
+
+// Round-to-nearest-even of a double to bfloat16 (8-bit significand), bits.
+uint16_t bf16_rn(double x) {
+  if (x == 0.0 || !std::isfinite(x)) return std::signbit(x) ? 0x8000u : 0u;
+  int e = 0;
+  const double m = std::frexp(std::fabs(x), &e);  // |x| = m 2^e, m in [0.5, 1)
+  double M = std::nearbyint(std::ldexp(m, 8));     // 8 significant bits, ties to even
+  if (M == 256.0) {
+    M = 128.0;
+    e += 1;
+  }
+  const float v = (float)std::ldexp(M, e - 8);     // exact: at most 8 significant bits
+  uint32_t u;
+  std::memcpy(&u, &v, sizeof u);
+  if (x < 0) u |= 0x80000000u;
+  return (uint16_t)(u >> 16);
+}
+
+double bf16_to_double(uint16_t h) {
+  const uint32_t u = (uint32_t)h << 16;
+  float f;
+  std::memcpy(&f, &u, sizeof f);
+  return (double)f;
 }
 
 // Validates a set; returns number of lookup-table chunks through *n_chunks.
@@ -294,7 +319,6 @@ int cashash_create(cashash_ctx** out, const cashash_params* p, const double* R_h
   const uint32_t rows = p->code_bits + p->n_tables * p->bits_per_table;
   for (uint64_t i = 0; i < (uint64_t)rows * DIM; ++i)
     if (!std::isfinite(R_host[i])) return CASHASH_EINVAL;
-  if (p->precision == CASHASH_BF16) return CASHASH_ENOTSUP;
   cashash_ctx* c = new (std::nothrow) cashash_ctx();
   if (!c) return CASHASH_ENOMEM;
   c->p = *p;
@@ -342,6 +366,28 @@ int cashash_create(cashash_ctx** out, const cashash_params* p, const double* R_h
   if (st == CASHASH_OK) st = cuda_err(cudaMemcpy(c->d_nrmR, nrm.data(), sizeof(double) * rows, cudaMemcpyHostToDevice));
   if (st == CASHASH_OK)
     st = cuda_err(cudaMemcpy(c->d_R32T, r32t.data(), sizeof(float) * r32t.size(), cudaMemcpyHostToDevice));
+  if (st == CASHASH_OK && p->precision == CASHASH_BF16) {
+    // R = hi + lo + r with hi = bf16(R), lo = bf16(R - hi) (R - hi is exact by Sterbenz), |r| <= 2^-16 |R|;
+    // laid out as K-major core matrices: (row group, k group) at ((r8 * 16 + k8) * 64) elements
+    const uint32_t NP = (rows + 15) / 16 * 16;
+    c->np_tc = NP;
+    std::vector<uint16_t> hb((size_t)2 * NP * DIM, 0);
+    for (uint32_t b = 0; b < rows; ++b)
+      for (int j = 0; j < DIM; ++j) {
+        const double v = R_host[(size_t)b * DIM + j];
+        const uint16_t hi = bf16_rn(v);
+        const uint16_t lo = bf16_rn(v - bf16_to_double(hi));
+        const size_t off = ((size_t)(b >> 3) * 16 + (j >> 3)) * 64 + (b & 7) * 8 + (j & 7);
+        hb[off] = hi;
+        hb[(size_t)NP * DIM + off] = lo;
+      }
+    cap = 0;
+    uint16_t* d = nullptr;
+    st = grow(d, cap, hb.size());
+    c->d_Rbf = d;
+    if (st == CASHASH_OK)
+      st = cuda_err(cudaMemcpy(c->d_Rbf, hb.data(), hb.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
+  }
   if (st == CASHASH_OK) st = cuda_err(cudaMemset(c->d_cnt, 0, 8 * sizeof(unsigned long long)));
   if (st == CASHASH_OK) st = cuda_err(cudaMemset(c->d_status, 0, sizeof(uint32_t)));
   if (st == CASHASH_OK) st = cuda_err(cudaMemset(c->d_mu, 0, DIM * sizeof(double)));
@@ -383,7 +429,8 @@ int cashash_build_codes(cashash_ctx* c, const cashash_set* s, const double* mean
       CK(launch_colsum(s->desc, n, c->d_colsum, stream));
       c->n_launches += n ? 1 : 0;
     }
-    const float alpha_scale = 0x1p-16f;
+    // bound factor on ||R_b|| ||x||: FP32 FMA chains (2^-16), BF16 tensor cores (2^-15)
+    const float alpha_scale = c->p.precision == CASHASH_BF16 ? 0x1p-15f : 0x1p-16f;
     CK(launch_row_consts(c->d_colsum, n, mean_host ? 1 : 0, c->d_mu, c->d_R, c->d_nrmR, c->rows, alpha_scale,
                          c->d_rc, stream));
     c->n_launches += 1;
@@ -392,8 +439,12 @@ int cashash_build_codes(cashash_ctx* c, const cashash_set* s, const double* mean
   if (n) {
     {
       StageTimer tm(c, CASHASH_STAGE_PROJECT, stream);
-      CK(launch_project_fp32(s->desc, n, c->d_R32T, c->d_rc, c->kp, s->codes, s->buckets, s->sqnorm, c->d_flagmask,
-                             c->d_flaglist, c->d_cnt + 0, stream));
+      if (c->p.precision == CASHASH_BF16)
+        CK(launch_project_bf16(s->desc, n, c->d_Rbf, c->np_tc, c->d_rc, c->kp, s->codes, s->buckets, s->sqnorm,
+                               c->d_flagmask, c->d_flaglist, c->d_cnt + 0, c->d_status, stream));
+      else
+        CK(launch_project_fp32(s->desc, n, c->d_R32T, c->d_rc, c->kp, s->codes, s->buckets, s->sqnorm, c->d_flagmask,
+                               c->d_flaglist, c->d_cnt + 0, stream));
     }
     {
       StageTimer tm(c, CASHASH_STAGE_REEVAL, stream);

@@ -106,48 +106,6 @@ cudaError_t launch_row_consts(const unsigned long long* sums, uint64_t n, int ha
 }
 
 // ---------------------------------------------------------------------------
-// Shared epilogue: from the approximate projections of one feature, write its
-// code words, bucket bytes and squared norm, and record flagged rows.
-// sbits / sflag hold 192 bits per feature (rows 0..191).
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t extract_bits(const uint32_t* w, uint32_t pos, uint32_t m) {
-  if (m == 0) return 0;
-  const uint32_t wi = pos >> 5, sh = pos & 31;
-  uint64_t v = w[wi];
-  if (wi + 1 < 6) v |= (uint64_t)w[wi + 1] << 32;
-  return (uint32_t)(v >> sh) & ((1u << m) - 1u);
-}
-
-__device__ __forceinline__ void write_feature(uint64_t f, const uint32_t* bits, const uint32_t* flags,
-                                              uint32_t sq, const KParams& kp, uint32_t* __restrict__ codes,
-                                              uint8_t* __restrict__ buckets, uint32_t* __restrict__ sqnorm,
-                                              uint32_t* __restrict__ flagmask, uint32_t* __restrict__ flaglist,
-                                              unsigned long long* __restrict__ nflag_feat) {
-  uint4 c;
-  c.x = bits[0];
-  c.y = kp.code_bits > 32 ? bits[1] : 0u;
-  c.z = kp.code_bits > 64 ? bits[2] : 0u;
-  c.w = kp.code_bits > 96 ? bits[3] : 0u;
-  reinterpret_cast<uint4*>(codes)[f] = c;
-  uint32_t b[8];
-#pragma unroll
-  for (int t = 0; t < 8; ++t)
-    b[t] = ((uint32_t)t < kp.n_tables) ? extract_bits(bits, kp.code_bits + t * kp.bits_per_table, kp.bits_per_table) : 0u;
-  uint2 bb;
-  bb.x = b[0] | (b[1] << 8) | (b[2] << 16) | (b[3] << 24);
-  bb.y = b[4] | (b[5] << 8) | (b[6] << 16) | (b[7] << 24);
-  reinterpret_cast<uint2*>(buckets)[f] = bb;
-  sqnorm[f] = sq;
-  const uint32_t any = flags[0] | flags[1] | flags[2] | flags[3] | flags[4] | flags[5];
-  if (any) {
-#pragma unroll
-    for (int k = 0; k < 6; ++k) flagmask[f * 6 + k] = flags[k];
-    const unsigned long long slot = atomicAdd(nflag_feat, 1ull);
-    flaglist[slot] = (uint32_t)f;  // features are < 2^32 per set (checked on the host)
-  }
-}
-
-// ---------------------------------------------------------------------------
 // FP32 CUDA-core projection.  Tile: 64 features x 192 rows per CTA of 256
 // threads; thread (fg, rg) owns features 4fg..4fg+3 and rows 12rg..12rg+11.
 // Each accumulator is one sequential FMA chain over j = 0..127, which the
@@ -282,9 +240,10 @@ cudaError_t launch_project_fp32(const uint8_t* desc, uint64_t n, const float* R3
 // ---------------------------------------------------------------------------
 // Exact re-evaluation of flagged (feature, row) projections: the double
 // sequence t = x_j - mu_j, p = R_bj * t, s = s + p for j = 0..127, each
-// rounded to nearest (explicit _rn intrinsics, so no contraction).  One warp
-// per flagged feature; lanes take its flagged rows.  Bits that come out 1
-// are ORed into the codes / bucket bytes (they were written as 0).
+// rounded to nearest (explicit _rn intrinsics, so no contraction).  One
+// flagged feature per thread, so a warp runs 32 independent chains; within a
+// chain the products are formed ahead of the (ordered) additions.  Bits that
+// come out 1 are ORed into the codes / bucket bytes (they were written as 0).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_fix_fp64(const uint8_t* __restrict__ desc, const double* __restrict__ mu,
                                                   const double* __restrict__ R, KParams kp,
@@ -297,52 +256,50 @@ __global__ void __launch_bounds__(256) k_fix_fp64(const uint8_t* __restrict__ de
   __shared__ double mu_s[DIM];
   for (int i = threadIdx.x; i < DIM; i += blockDim.x) mu_s[i] = mu[i];
   __syncthreads();
-  const int lane = threadIdx.x & 31;
-  const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   uint64_t nf = *nflag_feat;
   if (nf > max_feat) nf = max_feat;
-  for (uint64_t idx = warp; idx < nf; idx += nwarps) {
+  unsigned long long done = 0;
+  for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < nf;
+       idx += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t f = flaglist[idx];
-    uint32_t m[6];
-    uint32_t cnt = 0;
-#pragma unroll
+    const uint4* xr = reinterpret_cast<const uint4*>(desc + f * DIM);
     for (int k = 0; k < 6; ++k) {
-      m[k] = flagmask[f * 6 + k];
-      cnt += __popc(m[k]);
-    }
-    if (lane == 0) atomicAdd(n_reeval, (unsigned long long)cnt);
-    const uint8_t* x = desc + f * DIM;
-    for (uint32_t r = lane; r < cnt; r += 32) {
-      // row of the r-th set bit (r < cnt, so the word index stays below 6)
-      uint32_t rr = r;
-      int k = 0;
-      while (rr >= (uint32_t)__popc(m[k])) {
-        rr -= __popc(m[k]);
-        ++k;
-      }
-      uint32_t w = m[k];
-      for (uint32_t s = 0; s < rr; ++s) w &= w - 1;
-      const uint32_t row = 32 * k + (__ffs(w) - 1);
-      const double* Rr = R + (size_t)row * DIM;
-      double s = 0.0;
-      for (int j = 0; j < DIM; ++j) {
-        const double t = __dsub_rn((double)x[j], mu_s[j]);
-        const double p = __dmul_rn(Rr[j], t);
-        s = __dadd_rn(s, p);
-      }
-      if (s > 0.0) {
-        if (row < kp.code_bits) {
-          atomicOr(&codes[f * 4 + (row >> 5)], 1u << (row & 31));
-        } else {
-          const uint32_t rt = row - kp.code_bits;
-          const uint32_t t = rt / kp.bits_per_table, i = rt % kp.bits_per_table;
-          const uint64_t byte = f * 8 + t;
-          atomicOr(reinterpret_cast<uint32_t*>(buckets) + (byte >> 2), 1u << (8 * (byte & 3) + i));
+      uint32_t m = flagmask[f * 6 + k];
+      while (m) {
+        const uint32_t row = 32 * k + (__ffs(m) - 1);
+        m &= m - 1;
+        ++done;
+        const double* Rr = R + (size_t)row * DIM;
+        double s = 0.0;
+        for (int c = 0; c < 8; ++c) {  // 16 descriptor bytes per step
+          const uint4 v = __ldg(xr + c);
+          const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+          double p[16];
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            const int j = 16 * c + e;
+            const double t = __dsub_rn((double)((w[e >> 2] >> (8 * (e & 3))) & 0xFFu), mu_s[j]);
+            p[e] = __dmul_rn(__ldg(Rr + j), t);
+          }
+#pragma unroll
+          for (int e = 0; e < 16; ++e) s = __dadd_rn(s, p[e]);
+        }
+        if (s > 0.0) {
+          if (row < kp.code_bits) {
+            atomicOr(&codes[f * 4 + (row >> 5)], 1u << (row & 31));
+          } else {
+            const uint32_t rt = row - kp.code_bits;
+            const uint32_t t = rt / kp.bits_per_table, i = rt % kp.bits_per_table;
+            const uint64_t byte = f * 8 + t;
+            atomicOr(reinterpret_cast<uint32_t*>(buckets) + (byte >> 2), 1u << (8 * (byte & 3) + i));
+          }
         }
       }
     }
   }
+  // one counter update per warp
+  for (int o = 16; o > 0; o >>= 1) done += __shfl_xor_sync(0xFFFFFFFFu, done, o);
+  if ((threadIdx.x & 31) == 0 && done) atomicAdd(n_reeval, done);
 }
 
 cudaError_t launch_fix_fp64(const uint8_t* desc, const double* mu, const double* R, const KParams& kp,
@@ -353,7 +310,7 @@ cudaError_t launch_fix_fp64(const uint8_t* desc, const double* mu, const double*
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  k_fix_fp64<<<nsm * 4, 256, 0, s>>>(desc, mu, R, kp, flagmask, flaglist, nflag_feat, max_feat, codes, buckets,
+  k_fix_fp64<<<nsm * 8, 256, 0, s>>>(desc, mu, R, kp, flagmask, flaglist, nflag_feat, max_feat, codes, buckets,
                                      n_reeval);
   return cudaGetLastError();
 }

@@ -50,6 +50,53 @@ struct RowConst {
   float pad;
 };
 
+constexpr int PT_ROWS_TC = 192;   // projection rows supported by the tensor-core form (padded to 16)
+
+#ifdef __CUDACC__
+// ---------------------------------------------------------------------------
+// Shared epilogue: from the approximate projections of one feature, write its
+// code words, bucket bytes and squared norm, and record flagged rows.
+// sbits / sflag hold 192 bits per feature (rows 0..191).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t extract_bits(const uint32_t* w, uint32_t pos, uint32_t m) {
+  if (m == 0) return 0;
+  const uint32_t wi = pos >> 5, sh = pos & 31;
+  uint64_t v = w[wi];
+  if (wi + 1 < 6) v |= (uint64_t)w[wi + 1] << 32;
+  return (uint32_t)(v >> sh) & ((1u << m) - 1u);
+}
+
+__device__ __forceinline__ void write_feature(uint64_t f, const uint32_t* bits, const uint32_t* flags,
+                                              uint32_t sq, const KParams& kp, uint32_t* __restrict__ codes,
+                                              uint8_t* __restrict__ buckets, uint32_t* __restrict__ sqnorm,
+                                              uint32_t* __restrict__ flagmask, uint32_t* __restrict__ flaglist,
+                                              unsigned long long* __restrict__ nflag_feat) {
+  uint4 c;
+  c.x = bits[0];
+  c.y = kp.code_bits > 32 ? bits[1] : 0u;
+  c.z = kp.code_bits > 64 ? bits[2] : 0u;
+  c.w = kp.code_bits > 96 ? bits[3] : 0u;
+  reinterpret_cast<uint4*>(codes)[f] = c;
+  uint32_t b[8];
+#pragma unroll
+  for (int t = 0; t < 8; ++t)
+    b[t] = ((uint32_t)t < kp.n_tables) ? extract_bits(bits, kp.code_bits + t * kp.bits_per_table, kp.bits_per_table) : 0u;
+  uint2 bb;
+  bb.x = b[0] | (b[1] << 8) | (b[2] << 16) | (b[3] << 24);
+  bb.y = b[4] | (b[5] << 8) | (b[6] << 16) | (b[7] << 24);
+  reinterpret_cast<uint2*>(buckets)[f] = bb;
+  sqnorm[f] = sq;
+  const uint32_t any = flags[0] | flags[1] | flags[2] | flags[3] | flags[4] | flags[5];
+  if (any) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) flagmask[f * 6 + k] = flags[k];
+    const unsigned long long slot = atomicAdd(nflag_feat, 1ull);
+    flaglist[slot] = (uint32_t)f;  // features are < 2^32 per set (checked on the host)
+  }
+}
+
+#endif
+
 // ---- launchers (return cudaError_t of the launch) ----
 cudaError_t launch_colsum(const uint8_t* desc, uint64_t n, unsigned long long* sums, cudaStream_t s);
 cudaError_t launch_row_consts(const unsigned long long* sums, uint64_t n, int have_mean, double* mu,
@@ -59,10 +106,10 @@ cudaError_t launch_project_fp32(const uint8_t* desc, uint64_t n, const float* R3
                                 const KParams& kp, uint32_t* codes, uint8_t* buckets, uint32_t* sqnorm,
                                 uint32_t* flagmask, uint32_t* flaglist, unsigned long long* nflag_feat,
                                 cudaStream_t s);
-cudaError_t launch_project_bf16(const uint8_t* desc, uint64_t n, const void* Rbf, const RowConst* rc,
+cudaError_t launch_project_bf16(const uint8_t* desc, uint64_t n, const void* Rbf, uint32_t NP, const RowConst* rc,
                                 const KParams& kp, uint32_t* codes, uint8_t* buckets, uint32_t* sqnorm,
                                 uint32_t* flagmask, uint32_t* flaglist, unsigned long long* nflag_feat,
-                                cudaStream_t s);
+                                uint32_t* status, cudaStream_t s);
 cudaError_t launch_fix_fp64(const uint8_t* desc, const double* mu, const double* R, const KParams& kp,
                             const uint32_t* flagmask, const uint32_t* flaglist,
                             const unsigned long long* nflag_feat, uint64_t max_feat, uint32_t* codes,

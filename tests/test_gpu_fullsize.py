@@ -90,9 +90,12 @@ def _sample_check(orc, s, off, mt, codes_of, mu, n_sample, seed):
         assert np.array_equal(mt[int(off[i]):int(off[i + 1])], exp), "pair %d (%d, %d)" % (i, a, b)
 
 
-def test_config1_full_size(ch, orc):
+@pytest.mark.parametrize("precision", [0, 1])
+def test_config1_full_size(ch, orc, precision):
+    """precision 0: config 1 (plain FP32 form); 1: config 2 (BF16 tensor-core
+    projection with exact re-evaluation under its rounding bound)."""
     s = synth.config1()
-    ctx, ds, plan, outs, stats, mu = _run_gpu(ch, s)
+    ctx, ds, plan, outs, stats, mu = _run_gpu(ch, s, precision=precision)
     po = orc.params()
     assert np.array_equal(mu, orc.mean(s.desc))
     codes, buckets = _oracle_codes(orc, s.desc, s.R, po, mu)
@@ -113,7 +116,7 @@ def test_config1_full_size(ch, orc):
 
 def test_config3_full_size(ch, orc):
     s = synth.config3()
-    ctx, ds, plan, outs, stats, mu = _run_gpu(ch, s)
+    ctx, ds, plan, outs, stats, mu = _run_gpu(ch, s, precision=1)
     po = orc.params()
     assert np.array_equal(mu, orc.mean(s.desc))
     (off1, mt1), (off2, mt2) = outs

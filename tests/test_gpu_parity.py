@@ -104,10 +104,22 @@ def _pairs(sizes, extra=()):
     return np.array(pr, np.uint32)
 
 
+@pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("sched", [0, 1])
-def test_default_parameters_ragged_images(ch, orc, sched):
+def test_default_parameters_ragged_images(ch, orc, sched, prec):
     s = synth.random_set(101, SIZES)
-    check_case(ch, orc, s, _pairs(SIZES), schedule=sched)
+    check_case(ch, orc, s, _pairs(SIZES), schedule=sched, precision=prec)
+
+
+@pytest.mark.parametrize("pk", [
+    dict(code_bits=64), dict(code_bits=32, n_tables=2), dict(code_bits=96, n_tables=4, bits_per_table=6),
+    dict(n_tables=8, bits_per_table=8), dict(n_tables=1, bits_per_table=0, top_k=8), dict(n_tables=3, bits_per_table=5),
+])
+def test_bf16_projection_row_counts(ch, orc, pk):
+    """Tensor-core projection with every padded row count it supports."""
+    sizes = [700, 1300, 0, 129, 4500]
+    s = synth.random_set(212, sizes)
+    check_case(ch, orc, s, _pairs(sizes), precision=1, **pk)
 
 
 @pytest.mark.parametrize("pk", [
@@ -204,12 +216,13 @@ def test_identical_and_degenerate_descriptors(ch, orc):
     s = synth.ImageSet(desc, np.array([0, 40, 41, 41, 71], np.uint64),
                        np.array([[0, 0], [0, 1], [1, 0], [2, 0], [0, 2], [3, 0], [0, 3], [3, 3]], np.uint32),
                        synth.projection_matrix(5))
-    check_case(ch, orc, s, s.pairs)
-    same = synth.ImageSet(np.repeat(one, 50, axis=0), np.array([0, 20, 50], np.uint64),
-                          np.array([[0, 1], [1, 0], [0, 0]], np.uint32), synth.projection_matrix(6))
-    ds, codes, buckets, stats = check_case(ch, orc, same, same.pairs)
-    assert not codes.any() and not buckets.any()
-    assert stats["n_reevaluated"] == 50 * 176
+    for prec in (0, 1):
+        check_case(ch, orc, s, s.pairs, precision=prec)
+        same = synth.ImageSet(np.repeat(one, 50, axis=0), np.array([0, 20, 50], np.uint64),
+                              np.array([[0, 1], [1, 0], [0, 0]], np.uint32), synth.projection_matrix(6))
+        ds, codes, buckets, stats = check_case(ch, orc, same, same.pairs, precision=prec)
+        assert not codes.any() and not buckets.any()
+        assert stats["n_reevaluated"] == 50 * 176
 
 
 @pytest.mark.parametrize("sched", [0, 1])
