@@ -287,6 +287,9 @@ def run_ours(args):
     e1 = torch.cuda.Event(enable_timing=True)
     for _ in range(args.steps):
         flush.zero_()
+        if args.thresholds == "fresh":
+            # forget the per-pair Hamming thresholds learned by earlier steps
+            ch.cashash_plan_set_threshold_hint(plan, p.code_bits, False)
         e0.record(stream)
         step()
         e1.record(stream)
@@ -399,6 +402,8 @@ def main():
     ap.add_argument("--schedule", default="persistent", choices=["persistent", "per_pair"])
     ap.add_argument("--ref-pairs", type=int, default=480)
     ap.add_argument("--max-pairs", type=int, default=0, help="match only the first N pairs (profiling case)")
+    ap.add_argument("--thresholds", default="learned", choices=["learned", "fresh"],
+                    help="fresh: clear the learned per-pair Hamming thresholds before every timed step")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

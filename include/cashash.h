@@ -162,19 +162,24 @@ void cashash_plan_destroy(cashash_plan* plan);
  * when epi_px >= 0, else ignored (may be NULL).  When the total exceeds cap,
  * match_off is still complete, nothing beyond cap is written and
  * cashash_sync_status() returns EOVERFLOW.  Asynchronous on `stream`.
- * With the persistent schedule the launch sequence is captured once as a
- * CUDA graph (per set of output pointers, F and profiling setting) and
- * replayed on `stream`; calls on the same plan must not overlap.
+ * With the persistent schedule all pairs are matched by one batched kernel:
+ * a bucket join whose Hamming distances come from the tensor cores when the
+ * band is off and every query image fits its shared-memory counters (at
+ * least 40,000 features), else a speculative per-query kernel; the launch sequence
+ * is captured once as a CUDA graph (per set of output pointers, F and
+ * profiling setting) and replayed on `stream`; calls on the same plan must
+ * not overlap.
  * Errors: EINVAL, ECUDA. */
 int cashash_match_plan(cashash_ctx* ctx, cashash_plan* plan, const double* F_dev, uint64_t* match_off,
                        uint32_t* matches, uint64_t cap, cashash_stream_t stream);
 
 /* Performance hint for the batched (persistent) schedule: the Hamming
- * distance below which candidates are kept for ranking when matching starts.
- * The kernel then adapts it to the largest k-th ranked distance it observes
- * (unless `fixed` is non-zero).  Results never depend on it: a query for
- * which the hint turns away candidates it needed is re-matched exactly.
- * hamming >= code_bits disables the speculation.  Errors: EINVAL, ECUDA. */
+ * distance at or below which candidates are kept for ranking when matching
+ * starts.  The kernels then adapt it per pair to the k-th ranked distances
+ * they observe (unless `fixed` is non-zero).  Results never depend on it: a
+ * query for which the hint turns away candidates it needed is re-matched
+ * exactly.  hamming >= code_bits disables the speculation.
+ * Errors: EINVAL, ECUDA. */
 int cashash_plan_set_threshold_hint(cashash_plan* plan, uint32_t hamming, int fixed);
 
 /* Convenience: plan + match + plan release in one call (same outputs). */

@@ -60,6 +60,10 @@ struct cashash_ctx {
   uint64_t* d_chunk_feat0 = nullptr;
   uint32_t* d_chunk_len = nullptr;
   uint64_t cap_cf0 = 0, cap_clen = 0;
+  uint64_t* d_img_f0 = nullptr;     // per image: first feature, feature count, join-table base
+  uint32_t* d_img_n = nullptr;
+  uint64_t* d_img_join = nullptr;
+  uint64_t cap_if0 = 0, cap_in = 0, cap_ij = 0;
   cudaStream_t last_stream = nullptr;
   uint64_t last_n_features = 0;
   uint64_t last_pairs = 0;
@@ -87,6 +91,9 @@ struct cashash_plan {
   uint32_t grid = 0;                   // persistent grid (resident CTAs)
   uint32_t tau_fixed = 0;              // keep the Hamming threshold hint fixed
   uint32_t occ_grid = 0;               // per-pair launches: resident CTAs
+  bool join = false;                   // persistent schedule: bucket join (else speculative kernel)
+  uint32_t na_max = 1;                 // largest query image (bucket-join scratch)
+  uint32_t* d_jhist = nullptr;         // bucket join: per-pair histogram of k-th Hamming distances
   std::vector<uint32_t> first, count;  // per-pair item ranges (per-pair schedule)
   // persistent schedule: the launch sequence captured as a CUDA graph, replayed
   // while the outputs, F and the profiling setting stay the same
@@ -243,6 +250,19 @@ struct StageTimer {
   }
 };
 
+// Byte offsets of every image's bucket-sorted tables in the table buffer
+// (after the chunked lookup tables).
+void join_layout(const uint64_t* img_off, uint32_t n_images, uint32_t T, std::vector<uint64_t>& base) {
+  uint64_t ch = 0;
+  for (uint32_t i = 0; i < n_images; ++i) ch += (img_off[i + 1] - img_off[i] + JC - 1) / JC;
+  uint64_t o = std::max<uint64_t>(ch, 1) * chunk_bytes(T);
+  base.resize(n_images);
+  for (uint32_t i = 0; i < n_images; ++i) {
+    base[i] = o;
+    o += (uint64_t)T * join_block(img_off[i + 1] - img_off[i]);
+  }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -281,12 +301,14 @@ void cashash_default_params(cashash_params* p) {
 
 uint64_t cashash_tables_bytes(const cashash_params* p, const uint64_t* img_off, uint32_t n_images) {
   if (!params_ok(p) || (n_images > 0 && !img_off)) return 0;
-  uint64_t ch = 0;
+  uint64_t ch = 0, jb = 0;
   for (uint32_t i = 0; i < n_images; ++i) {
     if (img_off[i + 1] < img_off[i]) return 0;
-    ch += (img_off[i + 1] - img_off[i] + JC - 1) / JC;
+    const uint64_t n = img_off[i + 1] - img_off[i];
+    ch += (n + JC - 1) / JC;
+    jb += (uint64_t)p->n_tables * join_block(n);
   }
-  return std::max<uint64_t>(ch, 1) * chunk_bytes(p->n_tables);
+  return std::max<uint64_t>(ch, 1) * chunk_bytes(p->n_tables) + jb;
 }
 
 void cashash_destroy(cashash_ctx* c) {
@@ -307,6 +329,7 @@ void cashash_destroy(cashash_ctx* c) {
   dfree(c->d_R); dfree(c->d_nrmR); dfree(c->d_R32T); dfree(c->d_Rbf); dfree(c->d_mu); dfree(c->d_rc);
   dfree(c->d_colsum); dfree(c->d_cnt); dfree(c->d_status); dfree(c->d_flagmask); dfree(c->d_flaglist);
   dfree(c->d_chunk_feat0); dfree(c->d_chunk_len);
+  dfree(c->d_img_f0); dfree(c->d_img_n); dfree(c->d_img_join);
   for (int i = 0; i < CASHASH_N_STAGES; ++i)
     for (int k = 0; k < 2; ++k)
       if (c->ev[i][k]) cudaEventDestroy(c->ev[i][k]);
@@ -412,7 +435,23 @@ int cashash_build_codes(cashash_ctx* c, const cashash_set* s, const double* mean
   if (st == CASHASH_OK) st = grow(c->d_flaglist, c->cap_flaglist, std::max<uint64_t>(n, 1));
   if (st == CASHASH_OK) st = grow(c->d_chunk_feat0, c->cap_cf0, std::max<uint64_t>(n_chunks, 1));
   if (st == CASHASH_OK) st = grow(c->d_chunk_len, c->cap_clen, std::max<uint64_t>(n_chunks, 1));
+  const uint64_t ni = std::max<uint32_t>(s->n_images, 1);
+  if (st == CASHASH_OK) st = grow(c->d_img_f0, c->cap_if0, ni);
+  if (st == CASHASH_OK) st = grow(c->d_img_n, c->cap_in, ni);
+  if (st == CASHASH_OK) st = grow(c->d_img_join, c->cap_ij, ni);
   if (st != CASHASH_OK) return st;
+  std::vector<uint64_t> jbase, if0(s->n_images);
+  std::vector<uint32_t> inn(s->n_images);
+  join_layout(s->img_off, s->n_images, c->p.n_tables, jbase);
+  for (uint32_t i = 0; i < s->n_images; ++i) {
+    if0[i] = s->img_off[i];
+    inn[i] = (uint32_t)(s->img_off[i + 1] - s->img_off[i]);
+  }
+  if (s->n_images) {
+    CK(cudaMemcpyAsync(c->d_img_f0, if0.data(), s->n_images * sizeof(uint64_t), cudaMemcpyHostToDevice, stream));
+    CK(cudaMemcpyAsync(c->d_img_n, inn.data(), s->n_images * sizeof(uint32_t), cudaMemcpyHostToDevice, stream));
+    CK(cudaMemcpyAsync(c->d_img_join, jbase.data(), s->n_images * sizeof(uint64_t), cudaMemcpyHostToDevice, stream));
+  }
   std::vector<uint64_t> f0;
   std::vector<uint32_t> len;
   chunk_layout(s->img_off, s->n_images, f0, len, nullptr);
@@ -455,8 +494,10 @@ int cashash_build_codes(cashash_ctx* c, const cashash_set* s, const double* mean
       StageTimer tm(c, CASHASH_STAGE_TABLES, stream);
       CK(launch_build_tables(s->buckets, c->d_chunk_feat0, c->d_chunk_len, (uint32_t)n_chunks, c->p.n_tables,
                              s->tables, stream));
+      CK(launch_build_join(s->buckets, s->codes, c->d_img_f0, c->d_img_n, c->d_img_join, s->n_images, c->p.n_tables,
+                           s->tables, stream));
     }
-    c->n_launches += 3;
+    c->n_launches += 4;
   }
   c->last_stream = stream;
   c->last_n_features = n;
@@ -481,6 +522,7 @@ void cashash_plan_destroy(cashash_plan* pl) {
   dfree(pl->d_item_ctr);
   dfree(pl->d_queue);
   dfree(pl->d_tau);
+  dfree(pl->d_jhist);
   if (pl->gexec) cudaGraphExecDestroy(pl->gexec);
   if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
   delete pl;
@@ -510,6 +552,8 @@ int cashash_plan_create(cashash_ctx* c, const cashash_set* s, const uint32_t* pa
   std::vector<uint32_t> len, firstc;
   chunk_layout(s->img_off, s->n_images, f0, len, &firstc);
   std::vector<PairInfo> info(P);
+  std::vector<uint64_t> jbase;
+  join_layout(s->img_off, s->n_images, c->p.n_tables, jbase);
   uint64_t qbase = 0;
   for (uint32_t i = 0; i < P; ++i) {
     const uint32_t a = pairs_host[2 * (size_t)i], b = pairs_host[2 * (size_t)i + 1];
@@ -520,35 +564,51 @@ int cashash_plan_create(cashash_ctx* c, const cashash_set* s, const uint32_t* pa
     pi.nB = (uint32_t)(s->img_off[b + 1] - s->img_off[b]);
     pi.bchunk0 = firstc[b];
     pi.pad = 0;
+    pi.ajoin = jbase[a];
+    pi.bjoin = jbase[b];
     pi.qbase = qbase;
     qbase += pi.nA;
   }
   pl->n_res = qbase;
-  const uint32_t tile = (uint32_t)match_tile_size(c->p.top_k, pl->persistent);
-  // work items: persistent schedule groups the pairs by candidate image so
-  // that a candidate image's chunks are reused from L2 by consecutive items
-  std::vector<uint32_t> order(P);
-  for (uint32_t i = 0; i < P; ++i) order[i] = i;
-  if (pl->persistent)
-    std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
-      return pairs_host[2 * (size_t)x + 1] < pairs_host[2 * (size_t)y + 1];
-    });
   std::vector<uint2> items;
   pl->first.assign(P, 0);
   pl->count.assign(P, 0);
-  for (uint32_t oi = 0; oi < P; ++oi) {
-    const uint32_t i = order[oi];
-    pl->first[i] = (uint32_t)items.size();
-    for (uint32_t q0 = 0; q0 < info[i].nA; q0 += tile) items.push_back(make_uint2(i, q0));
-    pl->count[i] = (uint32_t)items.size() - pl->first[i];
-  }
-  pl->n_items = (uint32_t)items.size();
+  uint32_t na_max = 0;
+  for (uint32_t i = 0; i < P; ++i) na_max = std::max(na_max, info[i].nA);
+  pl->na_max = std::max<uint32_t>(na_max, 1);
   const bool epi = c->p.epi_px >= 0.0;
   if (pl->persistent) {
-    pl->grid = match_grid(c->p.top_k, 1, epi, c->p.n_tables, pl->n_items);
-  } else {
-    pl->occ_grid = match_grid(c->p.top_k, 0, epi, c->p.n_tables, 0xFFFFFFFFu);
+    pl->grid = join_grid(c->kp, pl->na_max, P);
+    pl->join = pl->grid > 0;
   }
+  if (pl->join) {
+    // bucket join: one item per pair, the largest (N_A * N_B) first
+    std::vector<uint32_t> order(P);
+    for (uint32_t i = 0; i < P; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
+      return (uint64_t)info[x].nA * info[x].nB > (uint64_t)info[y].nA * info[y].nB;
+    });
+    for (uint32_t i : order) items.push_back(make_uint2(i, 0u));
+  } else {
+    // tiles of queries; the persistent form groups the pairs by candidate
+    // image so that a candidate image's chunks are reused from L2
+    const uint32_t tile = (uint32_t)match_tile_size(c->p.top_k, pl->persistent);
+    std::vector<uint32_t> order(P);
+    for (uint32_t i = 0; i < P; ++i) order[i] = i;
+    if (pl->persistent)
+      std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
+        return pairs_host[2 * (size_t)x + 1] < pairs_host[2 * (size_t)y + 1];
+      });
+    for (uint32_t oi = 0; oi < P; ++oi) {
+      const uint32_t i = order[oi];
+      pl->first[i] = (uint32_t)items.size();
+      for (uint32_t q0 = 0; q0 < info[i].nA; q0 += tile) items.push_back(make_uint2(i, q0));
+      pl->count[i] = (uint32_t)items.size() - pl->first[i];
+    }
+  }
+  pl->n_items = (uint32_t)items.size();
+  if (pl->persistent && !pl->join) pl->grid = match_grid(c->p.top_k, 1, epi, c->p.n_tables, pl->n_items);
+  if (!pl->persistent) pl->occ_grid = match_grid(c->p.top_k, 0, epi, c->p.n_tables, 0xFFFFFFFFu);
   uint64_t cap = 0;
   int st = grow(pl->d_pairs, cap, std::max<uint64_t>(P, 1));
   cap = 0;
@@ -562,8 +622,16 @@ int cashash_plan_create(cashash_ctx* c, const cashash_set* s, const uint32_t* pa
   cap = 0;
   if (st == CASHASH_OK) st = grow(pl->d_tau, cap, std::max<uint64_t>(P, 1));
   if (st == CASHASH_OK) st = cuda_err(cudaMemset(pl->d_tau, 0, sizeof(uint32_t) * std::max<uint64_t>(P, 1)));
-  if (st == CASHASH_OK && pl->persistent) {
+  if (st == CASHASH_OK && pl->join) {
     cap = 0;
+    st = grow(pl->d_queue, cap, std::max<uint64_t>((uint64_t)pl->grid * pl->na_max * JSEG, 1));
+    cap = 0;
+    if (st == CASHASH_OK) st = grow(pl->d_jhist, cap, std::max<uint64_t>((uint64_t)P * HBINS, 1));
+    if (st == CASHASH_OK)
+      st = cuda_err(cudaMemset(pl->d_jhist, 0, sizeof(uint32_t) * std::max<uint64_t>((uint64_t)P * HBINS, 1)));
+  } else if (st == CASHASH_OK && pl->persistent) {
+    cap = 0;
+    const uint64_t tile = (uint64_t)match_tile_size(c->p.top_k, 1);
     st = grow(pl->d_queue, cap, std::max<uint64_t>((uint64_t)pl->grid * tile * QCAP, 1));
   }
   if (st == CASHASH_OK && P)
@@ -604,6 +672,10 @@ int enqueue_match(cashash_ctx* c, cashash_plan* pl, const double* F_dev, uint64_
   a.queue = pl->d_queue;
   a.tau_pair = pl->d_tau;
   a.tau_fixed = pl->tau_fixed;
+  a.join = pl->tables;
+  a.jqueue = pl->d_queue;
+  a.jhist = pl->d_jhist;
+  a.na_max = pl->na_max;
   a.kp = c->kp;
   {
     StageTimer tm(c, CASHASH_STAGE_MATCH, stream, capturing);
@@ -612,7 +684,8 @@ int enqueue_match(cashash_ctx* c, cashash_plan* pl, const double* F_dev, uint64_
       a.items = pl->d_items;
       a.n_items = pl->n_items;
       a.item_ctr = pl->d_item_ctr + P;
-      CK(launch_match(a, 1, pl->grid, stream));
+      if (pl->join) CK(launch_join(a, pl->grid, stream));
+      else CK(launch_match(a, 1, pl->grid, stream));
       CK(launch_match_fallback(a, stream));
     } else {
       for (uint32_t i = 0; i < P; ++i) {
@@ -635,7 +708,8 @@ int enqueue_match(cashash_ctx* c, cashash_plan* pl, const double* F_dev, uint64_
 uint64_t match_launches(const cashash_plan* pl) {
   uint64_t n = pl->P ? 2 : 1;  // scan + compaction
   if (pl->persistent) {
-    n += (pl->grid ? 1 : 0) + (pl->n_res ? 1 : 0);
+    // calibration + join, or the speculative kernel; then the fallback
+    n += (pl->grid ? (pl->join ? 2 : 1) : 0) + (pl->n_res ? 1 : 0);
   } else {
     for (uint32_t i = 0; i < pl->P; ++i) n += pl->count[i] ? 1 : 0;
   }
@@ -698,6 +772,7 @@ int cashash_plan_set_threshold_hint(cashash_plan* pl, uint32_t hamming, int fixe
   std::vector<uint32_t> h(std::max<uint32_t>(pl->P, 1), v);
   CK(cudaDeviceSynchronize());
   CK(cudaMemcpy(pl->d_tau, h.data(), sizeof(uint32_t) * h.size(), cudaMemcpyHostToDevice));
+  if (pl->d_jhist) CK(cudaMemset(pl->d_jhist, 0, sizeof(uint32_t) * (size_t)std::max<uint32_t>(pl->P, 1) * HBINS));
   pl->tau_fixed = fixed ? 1u : 0u;
   return CASHASH_OK;
 }

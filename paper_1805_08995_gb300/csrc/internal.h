@@ -16,6 +16,8 @@ constexpr int OFF_STRIDE = 264;   // uint16 bucket offsets per (chunk, table): 2
 constexpr uint32_t NO_MATCH = 0xFFFFFFFFu;
 constexpr uint32_t PENDING = 0xFFFFFFFEu;  // query left to the exact fallback kernel
 constexpr uint32_t QCAP = 64;              // survivor-queue entries per query thread
+constexpr uint32_t JSEG = 64;              // bucket join: survivor-list entries per query
+constexpr uint32_t HBINS = 129;            // bucket join: per-pair histogram of k-th Hamming distances
 constexpr uint32_t KEY_INF = 0xFFFFFFFFu;
 
 // device status bits (ORed into the context's status word)
@@ -40,7 +42,17 @@ struct PairInfo {
   uint32_t nA, nB;      // feature counts
   uint32_t bchunk0;     // first lookup-table chunk of the candidate image
   uint32_t pad;
+  uint64_t ajoin, bjoin;  // byte offsets of the two images' bucket-sorted tables (join region)
 };
+
+// Bucket-sorted tables ("join" region of the table buffer), per image and
+// table t, at join_base(image) + t * join_block(N):
+//   uint32 off[260]   bucket v holds positions off[v] .. off[v+1]
+//   uint32 idx[N4]    feature index within the image, ascending within a bucket
+//   uint4  code[N]    the 128-bit code of that feature (inline copy)
+__host__ __device__ inline uint64_t join_block(uint64_t n) {
+  return 1040u + 4u * ((n + 3) / 4 * 4) + 16u * n;
+}
 
 // Per-row constants of the projection (Sec. 4.1) derived from R and the centre.
 struct RowConst {
@@ -116,6 +128,9 @@ cudaError_t launch_fix_fp64(const uint8_t* desc, const double* mu, const double*
                             uint8_t* buckets, unsigned long long* n_reeval, cudaStream_t s);
 cudaError_t launch_build_tables(const uint8_t* buckets, const uint64_t* chunk_feat0, const uint32_t* chunk_len,
                                 uint32_t n_chunks, uint32_t n_tables, uint8_t* tables, cudaStream_t s);
+cudaError_t launch_build_join(const uint8_t* buckets, const uint32_t* codes, const uint64_t* img_f0,
+                              const uint32_t* img_n, const uint64_t* img_join, uint32_t n_images, uint32_t n_tables,
+                              uint8_t* join, cudaStream_t s);
 
 struct MatchArgs {
   const uint8_t* desc;
@@ -138,8 +153,18 @@ struct MatchArgs {
   uint32_t* tau_pair;        // speculative form, per pair: 0 = no guess yet, else (threshold + 1);
                              // learned as the largest k-th Hamming distance seen, kept across launches
   uint32_t tau_fixed;        // speculative form: do not learn (keep the values set by the host)
+  const uint8_t* join;       // bucket join: table buffer holding the bucket-sorted tables
+  uint32_t* jqueue;          // bucket join: [grid][na_max][JSEG] survivor lists
+  uint32_t* jhist;           // bucket join: [P][HBINS] k-th Hamming distances seen per pair
+  uint32_t na_max;           // bucket join: largest query image of the plan
   KParams kp;
 };
+// Bucket-join matching (batched schedule): calibration of missing per-pair
+// thresholds, then the join kernel over items = pairs.
+cudaError_t launch_join(const MatchArgs& a, uint32_t grid, cudaStream_t s);
+// Resident CTAs of the join for n_items pairs; 0 when the join does not apply
+// (band filter on, or the largest query image exceeds its shared memory).
+uint32_t join_grid(const KParams& kp, uint32_t na_max, uint32_t n_items);
 // Matching kernel launch.  spec = 0: direct register top-k (one pair per
 // launch); spec = 1: survivor queues with a speculative threshold (batched).
 cudaError_t launch_match(const MatchArgs& a, int spec, uint32_t grid, cudaStream_t s);

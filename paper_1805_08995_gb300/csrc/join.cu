@@ -1,0 +1,549 @@
+// Batched matching as a bucket join on the tensor cores: Steps 1-4 of
+// Sec. 3.1 (+ the Sec. 5 threshold tau) organised around the lookup tables.
+//
+// Step 1 pairs a query with exactly the candidates that share its bucket in
+// some table, so for table t and short code v the work is the dense block
+// (queries of A in bucket v) x (candidates of B in bucket v).  With the
+// bucket-sorted tables (codes stored inline) a warp takes one (t, v) block
+// and computes its Hamming distances (Step 2) as one +-1 contraction: with a
+// code bit mapped to +1 / -1, the dot product of two 128-bit codes is
+// 128 - 2 H.  The +-1 values are exact in FP8 (e4m3) and every partial sum is
+// an integer of magnitude <= 128, so mma.m16n8k32 (FP8 in, f16 accumulators)
+// gives H exactly.  The query side enters negated and the accumulators start
+// at 1152, so each result is 1024 + 2 H: in [1024, 2048) an f16 has unit
+// spacing, so its low ten bits are 2 H and the key needs no conversion.
+// Because the Hamming distance does not depend on the order of the bits, each
+// lane expands one 32-bit code word of its row / column into eight FP8
+// registers (register i, byte b <- bit 8b + i); rows and columns use the same
+// map.
+//
+// Keys H <= theta (theta: the pair's threshold guess, learned per pair from the
+// k-th distances of earlier launches, capped by the Sec. 5 tau) are appended to
+// the query's survivor list: a counter per query in shared memory, a list of
+// JSEG entries per query in global memory.  After the scan the CTA finalises
+// the pair's queries, one thread per query: the k smallest distinct survivors
+// (Step 3; a point met through several tables appears once), exact squared
+// distances with 8 lanes per 128-byte row (Step 4) and Lowe's ratio test.  A
+// query whose list overflowed, or that holds fewer than k distinct survivors
+// while the guess turned some candidate away, is left PENDING for the exact
+// fallback kernel, so results never depend on the guess.
+#include <cuda_fp16.h>
+
+#include "internal.h"
+
+namespace chx {
+
+constexpr int JT = 256;            // threads of a join CTA
+constexpr int CAL_SAMPLES = 128;   // calibration: sampled queries per pair
+constexpr uint32_t CAL_MARGIN = 1; // calibration: Hamming margin over the second largest sample
+constexpr int NTC = 4;             // candidate tiles (of 8) held in registers at a time
+
+template <int KC>
+__device__ __forceinline__ void jt_insert(uint32_t (&top)[KC], uint32_t k) {
+#pragma unroll
+  for (int s = 0; s < KC; ++s) {
+    const uint32_t t = top[s];
+    const bool dup = (t == k);
+    top[s] = min(t, k);
+    k = dup ? KEY_INF : max(t, k);
+  }
+}
+
+template <int KC>
+__device__ __forceinline__ uint32_t jt_kth(const uint32_t (&top)[KC], uint32_t K) {
+  uint32_t v = KEY_INF;
+#pragma unroll
+  for (int s = 0; s < KC; ++s)
+    if ((uint32_t)s + 1 == K) v = top[s];
+  return v;
+}
+
+__device__ __forceinline__ uint32_t jt_hamming(uint4 a, uint4 b) {
+  return __popc(a.x ^ b.x) + __popc(a.y ^ b.y) + __popc(a.z ^ b.z) + __popc(a.w ^ b.w);
+}
+
+struct JView {  // one image's bucket-sorted table t
+  const uint32_t* off;
+  const uint32_t* idx;
+  const uint4* rec;
+};
+
+__device__ __forceinline__ JView jview(const uint8_t* join, uint64_t base, uint32_t n, uint32_t t) {
+  const uint8_t* b = join + base + (uint64_t)t * join_block(n);
+  JView v;
+  v.off = reinterpret_cast<const uint32_t*>(b);
+  v.idx = reinterpret_cast<const uint32_t*>(b + 1040);
+  v.rec = reinterpret_cast<const uint4*>(b + 1040 + 4 * ((n + 3) / 4 * 4));
+  return v;
+}
+
+// Dynamic shared memory: survivor counters of the pair's queries, then the
+// finalisation's keys and distances.
+__host__ __device__ inline size_t join_smem_bytes(int KC, uint32_t na_max) {
+  return (size_t)4 * ((na_max + 3) / 4 * 4) + (size_t)2 * KC * JT * 4;
+}
+
+// One 32-bit code word as eight FP8 registers of +-1 (byte b of register i is
+// bit 8b + i of w; e4m3 0x38 = +1, 0xB8 = -1): bit 1 -> +1 (NEG = false) or
+// -1 (NEG = true); on = false gives zeros for padding rows and columns.
+template <bool NEG>
+__device__ __forceinline__ void pm1_expand(uint32_t w, bool on, uint32_t (&r)[8]) {
+  const uint32_t m = on ? 0x80808080u : 0u, c = on ? (NEG ? 0xB8B8B8B8u : 0x38383838u) : 0u;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) r[i] = NEG ? (((w << (7 - i)) & m) ^ c) : (((w << (7 - i)) & m) | c);
+}
+
+// D += A (16x32, FP8) * B (32x8, FP8), f16 accumulators: d0 holds row g,
+// d1 row g + 8 (columns 2 (lane % 4) and +1), g = lane / 4.
+__device__ __forceinline__ void mma_pm1(uint32_t& d0, uint32_t& d1, uint32_t a0, uint32_t a1, uint32_t a2,
+                                        uint32_t a3, uint32_t b0, uint32_t b1) {
+  asm("mma.sync.aligned.m16n8k32.row.col.f16.e4m3.e4m3.f16 {%0,%1}, {%2,%3,%4,%5}, {%6,%7}, {%0,%1};"
+      : "+r"(d0), "+r"(d1)
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ uint32_t le_mask(uint32_t d, __half2 t) {
+  __half2 h;
+  memcpy(&h, &d, 4);
+  return __hle2_mask(h, t);
+}
+
+constexpr uint32_t ACC0 = 0x64806480u;  // f16 (1152, 1152): results are 1024 + 2 H
+
+// Key H << 24 | j from the low / high f16 result (bits 0x6400 + 2 H).
+__device__ __forceinline__ uint32_t key_lo(uint32_t d, uint32_t j) { return ((d & 0x3FEu) << 23) | j; }
+__device__ __forceinline__ uint32_t key_hi(uint32_t d, uint32_t j) { return ((d & 0x03FE0000u) << 7) | j; }
+
+// Hamming threshold for a pair: the 99.5th percentile of the k-th distances
+// seen so far (histogram kept across launches), else the calibration / host
+// hint; 0 = none.  Computed by warp 0.
+__device__ __forceinline__ uint32_t pair_threshold(const MatchArgs& a, uint32_t p, int lane) {
+  const uint32_t* h = a.jhist + (size_t)p * HBINS;
+  uint32_t v[5], tot = 0;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const uint32_t b = lane * 5 + k;  // lanes own 5 consecutive bins
+    v[k] = b < HBINS ? *reinterpret_cast<const volatile uint32_t*>(h + b) : 0u;
+    tot += v[k];
+  }
+  uint32_t incl = tot;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t o = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+    if (lane >= d) incl += o;
+  }
+  const uint32_t all = __shfl_sync(0xFFFFFFFFu, incl, 31);
+  uint32_t guess = *reinterpret_cast<const volatile uint32_t*>(a.tau_pair + p);
+  if (!a.tau_fixed && all >= 64) {
+    const uint32_t want = all - all / 200;  // 99.5 %
+    uint32_t run = incl - tot, bin = 0xFFFFFFFFu;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      run += v[k];
+      if (bin == 0xFFFFFFFFu && run >= want) bin = lane * 5 + k;
+    }
+    uint32_t best = bin;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(0xFFFFFFFFu, best, o));
+    if (best != 0xFFFFFFFFu) guess = best + 1u;
+  }
+  return guess;
+}
+
+// Bucket offsets of join task `task` (table task / nbk, bucket task % nbk) in
+// both images; zeros past the last task.
+__device__ __forceinline__ void load_offsets(const uint8_t* join, const PairInfo& P, uint64_t ablk, uint64_t bblk,
+                                             uint32_t nbk, uint32_t ntask, uint32_t task, uint32_t (&o)[4]) {
+  o[0] = o[1] = o[2] = o[3] = 0u;
+  if (task < ntask) {
+    const uint32_t t = task / nbk, v = task - t * nbk;
+    const uint32_t* ao = reinterpret_cast<const uint32_t*>(join + P.ajoin + t * ablk) + v;
+    const uint32_t* bo = reinterpret_cast<const uint32_t*>(join + P.bjoin + t * bblk) + v;
+    o[0] = __ldg(ao);
+    o[1] = __ldg(ao + 1);
+    o[2] = __ldg(bo);
+    o[3] = __ldg(bo + 1);
+  }
+}
+
+// Appends a key to query qa's survivor list.
+__device__ __forceinline__ void jt_push(uint32_t* cnt_s, uint32_t* seg, uint32_t qa, uint32_t key) {
+  const uint32_t slot = atomicAdd(cnt_s + qa, 1u);
+  if (slot < JSEG) seg[(size_t)qa * JSEG + slot] = key;
+}
+
+template <int KC, bool TAU>
+__global__ void __launch_bounds__(JT, 2) k_join(MatchArgs a) {
+  extern __shared__ __align__(16) uint8_t jsm[];
+  __shared__ uint32_t s_item, s_tau, s_task;
+  __shared__ uint32_t s_hist[HBINS];
+  __shared__ PairInfo s_P;
+  const KParams kp = a.kp;
+  const uint32_t T = kp.n_tables, K = kp.top_k, nbk = 1u << kp.bits_per_table;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t g = (uint32_t)lane >> 2, l4 = (uint32_t)lane & 3u;
+  uint32_t* cnt_s = reinterpret_cast<uint32_t*>(jsm);
+  uint32_t* key_s = cnt_s + (a.na_max + 3) / 4 * 4;
+  uint32_t* dist_s = key_s + KC * JT;
+  uint32_t* seg = a.jqueue + (size_t)blockIdx.x * a.na_max * JSEG;
+  const uint32_t h_user = TAU ? kp.tau : 128u;  // Sec. 5: keys with H > tau are no candidates
+
+  for (;;) {
+    __syncthreads();
+    if (tid == 0) {
+      const uint32_t it0 = atomicAdd(a.item_ctr, 1u);
+      uint32_t p0 = 0xFFFFFFFFu;
+      if (it0 < a.n_items) {
+        p0 = a.items[it0].x;
+        s_P = a.pairs[p0];
+      }
+      s_item = p0;
+      s_task = 0;
+    }
+    for (uint32_t b = tid; b < HBINS; b += JT) s_hist[b] = 0;
+    __syncthreads();
+    const uint32_t it = s_item;  // pair index
+    if (it == 0xFFFFFFFFu) break;
+    if (warp == 0) {
+      const uint32_t gs = pair_threshold(a, it, lane);
+      if (lane == 0) s_tau = gs;
+    }
+    const PairInfo P = s_P;
+    for (uint32_t q = tid; q < P.nA; q += JT) cnt_s[q] = 0;
+    __syncthreads();
+    // survivors: H <= h_thr
+    uint32_t h_thr = h_user;
+    {
+      const uint32_t ts = s_tau;  // 0: no guess; else threshold + 1
+      if (ts != 0 && ts - 1u < h_thr) h_thr = ts - 1u;
+    }
+    const bool cut = h_thr < h_user;  // the guess may turn candidates away
+    const __half2 t2 = __float2half2_rn(1024.f + 2.f * (float)min(h_thr, 128u));
+    // the pair's two images: table t of image X starts at join + Xjoin + t * Xblk
+    const uint64_t ablk = join_block(P.nA), bblk = join_block(P.nB);
+    const uint64_t arec = 1040u + 4u * ((P.nA + 3) / 4 * 4), brec = 1040u + 4u * ((P.nB + 3) / 4 * 4);
+
+    // ---- scan: (table, bucket) blocks on the tensor cores, one warp per block ----
+    // The bucket offsets of the next block are loaded while the current one runs.
+    const uint32_t ntask = T * nbk;
+    uint32_t task = 0;
+    if (lane == 0) task = atomicAdd(&s_task, 1u);
+    task = __shfl_sync(0xFFFFFFFFu, task, 0);
+    uint32_t ob[4];  // off_A[v], off_A[v + 1], off_B[v], off_B[v + 1] of `task`
+    load_offsets(a.join, P, ablk, bblk, nbk, ntask, task, ob);
+    while (task < ntask) {
+      uint32_t nxt = 0;
+      if (lane == 0) nxt = atomicAdd(&s_task, 1u);
+      nxt = __shfl_sync(0xFFFFFFFFu, nxt, 0);
+      uint32_t onx[4];
+      load_offsets(a.join, P, ablk, bblk, nbk, ntask, nxt, onx);
+      const uint32_t t = task / nbk;
+      const uint8_t* Ab = a.join + P.ajoin + t * ablk;
+      const uint8_t* Bb = a.join + P.bjoin + t * bblk;
+      const uint32_t qs = ob[0], nq = ob[1] - ob[0];
+      const uint32_t cs = ob[2], nc = ob[3] - ob[2];
+      task = nxt;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) ob[k] = onx[k];
+      if (nq == 0 || nc == 0) continue;
+      const uint32_t* Aidx = reinterpret_cast<const uint32_t*>(Ab + 1040) + qs;
+      const uint32_t* Bidx = reinterpret_cast<const uint32_t*>(Bb + 1040) + cs;
+      const uint32_t* Aw = reinterpret_cast<const uint32_t*>(Ab + arec) + 4 * qs + l4;
+      const uint32_t* Bw = reinterpret_cast<const uint32_t*>(Bb + brec) + 4 * cs + l4;
+      for (uint32_t c0 = 0; c0 < nc; c0 += 8 * NTC) {
+        const uint32_t ntiles = min((uint32_t)NTC, (nc - c0 + 7) / 8);
+        uint32_t bf[NTC][8], jc[NTC][2];
+#pragma unroll
+        for (int n = 0; n < NTC; ++n) {
+          const uint32_t col = c0 + n * 8 + g;
+          const bool on = (uint32_t)n < ntiles && col < nc;
+          pm1_expand<false>(on ? __ldg(Bw + (size_t)col * 4) : 0u, on, bf[n]);
+          const uint32_t cc = c0 + n * 8 + 2 * l4;
+          jc[n][0] = ((uint32_t)n < ntiles && cc < nc) ? __ldg(Bidx + cc) : 0xFFFFFFFFu;
+          jc[n][1] = ((uint32_t)n < ntiles && cc + 1 < nc) ? __ldg(Bidx + cc + 1) : 0xFFFFFFFFu;
+        }
+        for (uint32_t r0 = 0; r0 < nq; r0 += 16) {
+          const uint32_t ra = r0 + g, rb = r0 + g + 8;
+          const bool va = ra < nq, vb = rb < nq;
+          uint32_t af[8], ag[8];
+          pm1_expand<true>(va ? __ldg(Aw + (size_t)ra * 4) : 0u, va, af);
+          pm1_expand<true>(vb ? __ldg(Aw + (size_t)rb * 4) : 0u, vb, ag);
+          const uint32_t qa = va ? __ldg(Aidx + ra) : 0u;
+          const uint32_t qb = vb ? __ldg(Aidx + rb) : 0u;
+#pragma unroll
+          for (int n = 0; n < NTC; ++n) {
+            if ((uint32_t)n >= ntiles) break;  // warp-uniform
+            uint32_t d0 = ACC0, d1 = ACC0;
+#pragma unroll
+            for (int s = 0; s < 4; ++s)
+              mma_pm1(d0, d1, af[2 * s], ag[2 * s], af[2 * s + 1], ag[2 * s + 1], bf[n][2 * s], bf[n][2 * s + 1]);
+            uint32_t m0 = le_mask(d0, t2), m1 = le_mask(d1, t2);
+            if (!va) m0 = 0u;
+            if (!vb) m1 = 0u;
+            if (m0 | m1) {
+              if ((m0 & 0xFFFFu) && jc[n][0] != 0xFFFFFFFFu) jt_push(cnt_s, seg, qa, key_lo(d0, jc[n][0]));
+              if ((m0 >> 16) && jc[n][1] != 0xFFFFFFFFu) jt_push(cnt_s, seg, qa, key_hi(d0, jc[n][1]));
+              if ((m1 & 0xFFFFu) && jc[n][0] != 0xFFFFFFFFu) jt_push(cnt_s, seg, qb, key_lo(d1, jc[n][0]));
+              if ((m1 >> 16) && jc[n][1] != 0xFFFFFFFFu) jt_push(cnt_s, seg, qb, key_hi(d1, jc[n][1]));
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();
+
+    // ---- finalise: top-k of the survivors, distances, ratio test ----
+    for (uint32_t q0 = 0; q0 < P.nA; q0 += JT) {
+      const uint32_t q = q0 + tid;
+      const bool valid = q < P.nA;
+      uint32_t top[KC];
+#pragma unroll
+      for (int s = 0; s < KC; ++s) top[s] = KEY_INF;
+      bool pending = false;
+      if (valid) {
+        const uint32_t n = cnt_s[q];
+        pending = n > JSEG;  // survivors were dropped
+        const uint4* ql = reinterpret_cast<const uint4*>(seg + (size_t)q * JSEG);
+        const uint32_t m = min(n, JSEG);
+        for (uint32_t e0 = 0; e0 < m; e0 += 16) {
+          uint4 x[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            x[i] = e0 + 4 * i < m ? ql[e0 / 4 + i] : make_uint4(KEY_INF, KEY_INF, KEY_INF, KEY_INF);
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const uint32_t kk[4] = {x[i].x, x[i].y, x[i].z, x[i].w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              if (e0 + 4 * i + u < m && kk[u] < top[KC - 1]) jt_insert<KC>(top, kk[u]);
+          }
+        }
+        const uint32_t kth = jt_kth<KC>(top, K);
+        if (!pending && kth == KEY_INF && cut) {
+          // fewer than k: exact only if no candidate was turned away by the guess
+          const uint2 qbk = __ldg(reinterpret_cast<const uint2*>(a.buckets) + P.a0 + q);
+          uint32_t nlook = 0;
+          for (uint32_t t = 0; t < T; ++t) {
+            const JView B = jview(a.join, P.bjoin, P.nB, t);
+            const uint32_t v = (t < 4 ? (qbk.x >> (8 * t)) : (qbk.y >> (8 * (t - 4)))) & 0xFFu;
+            nlook += __ldg(B.off + v + 1) - __ldg(B.off + v);
+          }
+          pending = nlook > n;
+        }
+        if (!pending && kth != KEY_INF && !a.tau_fixed) atomicAdd(s_hist + (kth >> 24), 1u);
+      }
+#pragma unroll
+      for (int s = 0; s < KC; ++s) key_s[s * JT + tid] = (valid && !pending) ? top[s] : KEY_INF;
+      __syncwarp();
+      const uint32_t wbase = warp * 32;
+      const int grp = lane >> 3, sub = lane & 7;
+      constexpr int DB = KC <= 10 ? KC : 8;  // candidate rows in flight per query
+      for (uint32_t qq0 = 0; qq0 < 32; qq0 += 4) {
+        const uint32_t qi = wbase + qq0 + grp;
+        const bool has = key_s[qi] != KEY_INF;
+        const uint64_t fa = P.a0 + q0 + qi;
+        uint4 av = make_uint4(0u, 0u, 0u, 0u);
+        if (has) av = __ldg(reinterpret_cast<const uint4*>(a.desc + fa * DIM) + sub);
+        for (uint32_t s0 = 0; s0 < K; s0 += DB) {
+          uint32_t key[DB];
+          uint4 bv[DB];
+#pragma unroll
+          for (int d = 0; d < DB; ++d) {
+            key[d] = (has && s0 + d < K) ? key_s[(s0 + d) * JT + qi] : KEY_INF;
+            bv[d] = make_uint4(0u, 0u, 0u, 0u);
+            if (key[d] != KEY_INF)
+              bv[d] = __ldg(reinterpret_cast<const uint4*>(a.desc + (P.b0 + (key[d] & 0xFFFFFFu)) * DIM) + sub);
+          }
+#pragma unroll
+          for (int d = 0; d < DB; ++d) {
+            uint32_t dot = 0;
+            dot = __dp4a(av.x, bv[d].x, dot);
+            dot = __dp4a(av.y, bv[d].y, dot);
+            dot = __dp4a(av.z, bv[d].z, dot);
+            dot = __dp4a(av.w, bv[d].w, dot);
+            dot += __shfl_xor_sync(0xFFFFFFFFu, dot, 1);
+            dot += __shfl_xor_sync(0xFFFFFFFFu, dot, 2);
+            dot += __shfl_xor_sync(0xFFFFFFFFu, dot, 4);
+            if (sub == 0 && key[d] != KEY_INF) {
+              const uint64_t fb = P.b0 + (key[d] & 0xFFFFFFu);
+              dist_s[(s0 + d) * JT + qi] = __ldg(a.sqnorm + fa) + __ldg(a.sqnorm + fb) - 2u * dot;
+            }
+          }
+        }
+      }
+      __syncwarp();
+      bool matched = false;
+      if (valid) {
+        uint32_t nv = 0, d1 = 0xFFFFFFFFu, d2 = 0xFFFFFFFFu, j1 = NO_MATCH;
+        for (uint32_t s = 0; s < K; ++s) {
+          const uint32_t key = key_s[s * JT + tid];
+          if (key == KEY_INF) continue;
+          ++nv;
+          const uint32_t d = dist_s[s * JT + tid], j = key & 0xFFFFFFu;
+          if (d < d1 || (d == d1 && j < j1)) {
+            d2 = d1;
+            d1 = d;
+            j1 = j;
+          } else if (d < d2) {
+            d2 = d;
+          }
+        }
+        matched = nv >= 2 && (uint64_t)kp.ratio_den * kp.ratio_den * d1 < (uint64_t)kp.ratio_num * kp.ratio_num * d2;
+        a.res[P.qbase + q] = pending ? PENDING : (matched ? j1 : NO_MATCH);
+      }
+      const uint32_t bal = __ballot_sync(0xFFFFFFFFu, matched);
+      if (lane == 0 && bal) atomicAdd(a.pair_cnt + it, (unsigned long long)__popc(bal));
+      __syncwarp();
+    }
+    __syncthreads();
+    if (!a.tau_fixed)
+      for (uint32_t b = tid; b < HBINS; b += JT)
+        if (s_hist[b]) atomicAdd(a.jhist + (size_t)it * HBINS + b, s_hist[b]);
+  }
+}
+
+// Threshold guess for pairs that have none yet, from CAL_SAMPLES sampled
+// queries (one CTA per pair, one thread per query): the exact k-th Hamming
+// distance of each, then the second largest of them plus CAL_MARGIN.  Only a
+// performance hint; results never depend on it.
+template <int KC, bool TAU>
+__global__ void __launch_bounds__(CAL_SAMPLES) k_join_calibrate(MatchArgs a) {
+  __shared__ uint32_t s_top[CAL_SAMPLES / 32][2];
+  const KParams kp = a.kp;
+  const uint32_t T = kp.n_tables, K = kp.top_k;
+  const uint32_t thr_user = TAU ? ((kp.tau + 1u) << 24) : KEY_INF;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (uint32_t p = blockIdx.x; p < a.n_pairs; p += gridDim.x) {
+    if (*reinterpret_cast<volatile uint32_t*>(a.tau_pair + p) != 0) continue;  // uniform over the CTA
+    const PairInfo P = a.pairs[p];
+    if (P.nA == 0 || P.nB == 0) continue;
+    const uint32_t q = (uint32_t)(((uint64_t)threadIdx.x * P.nA) / CAL_SAMPLES);
+    const uint4 qc = __ldg(reinterpret_cast<const uint4*>(a.codes) + P.a0 + q);
+    const uint2 qb = __ldg(reinterpret_cast<const uint2*>(a.buckets) + P.a0 + q);
+    uint32_t top[KC];
+#pragma unroll
+    for (int s = 0; s < KC; ++s) top[s] = KEY_INF;
+    for (uint32_t t = 0; t < T; ++t) {
+      const JView B = jview(a.join, P.bjoin, P.nB, t);
+      const uint32_t v = (t < 4 ? (qb.x >> (8 * t)) : (qb.y >> (8 * (t - 4)))) & 0xFFu;
+      const uint32_t cs = __ldg(B.off + v), ce = __ldg(B.off + v + 1);
+      for (uint32_t c = cs; c < ce; ++c) {
+        const uint32_t key = (jt_hamming(__ldg(B.rec + c), qc) << 24) | __ldg(B.idx + c);
+        if (TAU && key >= thr_user) continue;
+        if (key < top[KC - 1]) jt_insert<KC>(top, key);
+      }
+    }
+    const uint32_t kth = jt_kth<KC>(top, K);
+    const uint32_t hk = kth == KEY_INF ? 0xFFFFFFFFu : (kth >> 24);  // fewer than k candidates: largest
+    // the two largest values of the warp, then of the CTA
+    uint32_t m1 = hk;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m1 = max(m1, __shfl_xor_sync(0xFFFFFFFFu, m1, o));
+    const uint32_t eq = __ballot_sync(0xFFFFFFFFu, hk == m1);
+    uint32_t m2 = (hk == m1 && (eq & ((1u << lane) - 1u)) == 0) ? 0u : hk;  // drop one copy of the maximum
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m2 = max(m2, __shfl_xor_sync(0xFFFFFFFFu, m2, o));
+    if (lane == 0) {
+      s_top[warp][0] = m1;
+      s_top[warp][1] = m2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint32_t b1 = 0, b2 = 0;
+      for (int w = 0; w < CAL_SAMPLES / 32; ++w)
+        for (int k = 0; k < 2; ++k) {
+          const uint32_t x = s_top[w][k];
+          if (x > b1) {
+            b2 = b1;
+            b1 = x;
+          } else if (x > b2) {
+            b2 = x;
+          }
+        }
+      // two or more samples with fewer than k candidates: leave the pair without a guess
+      if (b2 != 0xFFFFFFFFu) atomicMax(a.tau_pair + p, b2 + CAL_MARGIN + 1u);
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+namespace {
+
+template <int KC, bool TAU>
+cudaError_t run_join(const MatchArgs* a, uint32_t grid, cudaStream_t s, uint32_t* occ, uint32_t na_max,
+                     bool calibrate) {
+  static int attr_dev = -1;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (attr_dev != dev) {
+    int optin = 0;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_join<KC, TAU>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - 2048);
+    if (e != cudaSuccess) return e;
+    attr_dev = dev;
+  }
+  const size_t smem = join_smem_bytes(KC, na_max);
+  if (occ) {
+    int nb = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_join<KC, TAU>, JT, smem);
+    *occ = (uint32_t)(nb > 0 ? nb : 0);
+    return e;
+  }
+  if (calibrate) {
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const uint32_t want = a->n_pairs;
+    k_join_calibrate<KC, TAU><<<want < (uint32_t)nsm * 8 ? want : (uint32_t)nsm * 8, CAL_SAMPLES, 0, s>>>(*a);
+    return cudaGetLastError();
+  }
+  k_join<KC, TAU><<<grid, JT, smem, s>>>(*a);
+  return cudaGetLastError();
+}
+
+template <int KC>
+cudaError_t run_join_kc(const MatchArgs* a, bool tau, uint32_t grid, cudaStream_t s, uint32_t* occ, uint32_t na_max,
+                        bool cal) {
+  return tau ? run_join<KC, true>(a, grid, s, occ, na_max, cal) : run_join<KC, false>(a, grid, s, occ, na_max, cal);
+}
+
+cudaError_t join_dispatch(uint32_t k, const MatchArgs* a, bool tau, uint32_t grid, cudaStream_t s, uint32_t* occ,
+                          uint32_t na_max, bool cal) {
+  if (k <= 4) return run_join_kc<4>(a, tau, grid, s, occ, na_max, cal);
+  if (k <= 8) return run_join_kc<8>(a, tau, grid, s, occ, na_max, cal);
+  if (k <= 10) return run_join_kc<10>(a, tau, grid, s, occ, na_max, cal);
+  if (k <= 16) return run_join_kc<16>(a, tau, grid, s, occ, na_max, cal);
+  return run_join_kc<32>(a, tau, grid, s, occ, na_max, cal);
+}
+
+int kc_of(uint32_t k) { return k <= 4 ? 4 : k <= 8 ? 8 : k <= 10 ? 10 : k <= 16 ? 16 : 32; }
+
+}  // namespace
+
+uint32_t join_grid(const KParams& kp, uint32_t na_max, uint32_t n_items) {
+  if (kp.epi_px >= 0.0) return 0;  // the band form is matched by the speculative kernel
+  int dev = 0, nsm = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (join_smem_bytes(kc_of(kp.top_k), na_max) + 4096 > (size_t)optin) return 0;
+  uint32_t occ = 0;
+  if (join_dispatch(kp.top_k, nullptr, kp.tau < kp.code_bits, 0, 0, &occ, na_max, false) != cudaSuccess) {
+    cudaGetLastError();
+    occ = 0;
+  }
+  const uint64_t gr = (uint64_t)nsm * occ;
+  return (uint32_t)(n_items < gr ? n_items : gr);
+}
+
+cudaError_t launch_join(const MatchArgs& a, uint32_t grid, cudaStream_t s) {
+  if (a.n_items == 0 || grid == 0) return cudaSuccess;
+  const bool tau = a.kp.tau < a.kp.code_bits;
+  cudaError_t e = join_dispatch(a.kp.top_k, &a, tau, grid, s, nullptr, a.na_max, true);
+  if (e != cudaSuccess) return e;
+  return join_dispatch(a.kp.top_k, &a, tau, grid, s, nullptr, a.na_max, false);
+}
+
+}  // namespace chx

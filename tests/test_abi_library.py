@@ -59,7 +59,14 @@ def test_tables_bytes_host_arithmetic(lib):
     p = ch.cashash_default_params()
     off = np.array([0, 3968, 3969, 3969, 20000], np.uint64)
     # chunks of 3968 features: 1 + 1 + 0 + 5 = 7; each holds 6 tables x (264 + 3968) uint16
-    assert ch.cashash_tables_bytes(p, off) == 7 * 6 * (264 + 3968) * 2
+    chunked = 7 * 6 * (264 + 3968) * 2
+    # bucket-sorted tables: per image and table 257(+3) uint32 offsets, uint32 indices, 16-byte codes
+
+    def block(n):
+        return 1040 + 4 * ((n + 3) // 4 * 4) + 16 * n
+
+    joined = 6 * sum(block(n) for n in (3968, 1, 0, 16031))
+    assert ch.cashash_tables_bytes(p, off) == chunked + joined
     bad = ch.cashash_default_params(n_tables=0)
     assert ch.cashash_tables_bytes(bad, off) == 0
     assert ch.cashash_tables_bytes(p, np.array([0, 5, 3], np.uint64)) == 0

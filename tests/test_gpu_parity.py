@@ -136,11 +136,14 @@ def test_parameter_variants(ch, orc, pk, sched):
     check_case(ch, orc, s, _pairs(sizes), schedule=sched, **pk)
 
 
-@pytest.mark.parametrize("hint,fixed", [(0, True), (30, True), (50, True), (53, True), (56, False), (0, False)])
+@pytest.mark.parametrize("hint,fixed", [(0, True), (30, True), (50, True), (53, True), (56, False), (0, False),
+                                        (64, True), (100, True)])
 def test_speculative_threshold_never_changes_results(ch, orc, hint, fixed):
     """The batched kernel's Hamming threshold is a guess; queries it starves
     are re-matched exactly.  Forcing bad guesses (0: every query falls back;
-    near the median k-th distance: about half do) must not change a match."""
+    near the median k-th distance: about half do; 64 and above: padding rows
+    of the tensor-core tiles pass the compare and must be masked, and most
+    survivor lists overflow) must not change a match."""
     sizes = [2600, 4100, 0, 900, 5200]
     s = synth.random_set(707, sizes)
     pairs = _pairs(sizes)
@@ -163,6 +166,47 @@ def test_speculative_threshold_never_changes_results(ch, orc, hint, fixed):
         off = moff.cpu().numpy().astype(np.uint64)
         assert np.array_equal(off, eoff)
         assert np.array_equal(mt[:int(off[-1])].cpu().numpy().view(np.uint32), emt)
+    plan.close()
+    ctx.close()
+
+
+@pytest.mark.parametrize("case", ["join", "large_image", "band"])
+def test_batched_kernel_choice(ch, orc, case):
+    """The batched schedule runs the tensor-core bucket join (calibration +
+    join + fallback + scan + compaction = 5 launches) unless the band is on or
+    a query image exceeds the join's shared-memory counters; then the
+    speculative per-query kernel (4 launches).  Both match the oracle."""
+    import math
+    pk = dict(schedule=1)
+    if case == "band":
+        s = synth.epipolar_set(43, n_views=4, n_points=9000, arc=2 * math.pi * 4 / 250, z_max=0.355)
+        pairs = np.concatenate([s.pairs, s.pairs[:, ::-1]])
+        s.F = np.concatenate([s.F, s.F.reshape(-1, 3, 3).transpose(0, 2, 1).reshape(-1, 9)])
+        pk["epi_px"] = 4.0
+    else:
+        sizes = [3000, 2500, 700] if case == "join" else [56000, 1500]
+        s = synth.random_set(808, sizes)
+        pairs = _pairs(sizes) if case == "join" else np.array([[0, 1], [1, 0]], np.uint32)
+    p = ch.cashash_default_params(**pk)
+    ctx = ch.cashash_create(p, s.R)
+    ds = ch.DeviceSet(p, s.img_off, s.desc, s.kpts)
+    ch.cashash_build_codes(ctx, ds)
+    plan = ch.cashash_plan_create(ctx, ds, pairs)
+    P = len(pairs)
+    cap = int(s.sizes()[pairs[:, 0]].sum())
+    moff = torch.zeros(P + 1, dtype=torch.int64, device="cuda")
+    mt = torch.zeros((cap, 2), dtype=torch.int32, device="cuda")
+    F = None if s.F is None else torch.from_numpy(np.ascontiguousarray(s.F)).cuda()
+    n0 = ch.cashash_get_stats(ctx)["n_launches"]
+    ch.cashash_match_plan(ctx, plan, moff, mt, cap, F=F)
+    assert ch.cashash_sync_status(ctx) == ch.CASHASH_OK
+    assert ch.cashash_get_stats(ctx)["n_launches"] - n0 == (5 if case == "join" else 4)
+    po = oparams(orc, pk)
+    mu, codes, buckets = oracle_codes(orc, s.desc, s.R, po)
+    eoff, emt = orc.match_pairs(s.desc, s.img_off, codes, buckets, pairs, po, F=s.F, kpts=s.kpts)
+    off = moff.cpu().numpy().astype(np.uint64)
+    assert np.array_equal(off, eoff)
+    assert np.array_equal(mt[:int(off[-1])].cpu().numpy().view(np.uint32), emt)
     plan.close()
     ctx.close()
 
@@ -196,6 +240,38 @@ def test_lookup_tables_are_the_bucket_sets(ch, orc):
                     got = idx[off[v]:off[v + 1]]
                     assert np.array_equal(got, np.nonzero(bb == v)[0])
             k += 1
+    ctx.close()
+
+
+def test_bucket_sorted_tables(ch, orc):
+    """The bucket-sorted tables (after the chunked ones): per image and table,
+    offsets of the 256 buckets, the features of each bucket in index order,
+    and each feature's 128-bit code inline."""
+    sizes = [5000, 10, 0, 3968, 7937]
+    s = synth.random_set(304, sizes)
+    p = ch.cashash_default_params()
+    ctx = ch.cashash_create(p, s.R)
+    ds = ch.DeviceSet(p, s.img_off, s.desc)
+    ch.cashash_build_codes(ctx, ds)
+    torch.cuda.synchronize()
+    raw = ds.tables.cpu().numpy()
+    codes, buckets = ds.codes_np(), ds.buckets_np(6)
+    n_chunks = sum((n + JC - 1) // JC for n in sizes)
+    o = max(n_chunks, 1) * 6 * (OFF_STRIDE + JC) * 2
+    for i, n in enumerate(sizes):
+        a0 = int(s.img_off[i])
+        blk = 1040 + 4 * ((n + 3) // 4 * 4) + 16 * n
+        for t in range(6):
+            b = raw[o + t * blk:o + (t + 1) * blk]
+            off = b[:1040].view(np.uint32)[:257].astype(np.int64)
+            idx = b[1040:1040 + 4 * n].view(np.uint32)
+            rec = b[1040 + 4 * ((n + 3) // 4 * 4):].view(np.uint32).reshape(-1, 4)
+            exp_off = np.concatenate([[0], np.cumsum(np.bincount(buckets[a0:a0 + n, t], minlength=256))])
+            assert np.array_equal(off, exp_off)
+            order = np.argsort(buckets[a0:a0 + n, t], kind="stable")
+            assert np.array_equal(idx, order)
+            assert np.array_equal(rec, codes[a0 + order])
+        o += 6 * blk
     ctx.close()
 
 
