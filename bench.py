@@ -37,6 +37,18 @@ FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0
 N_SM = 152
 POPC_PER_CLK_SM = 16          # 32-bit population counts per clock per SM (measured 15.96)
 L2_FLUSH_BYTES = 256 << 20
+# DRAM traffic per lookup entry of the matching kernel, from the ncu capture
+# summarised in profiles/ (valid only for the kernel source it was taken on).
+PROFILED_TRAFFIC = {}
+
+
+def source_sha256(rel: str):
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            return hashlib.sha256(f.read()).hexdigest()
+    except OSError:
+        return None
 
 
 def peaks():
@@ -317,23 +329,39 @@ def run_ours(args):
         t_max = float(tt.item())
     value = P * world * args.steps / t_max
 
-    # dominant kernel: the matching kernel; its work counted by the method's
-    # lookup entries (Step 1), one 128-bit Hamming distance = 4 popcounts each
+    # dominant kernel: the matching kernel (stage "match" times it alone); its
+    # work counted by the method's lookup entries (Step 1): one 128-bit Hamming
+    # distance each.  Peak: the CUDA-core ceiling of that step, 4 POPC per entry
+    # at 16 POPC/clk/SM; the bucket join computes the distances on the tensor
+    # cores instead (tensor_view) and is limited by its integer ALU / issue work.
     pk = peaks()
     T, m = p.n_tables, p.bits_per_table
     buckets = ds.buckets_np(T)
     entries = lookup_entries(buckets, s.img_off, s.pairs, T, m)
     t_match = statistics.mean(stage_ms["match"]) / 1e3
-    popc_rate = 4.0 * entries / t_match
-    popc_peak = POPC_PER_CLK_SM * N_SM * pk.get("sm_max_mhz", 2070.0) * 1e6
+    kernel = "k_join" if stage_ms["calibrate"] else "k_match"
+    sm_mhz = pk.get("sm_max_mhz", 2070.0)
+    ent_peak = POPC_PER_CLK_SM / 4.0 * N_SM * sm_mhz * 1e6
+    ent_rate = entries / t_match
+    fp8_peak = 2.0 * pk["bf16_tflops"] * 1e12  # nominal FP8 / BF16 dense ratio 4.5 / 2.25
+    traffic = None
+    prof = PROFILED_TRAFFIC.get(kernel)
+    if prof and prof["sha256"] == source_sha256(prof["source"]):
+        traffic = prof["bytes_per_entry"] * entries
     # touched-bytes view (per query: candidate codes + indices, k rows, query, offsets)
     touched = 20.0 * entries + float(s.sizes()[s.pairs[:, 0]].sum()) * (10 * 128 + 128 + 16 + 8 + 48)
-    roofline = {"bound": "alu", "achieved": popc_rate / 1e12, "peak": popc_peak / 1e12, "unit": "Tpopc/s",
-                "frac": popc_rate / popc_peak, "traffic": None, "kernel": "k_match",
+    roofline = {"bound": "alu", "achieved": ent_rate / 1e9, "peak": ent_peak / 1e9, "unit": "Gentries/s",
+                "frac": ent_rate / ent_peak, "traffic": traffic, "kernel": kernel,
                 "units_per_launch": entries, "unit_def": "lookup-table entries (one 128-bit Hamming each)",
                 "kernel_ms": t_match * 1e3,
-                "peak_def": "16 popc/clk/SM x 152 SMs x %.0f MHz (sm_max_mhz, %s)" % (
-                    pk.get("sm_max_mhz", 2070.0), pk["source"]),
+                "peak_def": "CUDA-core Hamming ceiling: 16 POPC/clk/SM / 4 POPC per entry x 152 SMs x %.0f MHz "
+                            "(sm_max_mhz, %s)" % (sm_mhz, pk["source"]),
+                "traffic_def": "dram bytes read + written per launch, per-entry figure of an ncu capture "
+                               "scaled by the entries; null when the kernel source differs from the profiled one",
+                "tensor_view": {"achieved_tflops": 256.0 * entries / t_match / 1e12,
+                                "peak_tflops": fp8_peak / 1e12,
+                                "frac": 256.0 * entries / t_match / fp8_peak,
+                                "note": "+-1 FP8 contraction, 2 x 128 flop per entry; peak = 2 x measured BF16"},
                 "hbm_view": {"touched_gbs": touched / t_match / 1e9,
                              "frac_of_hbm": touched / t_match / 1e9 / pk["hbm_gbs"],
                              "note": "bytes the method touches per query, mostly served from shared memory / L2"}}
@@ -398,9 +426,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="config1", choices=["config0", "config1", "config3"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16"])
     ap.add_argument("--schedule", default="persistent", choices=["persistent", "per_pair"])
-    ap.add_argument("--ref-pairs", type=int, default=480)
+    ap.add_argument("--ref-pairs", type=int, default=1200)
     ap.add_argument("--max-pairs", type=int, default=0, help="match only the first N pairs (profiling case)")
     ap.add_argument("--thresholds", default="learned", choices=["learned", "fresh"],
                     help="fresh: clear the learned per-pair Hamming thresholds before every timed step")

@@ -243,6 +243,8 @@ enum {
   CASHASH_STAGE_TABLES = 3,     /* lookup tables of Step 1 */
   CASHASH_STAGE_MATCH = 4,      /* matching kernel(s): Steps 1-4 */
   CASHASH_STAGE_COMPACT = 5,    /* per-pair offsets and compaction of the match lists */
+  CASHASH_STAGE_CALIBRATE = 6,  /* batched schedule: per-pair Hamming threshold guesses */
+  CASHASH_STAGE_FALLBACK = 7,   /* batched schedule: exact re-matching of the queries left pending */
   CASHASH_N_STAGES = 8
 };
 

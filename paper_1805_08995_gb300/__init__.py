@@ -45,7 +45,7 @@ class cashash_set(C.Structure):
 
 
 N_STAGES = 8
-STAGES = ("centre", "project", "reeval", "tables", "match", "compact")
+STAGES = ("centre", "project", "reeval", "tables", "match", "compact", "calibrate", "fallback")
 
 
 class cashash_stats(C.Structure):

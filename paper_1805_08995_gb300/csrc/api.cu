@@ -582,10 +582,21 @@ int cashash_plan_create(cashash_ctx* c, const cashash_set* s, const uint32_t* pa
     pl->join = pl->grid > 0;
   }
   if (pl->join) {
-    // bucket join: one item per pair, the largest (N_A * N_B) first
+    // bucket join: one item per pair.  The resident CTAs take consecutive
+    // items, so the pairs are ordered by tiles of S x S images (S^2 about the
+    // number of resident CTAs): the pairs in flight then share about 2 S
+    // images, whose descriptors and tables stay in L2.  Within a tile the
+    // largest (N_A * N_B) pairs come first.
+    const uint32_t S = std::max<uint32_t>(1, (uint32_t)std::lround(std::sqrt((double)pl->grid)));
+    std::vector<uint64_t> tkey(P);
+    for (uint32_t i = 0; i < P; ++i) {
+      const uint32_t a = pairs_host[2 * (size_t)i], b = pairs_host[2 * (size_t)i + 1];
+      tkey[i] = ((uint64_t)(std::min(a, b) / S) << 32) | (std::max(a, b) / S);
+    }
     std::vector<uint32_t> order(P);
     for (uint32_t i = 0; i < P; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
+      if (tkey[x] != tkey[y]) return tkey[x] < tkey[y];
       return (uint64_t)info[x].nA * info[x].nB > (uint64_t)info[y].nA * info[y].nB;
     });
     for (uint32_t i : order) items.push_back(make_uint2(i, 0u));
@@ -677,24 +688,32 @@ int enqueue_match(cashash_ctx* c, cashash_plan* pl, const double* F_dev, uint64_
   a.jhist = pl->d_jhist;
   a.na_max = pl->na_max;
   a.kp = c->kp;
-  {
-    StageTimer tm(c, CASHASH_STAGE_MATCH, stream, capturing);
-    CK(cudaMemsetAsync(pl->d_item_ctr, 0, sizeof(unsigned int) * ((size_t)P + 1), stream));
-    if (pl->persistent) {
-      a.items = pl->d_items;
-      a.n_items = pl->n_items;
-      a.item_ctr = pl->d_item_ctr + P;
+  CK(cudaMemsetAsync(pl->d_item_ctr, 0, sizeof(unsigned int) * ((size_t)P + 1), stream));
+  if (pl->persistent) {
+    a.items = pl->d_items;
+    a.n_items = pl->n_items;
+    a.item_ctr = pl->d_item_ctr + P;
+    if (pl->join) {
+      StageTimer tm(c, CASHASH_STAGE_CALIBRATE, stream, capturing);
+      CK(launch_join_calibrate(a, stream));
+    }
+    {
+      StageTimer tm(c, CASHASH_STAGE_MATCH, stream, capturing);
       if (pl->join) CK(launch_join(a, pl->grid, stream));
       else CK(launch_match(a, 1, pl->grid, stream));
+    }
+    {
+      StageTimer tm(c, CASHASH_STAGE_FALLBACK, stream, capturing);
       CK(launch_match_fallback(a, stream));
-    } else {
-      for (uint32_t i = 0; i < P; ++i) {
-        if (!pl->count[i]) continue;
-        a.items = pl->d_items + pl->first[i];
-        a.n_items = pl->count[i];
-        a.item_ctr = pl->d_item_ctr + i;
-        CK(launch_match(a, 0, std::min(pl->count[i], pl->occ_grid), stream));
-      }
+    }
+  } else {
+    StageTimer tm(c, CASHASH_STAGE_MATCH, stream, capturing);
+    for (uint32_t i = 0; i < P; ++i) {
+      if (!pl->count[i]) continue;
+      a.items = pl->d_items + pl->first[i];
+      a.n_items = pl->count[i];
+      a.item_ctr = pl->d_item_ctr + i;
+      CK(launch_match(a, 0, std::min(pl->count[i], pl->occ_grid), stream));
     }
   }
   {
@@ -726,6 +745,7 @@ int cashash_match_plan(cashash_ctx* c, cashash_plan* pl, const double* F_dev, ui
   if ((reinterpret_cast<uintptr_t>(match_off) & 7) || (reinterpret_cast<uintptr_t>(matches) & 3)) return CASHASH_EINVAL;
   CK(cudaSetDevice(c->device));
   c->ev_used[CASHASH_STAGE_MATCH] = c->ev_used[CASHASH_STAGE_COMPACT] = 0;
+  c->ev_used[CASHASH_STAGE_CALIBRATE] = c->ev_used[CASHASH_STAGE_FALLBACK] = 0;
   if (pl->persistent) {
     const bool same = pl->gexec && pl->g_F == F_dev && pl->g_moff == match_off && pl->g_mt == matches &&
                       pl->g_cap == cap && pl->g_prof == c->profiling;
@@ -754,6 +774,8 @@ int cashash_match_plan(cashash_ctx* c, cashash_plan* pl, const double* F_dev, ui
     CK(cudaGraphLaunch(pl->gexec, stream));
     if (c->profiling)  // the graph holds the stage events as external event-record nodes
       c->ev_used[CASHASH_STAGE_MATCH] = c->ev_used[CASHASH_STAGE_COMPACT] = 1;
+      c->ev_used[CASHASH_STAGE_FALLBACK] = 1;
+      if (pl->join) c->ev_used[CASHASH_STAGE_CALIBRATE] = 1;
   } else {
     const int st = enqueue_match(c, pl, F_dev, match_off, matches, cap, stream, false);
     if (st != CASHASH_OK) return st;

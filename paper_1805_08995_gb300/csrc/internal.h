@@ -160,7 +160,8 @@ struct MatchArgs {
   KParams kp;
 };
 // Bucket-join matching (batched schedule): calibration of missing per-pair
-// thresholds, then the join kernel over items = pairs.
+// thresholds (launch_join_calibrate), then the join kernel over items = pairs.
+cudaError_t launch_join_calibrate(const MatchArgs& a, cudaStream_t s);
 cudaError_t launch_join(const MatchArgs& a, uint32_t grid, cudaStream_t s);
 // Resident CTAs of the join for n_items pairs; 0 when the join does not apply
 // (band filter on, or the largest query image exceeds its shared memory).

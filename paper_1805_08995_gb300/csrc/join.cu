@@ -166,12 +166,6 @@ __device__ __forceinline__ void load_offsets(const uint8_t* join, const PairInfo
   }
 }
 
-// Appends a key to query qa's survivor list.
-__device__ __forceinline__ void jt_push(uint32_t* cnt_s, uint32_t* seg, uint32_t qa, uint32_t key) {
-  const uint32_t slot = atomicAdd(cnt_s + qa, 1u);
-  if (slot < JSEG) seg[(size_t)qa * JSEG + slot] = key;
-}
-
 template <int KC, bool TAU>
 __global__ void __launch_bounds__(JT, 2) k_join(MatchArgs a) {
   extern __shared__ __align__(16) uint8_t jsm[];
@@ -252,40 +246,75 @@ __global__ void __launch_bounds__(JT, 2) k_join(MatchArgs a) {
       const uint32_t* Bw = reinterpret_cast<const uint32_t*>(Bb + brec) + 4 * cs + l4;
       for (uint32_t c0 = 0; c0 < nc; c0 += 8 * NTC) {
         const uint32_t ntiles = min((uint32_t)NTC, (nc - c0 + 7) / 8);
-        uint32_t bf[NTC][8], jc[NTC][2];
+        uint32_t bf[NTC][8], jc[NTC][2], jok = 0;  // jok bit 2n + c: column 2 (lane % 4) + c of tile n exists
 #pragma unroll
         for (int n = 0; n < NTC; ++n) {
           const uint32_t col = c0 + n * 8 + g;
           const bool on = (uint32_t)n < ntiles && col < nc;
           pm1_expand<false>(on ? __ldg(Bw + (size_t)col * 4) : 0u, on, bf[n]);
           const uint32_t cc = c0 + n * 8 + 2 * l4;
-          jc[n][0] = ((uint32_t)n < ntiles && cc < nc) ? __ldg(Bidx + cc) : 0xFFFFFFFFu;
-          jc[n][1] = ((uint32_t)n < ntiles && cc + 1 < nc) ? __ldg(Bidx + cc + 1) : 0xFFFFFFFFu;
+          const bool o0 = (uint32_t)n < ntiles && cc < nc, o1 = (uint32_t)n < ntiles && cc + 1 < nc;
+          jc[n][0] = o0 ? __ldg(Bidx + cc) : 0u;
+          jc[n][1] = o1 ? __ldg(Bidx + cc + 1) : 0u;
+          jok |= ((o0 ? 1u : 0u) | (o1 ? 2u : 0u)) << (2 * n);
         }
+        // rows g and g + 8 of the first row tile; each iteration loads the next tile's
+        uint32_t wa = g < nq ? __ldg(Aw + (size_t)g * 4) : 0u;
+        uint32_t wb = g + 8 < nq ? __ldg(Aw + (size_t)(g + 8) * 4) : 0u;
+        uint32_t qa = g < nq ? __ldg(Aidx + g) : 0u;
+        uint32_t qb = g + 8 < nq ? __ldg(Aidx + g + 8) : 0u;
         for (uint32_t r0 = 0; r0 < nq; r0 += 16) {
-          const uint32_t ra = r0 + g, rb = r0 + g + 8;
-          const bool va = ra < nq, vb = rb < nq;
+          const bool va = r0 + g < nq, vb = r0 + g + 8 < nq;
           uint32_t af[8], ag[8];
-          pm1_expand<true>(va ? __ldg(Aw + (size_t)ra * 4) : 0u, va, af);
-          pm1_expand<true>(vb ? __ldg(Aw + (size_t)rb * 4) : 0u, vb, ag);
-          const uint32_t qa = va ? __ldg(Aidx + ra) : 0u;
-          const uint32_t qb = vb ? __ldg(Aidx + rb) : 0u;
+          pm1_expand<true>(wa, va, af);
+          pm1_expand<true>(wb, vb, ag);
+          const uint32_t qa_c = qa, qb_c = qb;
+          {
+            const uint32_t ra = r0 + 16 + g, rb = r0 + 24 + g;
+            wa = ra < nq ? __ldg(Aw + (size_t)ra * 4) : 0u;
+            wb = rb < nq ? __ldg(Aw + (size_t)rb * 4) : 0u;
+            qa = ra < nq ? __ldg(Aidx + ra) : 0u;
+            qb = rb < nq ? __ldg(Aidx + rb) : 0u;
+          }
+          uint32_t d[NTC][2];
+          uint32_t acc_a = 0, acc_b = 0;  // survivors: bit 2n (low f16 of tile n) and bit 17 + 2n (high)
 #pragma unroll
           for (int n = 0; n < NTC; ++n) {
-            if ((uint32_t)n >= ntiles) break;  // warp-uniform
-            uint32_t d0 = ACC0, d1 = ACC0;
+            d[n][0] = d[n][1] = ACC0;
+            if ((uint32_t)n < ntiles) {  // warp-uniform
 #pragma unroll
-            for (int s = 0; s < 4; ++s)
-              mma_pm1(d0, d1, af[2 * s], ag[2 * s], af[2 * s + 1], ag[2 * s + 1], bf[n][2 * s], bf[n][2 * s + 1]);
-            uint32_t m0 = le_mask(d0, t2), m1 = le_mask(d1, t2);
-            if (!va) m0 = 0u;
-            if (!vb) m1 = 0u;
-            if (m0 | m1) {
-              if ((m0 & 0xFFFFu) && jc[n][0] != 0xFFFFFFFFu) jt_push(cnt_s, seg, qa, key_lo(d0, jc[n][0]));
-              if ((m0 >> 16) && jc[n][1] != 0xFFFFFFFFu) jt_push(cnt_s, seg, qa, key_hi(d0, jc[n][1]));
-              if ((m1 & 0xFFFFu) && jc[n][0] != 0xFFFFFFFFu) jt_push(cnt_s, seg, qb, key_lo(d1, jc[n][0]));
-              if ((m1 >> 16) && jc[n][1] != 0xFFFFFFFFu) jt_push(cnt_s, seg, qb, key_hi(d1, jc[n][1]));
+              for (int s = 0; s < 4; ++s)
+                mma_pm1(d[n][0], d[n][1], af[2 * s], ag[2 * s], af[2 * s + 1], ag[2 * s + 1], bf[n][2 * s],
+                        bf[n][2 * s + 1]);
+              const uint32_t sel = (1u << (2 * n)) | (1u << (17 + 2 * n));
+              acc_a |= le_mask(d[n][0], t2) & sel;
+              acc_b |= le_mask(d[n][1], t2) & sel;
             }
+          }
+          // bit 2n + c: entry (row, column 2 (lane % 4) + c of tile n) survives
+          uint32_t ka = (acc_a | (acc_a >> 16)) & 0xFFu, kb = (acc_b | (acc_b >> 16)) & 0xFFu;
+          ka &= va ? jok : 0u;
+          kb &= vb ? jok : 0u;
+          if (ka | kb) {
+            // one counter update per row, then the row's survivors at consecutive slots
+            uint32_t pa = ka ? atomicAdd(cnt_s + qa_c, (uint32_t)__popc(ka)) : 0u;
+            uint32_t pb = kb ? atomicAdd(cnt_s + qb_c, (uint32_t)__popc(kb)) : 0u;
+            uint32_t* sa = seg + (size_t)qa_c * JSEG;
+            uint32_t* sb = seg + (size_t)qb_c * JSEG;
+#pragma unroll
+            for (int n = 0; n < NTC; ++n)
+#pragma unroll
+              for (int c = 0; c < 2; ++c) {
+                const int bit = 2 * n + c;
+                if ((ka >> bit) & 1u) {
+                  if (pa < JSEG) sa[pa] = c ? key_hi(d[n][0], jc[n][1]) : key_lo(d[n][0], jc[n][0]);
+                  ++pa;
+                }
+                if ((kb >> bit) & 1u) {
+                  if (pb < JSEG) sb[pb] = c ? key_hi(d[n][1], jc[n][1]) : key_lo(d[n][1], jc[n][0]);
+                  ++pb;
+                }
+              }
           }
         }
       }
@@ -538,12 +567,14 @@ uint32_t join_grid(const KParams& kp, uint32_t na_max, uint32_t n_items) {
   return (uint32_t)(n_items < gr ? n_items : gr);
 }
 
+cudaError_t launch_join_calibrate(const MatchArgs& a, cudaStream_t s) {
+  if (a.n_pairs == 0) return cudaSuccess;
+  return join_dispatch(a.kp.top_k, &a, a.kp.tau < a.kp.code_bits, 0, s, nullptr, a.na_max, true);
+}
+
 cudaError_t launch_join(const MatchArgs& a, uint32_t grid, cudaStream_t s) {
   if (a.n_items == 0 || grid == 0) return cudaSuccess;
-  const bool tau = a.kp.tau < a.kp.code_bits;
-  cudaError_t e = join_dispatch(a.kp.top_k, &a, tau, grid, s, nullptr, a.na_max, true);
-  if (e != cudaSuccess) return e;
-  return join_dispatch(a.kp.top_k, &a, tau, grid, s, nullptr, a.na_max, false);
+  return join_dispatch(a.kp.top_k, &a, a.kp.tau < a.kp.code_bits, grid, s, nullptr, a.na_max, false);
 }
 
 }  // namespace chx
