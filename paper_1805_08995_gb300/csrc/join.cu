@@ -364,35 +364,46 @@ __global__ void __launch_bounds__(JT, 2) k_join(MatchArgs a) {
 #pragma unroll
       for (int s = 0; s < KC; ++s) key_s[s * JT + tid] = (valid && !pending) ? top[s] : KEY_INF;
       __syncwarp();
+      // 4 lanes per 128-byte row (32 bytes each), 8 queries per step, the k rows in flight
       const uint32_t wbase = warp * 32;
-      const int grp = lane >> 3, sub = lane & 7;
-      constexpr int DB = KC <= 10 ? KC : 8;  // candidate rows in flight per query
-      for (uint32_t qq0 = 0; qq0 < 32; qq0 += 4) {
+      const int grp = lane >> 2, sub = lane & 3;
+      constexpr int DB = KC <= 10 ? KC : 8;
+      for (uint32_t qq0 = 0; qq0 < 32; qq0 += 8) {
         const uint32_t qi = wbase + qq0 + grp;
         const bool has = key_s[qi] != KEY_INF;
         const uint64_t fa = P.a0 + q0 + qi;
-        uint4 av = make_uint4(0u, 0u, 0u, 0u);
-        if (has) av = __ldg(reinterpret_cast<const uint4*>(a.desc + fa * DIM) + sub);
+        const uint4* arow = reinterpret_cast<const uint4*>(a.desc + fa * DIM) + 2 * sub;
+        uint4 av0 = make_uint4(0u, 0u, 0u, 0u), av1 = av0;
+        if (has) {
+          av0 = __ldg(arow);
+          av1 = __ldg(arow + 1);
+        }
         for (uint32_t s0 = 0; s0 < K; s0 += DB) {
           uint32_t key[DB];
-          uint4 bv[DB];
+          uint4 bv0[DB], bv1[DB];
 #pragma unroll
           for (int d = 0; d < DB; ++d) {
             key[d] = (has && s0 + d < K) ? key_s[(s0 + d) * JT + qi] : KEY_INF;
-            bv[d] = make_uint4(0u, 0u, 0u, 0u);
-            if (key[d] != KEY_INF)
-              bv[d] = __ldg(reinterpret_cast<const uint4*>(a.desc + (P.b0 + (key[d] & 0xFFFFFFu)) * DIM) + sub);
+            bv0[d] = bv1[d] = make_uint4(0u, 0u, 0u, 0u);
+            if (key[d] != KEY_INF) {
+              const uint4* brow = reinterpret_cast<const uint4*>(a.desc + (P.b0 + (key[d] & 0xFFFFFFu)) * DIM) + 2 * sub;
+              bv0[d] = __ldg(brow);
+              bv1[d] = __ldg(brow + 1);
+            }
           }
 #pragma unroll
           for (int d = 0; d < DB; ++d) {
             uint32_t dot = 0;
-            dot = __dp4a(av.x, bv[d].x, dot);
-            dot = __dp4a(av.y, bv[d].y, dot);
-            dot = __dp4a(av.z, bv[d].z, dot);
-            dot = __dp4a(av.w, bv[d].w, dot);
+            dot = __dp4a(av0.x, bv0[d].x, dot);
+            dot = __dp4a(av0.y, bv0[d].y, dot);
+            dot = __dp4a(av0.z, bv0[d].z, dot);
+            dot = __dp4a(av0.w, bv0[d].w, dot);
+            dot = __dp4a(av1.x, bv1[d].x, dot);
+            dot = __dp4a(av1.y, bv1[d].y, dot);
+            dot = __dp4a(av1.z, bv1[d].z, dot);
+            dot = __dp4a(av1.w, bv1[d].w, dot);
             dot += __shfl_xor_sync(0xFFFFFFFFu, dot, 1);
             dot += __shfl_xor_sync(0xFFFFFFFFu, dot, 2);
-            dot += __shfl_xor_sync(0xFFFFFFFFu, dot, 4);
             if (sub == 0 && key[d] != KEY_INF) {
               const uint64_t fb = P.b0 + (key[d] & 0xFFFFFFu);
               dist_s[(s0 + d) * JT + qi] = __ldg(a.sqnorm + fa) + __ldg(a.sqnorm + fb) - 2u * dot;
