@@ -75,6 +75,10 @@ def workload(name: str, rank: int):
     elif name == "config3":
         s = synth.config3(seed=3 + 1000 * rank)
         desc = "config3: 2000 images log-uniform 1000..20000, 30 neighbours each, %d pairs" % len(s.pairs)
+    elif name == "config4":
+        s = synth.config4(seed=4 + 1000 * rank)
+        desc = ("config4: 500 pinhole views of 200000 points (helix cameras, 30%% clutter), views with >= 20%% "
+                "overlap paired: %d pairs, epipolar band 4 px, ground-truth F" % len(s.pairs))
     else:
         raise SystemExit("unknown workload " + name)
     return s, desc
@@ -176,7 +180,8 @@ def oracle_sample(s, n_pairs: int, seed: int = 0):
     N_A * N_B).  Returns (pairs/s, cores, sample text, seconds)."""
     import oracle as orc
     cores = os.cpu_count() or 1
-    po = orc.params()
+    band = s.F is not None
+    po = orc.params(epi_px=4.0) if band else orc.params()
     rng = np.random.default_rng(seed)
     P = len(s.pairs)
     pick = np.sort(rng.choice(P, size=min(n_pairs, P), replace=False))
@@ -195,8 +200,11 @@ def oracle_sample(s, n_pairs: int, seed: int = 0):
     t_hash = time.perf_counter() - t0
     remap = {int(i): k for k, i in enumerate(imgs)}
     sp2 = np.array([[remap[int(a)], remap[int(b)]] for a, b in sp], np.uint32)
+    kw = {}
+    if band:
+        kw = dict(F=s.F[pick], kpts=np.concatenate([s.kpts[int(s.img_off[i]):int(s.img_off[i + 1])] for i in imgs]))
     t0 = time.perf_counter()
-    orc.match_pairs(sub_desc, sub_off, codes, buckets, sp2, po, n_threads=cores)
+    orc.match_pairs(sub_desc, sub_off, codes, buckets, sp2, po, n_threads=cores, **kw)
     t_match = time.perf_counter() - t0
     work_full = float((sizes[s.pairs[:, 0]] * sizes[s.pairs[:, 1]]).sum())
     work_smp = float((sizes[sp[:, 0]] * sizes[sp[:, 1]]).sum())
@@ -262,9 +270,10 @@ def run_ours(args):
         wdesc += " (first %d pairs only)" % args.max_pairs
     prec = ch.CASHASH_BF16 if args.precision == "bf16" else ch.CASHASH_FP32
     sched = ch.CASHASH_SCHED_PERSISTENT if args.schedule == "persistent" else ch.CASHASH_SCHED_PER_PAIR
-    p = ch.cashash_default_params(precision=prec, schedule=sched)
+    band = s.F is not None
+    p = ch.cashash_default_params(precision=prec, schedule=sched, **(dict(epi_px=4.0) if band else {}))
     ctx = ch.cashash_create(p, s.R)
-    ds = ch.DeviceSet(p, s.img_off, s.desc)
+    ds = ch.DeviceSet(p, s.img_off, s.desc, s.kpts if band else None)
     plan = ch.cashash_plan_create(ctx, ds, s.pairs)
     P = len(s.pairs)
     cap = int(s.sizes()[s.pairs[:, 0]].sum())
@@ -276,8 +285,12 @@ def run_ours(args):
 
     def step():
         ch.cashash_build_codes(ctx, ds, stream=stream)
-        ch.cashash_match_plan(ctx, plan, moff, mt, cap, stream=stream)
+        ch.cashash_match_plan(ctx, plan, moff, mt, cap, F=F_dev, stream=stream)
 
+    F_dev = torch.from_numpy(np.ascontiguousarray(s.F)).to(dev) if band else None
+    tuning = ch.cashash_plan_get_tuning(plan)
+    if sched == ch.CASHASH_SCHED_PERSISTENT and not args.no_autotune:
+        tuning = ch.cashash_plan_autotune(ctx, plan, F=F_dev, max_pairs=512, stream=stream)
     ch.cashash_set_profiling(ctx, True)
     for _ in range(args.warmup):
         flush.zero_()
@@ -374,19 +387,22 @@ def run_ours(args):
         mt_h = np.zeros((cap, 2), np.uint32)
         ctx2 = ch.cashash_create(p, s.R)
         for _ in range(max(1, args.warmup)):
-            ch.cashash_run_host(ctx2, pinned, s.img_off, s.pairs, cap, match_off=mo_h, matches=mt_h)
+            ch.cashash_run_host(ctx2, pinned, s.img_off, s.pairs, cap, match_off=mo_h, matches=mt_h,
+                                kpts=s.kpts if band else None, F=s.F if band else None)
         ts = []
         for _ in range(args.steps):
             flush.zero_()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             st, off, mth = ch.cashash_run_host(ctx2, pinned, s.img_off, s.pairs, cap, match_off=mo_h,
-                                               matches=mt_h)
+                                               matches=mt_h, kpts=s.kpts if band else None,
+                                               F=s.F if band else None)
             ts.append(time.perf_counter() - t0)
             assert st == ch.CASHASH_OK
         n_m = int(mo_h[P])
         e2e = {"value": P / statistics.mean(ts), "unit": "pairs/s",
-               "h2d_bytes_per_step": int(s.desc.nbytes + 8 * (len(s.img_off))),
+               "h2d_bytes_per_step": int(s.desc.nbytes + 8 * (len(s.img_off)) +
+                                         (s.kpts.nbytes + s.F.nbytes if band else 0)),
                "d2h_bytes_per_step": int(8 * (P + 1) + 8 * n_m)}
         ctx2.close()
 
@@ -406,7 +422,10 @@ def run_ours(args):
                 "config": {"workload": wdesc, "images": int(s.n_images), "features": int(s.desc.shape[0]),
                            "pairs": P, "precision": args.precision, "schedule": args.schedule,
                            "l2": "flushed: 256 MiB write between timed steps (outside the events)",
-                           "params": "n=128, 6 tables x 8 bits, k=10, ratio 0.8",
+                           "params": "n=128, 6 tables x 8 bits, k=10, ratio 0.8" + (", band 4 px" if band else ""),
+                           "kernel_tuning": {"kernel": {1: "join", 2: "query"}.get(tuning["kernel"], "per_pair"),
+                                             "tile": tuning["tile"], "ctas_per_sm": tuning["ctas_per_sm"],
+                                             "autotuned": tuning["ms_sample"] > 0},
                            "matches_per_step": int(stats["n_matches"]),
                            "reevaluated_projections": int(stats["n_reevaluated"])},
                 "features_per_s": s.desc.shape[0] * world * args.steps / t_max,
@@ -425,13 +444,14 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="config1", choices=["config0", "config1", "config3"])
+    ap.add_argument("--workload", default="config1", choices=["config0", "config1", "config3", "config4"])
     ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16"])
     ap.add_argument("--schedule", default="persistent", choices=["persistent", "per_pair"])
     ap.add_argument("--ref-pairs", type=int, default=1200)
     ap.add_argument("--max-pairs", type=int, default=0, help="match only the first N pairs (profiling case)")
     ap.add_argument("--thresholds", default="learned", choices=["learned", "fresh"],
                     help="fresh: clear the learned per-pair Hamming thresholds before every timed step")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the plan's default kernel configuration")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

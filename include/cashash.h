@@ -182,6 +182,40 @@ int cashash_match_plan(cashash_ctx* ctx, cashash_plan* plan, const double* F_dev
  * Errors: EINVAL, ECUDA. */
 int cashash_plan_set_threshold_hint(cashash_plan* plan, uint32_t hamming, int fixed);
 
+/* Kernel configuration of a batched (persistent) plan.  Every configuration
+ * gives the same, exact results; they differ in speed only.  The paper has no
+ * counterpart (it runs one kernel shape). */
+enum { CASHASH_KERNEL_JOIN = 1, CASHASH_KERNEL_QUERY = 2 };
+typedef struct {
+  uint32_t kernel;       /* CASHASH_KERNEL_JOIN: tensor-core bucket join (band off, query images that
+                            fit its shared-memory counters); CASHASH_KERNEL_QUERY: per-query
+                            speculative kernel over shared-memory staged table chunks */
+  uint32_t tile;         /* JOIN: candidate tiles of 8 columns held in registers (2 or 4);
+                            QUERY: queries per CTA (256, or 512 when top_k <= 16) */
+  uint32_t ctas_per_sm;  /* JOIN: resident CTAs per SM, 0 = as many as fit; QUERY: ignored */
+  uint32_t reserved;
+  double ms_sample;      /* set by cashash_plan_autotune: matching time (ms) of its sample with
+                            this configuration; -1 otherwise */
+} cashash_tuning;
+
+/* The configuration a plan matches with (chosen at creation: the join when it
+ * applies, else the per-query kernel).  Errors: EINVAL. */
+int cashash_plan_get_tuning(const cashash_plan* plan, cashash_tuning* out);
+
+/* Forces a configuration (fields normalised to supported values; the plan's
+ * captured graph is dropped).  Errors: EINVAL (not a batched plan),
+ * ENOTSUP (the join does not apply to this plan), ENOMEM, ECUDA. */
+int cashash_plan_set_tuning(cashash_plan* plan, const cashash_tuning* t);
+
+/* Autotuner: times every applicable configuration on a sample of at most
+ * max_pairs of the plan's pairs (0 = 512; spread over the pairs' N_A * N_B
+ * cost order), three runs each after two untimed ones, and keeps the plan's
+ * default configuration unless another is more than 3 % faster (then the
+ * fastest).  F_dev as for cashash_match_plan.  Synchronises `stream`;
+ * allocates temporary device buffers.  Errors: EINVAL, ENOMEM, ECUDA. */
+int cashash_plan_autotune(cashash_ctx* ctx, cashash_plan* plan, const double* F_dev, uint32_t max_pairs,
+                          cashash_stream_t stream);
+
 /* Convenience: plan + match + plan release in one call (same outputs). */
 int cashash_match_pairs(cashash_ctx* ctx, const cashash_set* set, const uint32_t* pairs_host, uint32_t P,
                         const double* F_dev, uint64_t* match_off, uint32_t* matches, uint64_t cap,

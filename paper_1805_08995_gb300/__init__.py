@@ -23,6 +23,7 @@ CASHASH_EOVERFLOW, CASHASH_EDEVICE, CASHASH_ETIMEOUT, CASHASH_ENOTSUP = 4, 5, 6,
 CASHASH_FP32, CASHASH_BF16 = 0, 1
 CASHASH_SCHED_PER_PAIR, CASHASH_SCHED_PERSISTENT = 0, 1
 CASHASH_NOALLOC_MAX_QUERIES = 65536
+CASHASH_KERNEL_JOIN, CASHASH_KERNEL_QUERY = 1, 2
 
 
 class CashashError(RuntimeError):
@@ -52,6 +53,11 @@ class cashash_stats(C.Structure):
     _fields_ = [("n_features", C.c_uint64), ("n_reevaluated", C.c_uint64), ("n_pairs", C.c_uint64),
                 ("n_matches", C.c_uint64), ("n_work_items", C.c_uint64), ("n_launches", C.c_uint64),
                 ("ms_stage", C.c_double * N_STAGES)]
+
+
+class cashash_tuning(C.Structure):
+    _fields_ = [("kernel", C.c_uint32), ("tile", C.c_uint32), ("ctas_per_sm", C.c_uint32), ("reserved", C.c_uint32),
+                ("ms_sample", C.c_double)]
 
 
 _lib = None
@@ -85,6 +91,9 @@ def _load():
             "cashash_plan_set_threshold_hint": ([vp, u32, C.c_int], C.c_int),
             "cashash_match_pair_noalloc": ([P(cashash_params), P(cashash_set), u32, u32, vp, vp, vp, u64, vp],
                                            C.c_int),
+            "cashash_plan_get_tuning": ([vp, P(cashash_tuning)], C.c_int),
+            "cashash_plan_set_tuning": ([vp, P(cashash_tuning)], C.c_int),
+            "cashash_plan_autotune": ([vp, vp, vp, u32, vp], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -100,7 +109,8 @@ def exported_symbols():
             "cashash_destroy", "cashash_build_codes", "cashash_get_mean", "cashash_plan_create",
             "cashash_plan_destroy", "cashash_match_plan", "cashash_match_pairs", "cashash_sync_status",
             "cashash_run_host", "cashash_get_stats", "cashash_set_profiling", "cashash_match_pair_noalloc",
-            "cashash_plan_set_threshold_hint"]
+            "cashash_plan_set_threshold_hint", "cashash_plan_get_tuning", "cashash_plan_set_tuning",
+            "cashash_plan_autotune"]
 
 
 def _check(st, what):
@@ -252,6 +262,25 @@ def cashash_plan_create(ctx: Context, dset: DeviceSet, pairs) -> Plan:
 def cashash_plan_set_threshold_hint(plan: Plan, hamming: int, fixed: bool = False):
     _check(_load().cashash_plan_set_threshold_hint(plan.handle, int(hamming), 1 if fixed else 0),
            "cashash_plan_set_threshold_hint")
+
+
+def cashash_plan_get_tuning(plan: Plan) -> dict:
+    t = cashash_tuning()
+    _check(_load().cashash_plan_get_tuning(plan.handle, C.byref(t)), "cashash_plan_get_tuning")
+    return {k: getattr(t, k) for k, _ in cashash_tuning._fields_ if k != "reserved"}
+
+
+def cashash_plan_set_tuning(plan: Plan, kernel: int, tile: int = 0, ctas_per_sm: int = 0):
+    t = cashash_tuning(kernel=kernel, tile=tile, ctas_per_sm=ctas_per_sm, reserved=0, ms_sample=-1.0)
+    _check(_load().cashash_plan_set_tuning(plan.handle, C.byref(t)), "cashash_plan_set_tuning")
+
+
+def cashash_plan_autotune(ctx: Context, plan: Plan, F=None, max_pairs: int = 0, stream=None) -> dict:
+    """Times every applicable kernel configuration on a sample of the plan's
+    pairs, keeps the fastest and returns it (see include/cashash.h)."""
+    _check(_load().cashash_plan_autotune(ctx.handle, plan.handle, _dptr(F), int(max_pairs), _stream(stream)),
+           "cashash_plan_autotune")
+    return cashash_plan_get_tuning(plan)
 
 
 def cashash_plan_destroy(plan: Plan):

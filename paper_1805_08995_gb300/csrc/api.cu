@@ -92,9 +92,15 @@ struct cashash_plan {
   uint32_t tau_fixed = 0;              // keep the Hamming threshold hint fixed
   uint32_t occ_grid = 0;               // per-pair launches: resident CTAs
   bool join = false;                   // persistent schedule: bucket join (else speculative kernel)
+  cashash_tuning tune{};               // persistent schedule: kernel configuration
   uint32_t na_max = 1;                 // largest query image (bucket-join scratch)
   uint32_t* d_jhist = nullptr;         // bucket join: per-pair histogram of k-th Hamming distances
+  uint64_t cap_items = 0, cap_queue = 0;
   std::vector<uint32_t> first, count;  // per-pair item ranges (per-pair schedule)
+  std::vector<PairInfo> info;          // host copies: pair records, pair list, the set and its offsets
+  std::vector<uint32_t> pairs_h;
+  std::vector<uint64_t> img_off_h;
+  cashash_set set{};
   // persistent schedule: the launch sequence captured as a CUDA graph, replayed
   // while the outputs, F and the profiling setting stay the same
   cudaStream_t cap_stream = nullptr;
@@ -528,6 +534,95 @@ void cashash_plan_destroy(cashash_plan* pl) {
   delete pl;
 }
 
+namespace {
+
+// Work items, grid and scratch of a plan for configuration t (persistent
+// schedule), or for the per-pair schedule.  Drops the captured graph.
+int plan_configure(cashash_plan* pl, cashash_tuning t) {
+  cashash_ctx* c = pl->ctx;
+  const uint32_t P = pl->P;
+  const std::vector<PairInfo>& info = pl->info;
+  const bool epi = c->p.epi_px >= 0.0;
+  if (pl->gexec) {
+    cudaGraphExecDestroy(pl->gexec);
+    pl->gexec = nullptr;
+  }
+  std::vector<uint2> items;
+  bool join = false;
+  uint32_t grid = 0;
+  if (!pl->persistent) {
+    const uint32_t tile = (uint32_t)match_tile_size(c->p.top_k, 0);
+    for (uint32_t i = 0; i < P; ++i) {
+      pl->first[i] = (uint32_t)items.size();
+      for (uint32_t q0 = 0; q0 < info[i].nA; q0 += tile) items.push_back(make_uint2(i, q0));
+      pl->count[i] = (uint32_t)items.size() - pl->first[i];
+    }
+    pl->occ_grid = match_grid(c->p.top_k, 0, epi, c->p.n_tables, 0xFFFFFFFFu);
+    t = cashash_tuning{};
+  } else if (t.kernel == CASHASH_KERNEL_JOIN) {
+    t.tile = t.tile <= 2 ? 2u : 4u;
+    grid = join_grid(c->kp, pl->na_max, P, t.tile, t.ctas_per_sm);
+    if (P && !grid) return CASHASH_ENOTSUP;
+    join = true;
+    // One item per pair.  The resident CTAs take consecutive items, so the
+    // pairs are ordered by tiles of S x S images (S^2 about the number of
+    // resident CTAs): the pairs in flight then share about 2 S images, whose
+    // descriptors and tables stay in L2.  Within a tile the largest
+    // (N_A * N_B) pairs come first.
+    const uint32_t S = std::max<uint32_t>(1, (uint32_t)std::lround(std::sqrt((double)grid)));
+    std::vector<uint64_t> tkey(P);
+    for (uint32_t i = 0; i < P; ++i) {
+      const uint32_t a = pl->pairs_h[2 * (size_t)i], b = pl->pairs_h[2 * (size_t)i + 1];
+      tkey[i] = ((uint64_t)(std::min(a, b) / S) << 32) | (std::max(a, b) / S);
+    }
+    std::vector<uint32_t> order(P);
+    for (uint32_t i = 0; i < P; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
+      if (tkey[x] != tkey[y]) return tkey[x] < tkey[y];
+      return (uint64_t)info[x].nA * info[x].nB > (uint64_t)info[y].nA * info[y].nB;
+    });
+    for (uint32_t i : order) items.push_back(make_uint2(i, 0u));
+  } else if (t.kernel == CASHASH_KERNEL_QUERY) {
+    t.tile = (uint32_t)match_tile_size(c->p.top_k, 1, t.tile);
+    t.ctas_per_sm = 0;
+    // tiles of queries, grouped by candidate image so that a candidate
+    // image's chunks are reused from L2 by consecutive items
+    std::vector<uint32_t> order(P);
+    for (uint32_t i = 0; i < P; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
+      return pl->pairs_h[2 * (size_t)x + 1] < pl->pairs_h[2 * (size_t)y + 1];
+    });
+    for (uint32_t i : order)
+      for (uint32_t q0 = 0; q0 < info[i].nA; q0 += t.tile) items.push_back(make_uint2(i, q0));
+    grid = match_grid(c->p.top_k, 1, epi, c->p.n_tables, (uint32_t)items.size(), t.tile);
+  } else {
+    return CASHASH_EINVAL;
+  }
+  int st = grow(pl->d_items, pl->cap_items, std::max<uint64_t>(items.size(), 1));
+  if (st == CASHASH_OK && pl->persistent) {
+    const uint64_t q = join ? (uint64_t)grid * pl->na_max * JSEG : (uint64_t)grid * t.tile * QCAP;
+    st = grow(pl->d_queue, pl->cap_queue, std::max<uint64_t>(q, 1));
+  }
+  if (st == CASHASH_OK && join && !pl->d_jhist) {
+    uint64_t cap = 0;
+    st = grow(pl->d_jhist, cap, std::max<uint64_t>((uint64_t)P * HBINS, 1));
+    if (st == CASHASH_OK)
+      st = cuda_err(cudaMemset(pl->d_jhist, 0, sizeof(uint32_t) * std::max<uint64_t>((uint64_t)P * HBINS, 1)));
+  }
+  if (st == CASHASH_OK && !items.empty())
+    st = cuda_err(cudaMemcpy(pl->d_items, items.data(), sizeof(uint2) * items.size(), cudaMemcpyHostToDevice));
+  if (st != CASHASH_OK) return st;
+  pl->n_items = (uint32_t)items.size();
+  pl->join = join;
+  pl->grid = grid;
+  t.ms_sample = -1.0;
+  t.reserved = 0;
+  pl->tune = t;
+  return CASHASH_OK;
+}
+
+}  // namespace
+
 int cashash_plan_create(cashash_ctx* c, const cashash_set* s, const uint32_t* pairs_host, uint32_t P,
                         cashash_plan** out) {
   if (!c || !out || !set_ok(s, nullptr) || (P > 0 && !pairs_host)) return CASHASH_EINVAL;
@@ -570,60 +665,18 @@ int cashash_plan_create(cashash_ctx* c, const cashash_set* s, const uint32_t* pa
     qbase += pi.nA;
   }
   pl->n_res = qbase;
-  std::vector<uint2> items;
-  pl->first.assign(P, 0);
-  pl->count.assign(P, 0);
   uint32_t na_max = 0;
   for (uint32_t i = 0; i < P; ++i) na_max = std::max(na_max, info[i].nA);
   pl->na_max = std::max<uint32_t>(na_max, 1);
-  const bool epi = c->p.epi_px >= 0.0;
-  if (pl->persistent) {
-    pl->grid = join_grid(c->kp, pl->na_max, P);
-    pl->join = pl->grid > 0;
-  }
-  if (pl->join) {
-    // bucket join: one item per pair.  The resident CTAs take consecutive
-    // items, so the pairs are ordered by tiles of S x S images (S^2 about the
-    // number of resident CTAs): the pairs in flight then share about 2 S
-    // images, whose descriptors and tables stay in L2.  Within a tile the
-    // largest (N_A * N_B) pairs come first.
-    const uint32_t S = std::max<uint32_t>(1, (uint32_t)std::lround(std::sqrt((double)pl->grid)));
-    std::vector<uint64_t> tkey(P);
-    for (uint32_t i = 0; i < P; ++i) {
-      const uint32_t a = pairs_host[2 * (size_t)i], b = pairs_host[2 * (size_t)i + 1];
-      tkey[i] = ((uint64_t)(std::min(a, b) / S) << 32) | (std::max(a, b) / S);
-    }
-    std::vector<uint32_t> order(P);
-    for (uint32_t i = 0; i < P; ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
-      if (tkey[x] != tkey[y]) return tkey[x] < tkey[y];
-      return (uint64_t)info[x].nA * info[x].nB > (uint64_t)info[y].nA * info[y].nB;
-    });
-    for (uint32_t i : order) items.push_back(make_uint2(i, 0u));
-  } else {
-    // tiles of queries; the persistent form groups the pairs by candidate
-    // image so that a candidate image's chunks are reused from L2
-    const uint32_t tile = (uint32_t)match_tile_size(c->p.top_k, pl->persistent);
-    std::vector<uint32_t> order(P);
-    for (uint32_t i = 0; i < P; ++i) order[i] = i;
-    if (pl->persistent)
-      std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
-        return pairs_host[2 * (size_t)x + 1] < pairs_host[2 * (size_t)y + 1];
-      });
-    for (uint32_t oi = 0; oi < P; ++oi) {
-      const uint32_t i = order[oi];
-      pl->first[i] = (uint32_t)items.size();
-      for (uint32_t q0 = 0; q0 < info[i].nA; q0 += tile) items.push_back(make_uint2(i, q0));
-      pl->count[i] = (uint32_t)items.size() - pl->first[i];
-    }
-  }
-  pl->n_items = (uint32_t)items.size();
-  if (pl->persistent && !pl->join) pl->grid = match_grid(c->p.top_k, 1, epi, c->p.n_tables, pl->n_items);
-  if (!pl->persistent) pl->occ_grid = match_grid(c->p.top_k, 0, epi, c->p.n_tables, 0xFFFFFFFFu);
+  pl->info = info;
+  pl->pairs_h.assign(pairs_host, pairs_host + 2 * (size_t)P);
+  pl->img_off_h.assign(s->img_off, s->img_off + (size_t)s->n_images + 1);
+  pl->set = *s;
+  pl->set.img_off = pl->img_off_h.data();
+  pl->first.assign(P, 0);
+  pl->count.assign(P, 0);
   uint64_t cap = 0;
   int st = grow(pl->d_pairs, cap, std::max<uint64_t>(P, 1));
-  cap = 0;
-  if (st == CASHASH_OK) st = grow(pl->d_items, cap, std::max<uint64_t>(items.size(), 1));
   cap = 0;
   if (st == CASHASH_OK) st = grow(pl->d_res, cap, std::max<uint64_t>(qbase, 1));
   cap = 0;
@@ -633,22 +686,23 @@ int cashash_plan_create(cashash_ctx* c, const cashash_set* s, const uint32_t* pa
   cap = 0;
   if (st == CASHASH_OK) st = grow(pl->d_tau, cap, std::max<uint64_t>(P, 1));
   if (st == CASHASH_OK) st = cuda_err(cudaMemset(pl->d_tau, 0, sizeof(uint32_t) * std::max<uint64_t>(P, 1)));
-  if (st == CASHASH_OK && pl->join) {
-    cap = 0;
-    st = grow(pl->d_queue, cap, std::max<uint64_t>((uint64_t)pl->grid * pl->na_max * JSEG, 1));
-    cap = 0;
-    if (st == CASHASH_OK) st = grow(pl->d_jhist, cap, std::max<uint64_t>((uint64_t)P * HBINS, 1));
-    if (st == CASHASH_OK)
-      st = cuda_err(cudaMemset(pl->d_jhist, 0, sizeof(uint32_t) * std::max<uint64_t>((uint64_t)P * HBINS, 1)));
-  } else if (st == CASHASH_OK && pl->persistent) {
-    cap = 0;
-    const uint64_t tile = (uint64_t)match_tile_size(c->p.top_k, 1);
-    st = grow(pl->d_queue, cap, std::max<uint64_t>((uint64_t)pl->grid * tile * QCAP, 1));
-  }
   if (st == CASHASH_OK && P)
     st = cuda_err(cudaMemcpy(pl->d_pairs, info.data(), sizeof(PairInfo) * P, cudaMemcpyHostToDevice));
-  if (st == CASHASH_OK && !items.empty())
-    st = cuda_err(cudaMemcpy(pl->d_items, items.data(), sizeof(uint2) * items.size(), cudaMemcpyHostToDevice));
+  if (st == CASHASH_OK) {
+    if (pl->persistent) {
+      cashash_tuning t{};  // the join when it applies, else the per-query kernel
+      t.kernel = CASHASH_KERNEL_JOIN;
+      t.tile = 4;
+      st = plan_configure(pl, t);
+      if (st == CASHASH_ENOTSUP) {
+        t.kernel = CASHASH_KERNEL_QUERY;
+        t.tile = 0;
+        st = plan_configure(pl, t);
+      }
+    } else {
+      st = plan_configure(pl, cashash_tuning{});
+    }
+  }
   if (st != CASHASH_OK) {
     cashash_plan_destroy(pl);
     return st;
@@ -699,8 +753,8 @@ int enqueue_match(cashash_ctx* c, cashash_plan* pl, const double* F_dev, uint64_
     }
     {
       StageTimer tm(c, CASHASH_STAGE_MATCH, stream, capturing);
-      if (pl->join) CK(launch_join(a, pl->grid, stream));
-      else CK(launch_match(a, 1, pl->grid, stream));
+      if (pl->join) CK(launch_join(a, pl->grid, pl->tune.tile, stream));
+      else CK(launch_match(a, 1, pl->grid, stream, pl->tune.tile));
     }
     {
       StageTimer tm(c, CASHASH_STAGE_FALLBACK, stream, capturing);
@@ -797,6 +851,130 @@ int cashash_plan_set_threshold_hint(cashash_plan* pl, uint32_t hamming, int fixe
   if (pl->d_jhist) CK(cudaMemset(pl->d_jhist, 0, sizeof(uint32_t) * (size_t)std::max<uint32_t>(pl->P, 1) * HBINS));
   pl->tau_fixed = fixed ? 1u : 0u;
   return CASHASH_OK;
+}
+
+int cashash_plan_get_tuning(const cashash_plan* pl, cashash_tuning* out) {
+  if (!pl || !out) return CASHASH_EINVAL;
+  *out = pl->tune;
+  return CASHASH_OK;
+}
+
+int cashash_plan_set_tuning(cashash_plan* pl, const cashash_tuning* t) {
+  if (!pl || !t || !pl->ctx || !pl->persistent) return CASHASH_EINVAL;
+  CK(cudaSetDevice(pl->ctx->device));
+  CK(cudaDeviceSynchronize());
+  const cashash_tuning keep = pl->tune;
+  const int st = plan_configure(pl, *t);
+  if (st != CASHASH_OK && plan_configure(pl, keep) != CASHASH_OK) return CASHASH_ECUDA;
+  return st;
+}
+
+int cashash_plan_autotune(cashash_ctx* c, cashash_plan* pl, const double* F_dev, uint32_t max_pairs,
+                          cashash_stream_t stream_) {
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+  if (!c || !pl || pl->ctx != c) return CASHASH_EINVAL;
+  if (c->p.epi_px >= 0.0 && pl->P > 0 && !F_dev) return CASHASH_EINVAL;
+  if (!pl->persistent || pl->P == 0) return CASHASH_OK;
+  CK(cudaSetDevice(c->device));
+  CK(cudaStreamSynchronize(stream));
+  const uint32_t P = pl->P;
+  const uint32_t S = std::min<uint32_t>(P, max_pairs ? max_pairs : 512u);
+  // the sample: S pairs spread over the plan's cost order
+  std::vector<uint32_t> order(P);
+  for (uint32_t i = 0; i < P; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
+    return (uint64_t)pl->info[x].nA * pl->info[x].nB > (uint64_t)pl->info[y].nA * pl->info[y].nB;
+  });
+  std::vector<uint32_t> pick(S), sub(2 * (size_t)S);
+  uint64_t cap = 0;
+  for (uint32_t i = 0; i < S; ++i) {
+    pick[i] = order[(uint32_t)(((uint64_t)i * P) / S)];
+    sub[2 * (size_t)i] = pl->pairs_h[2 * (size_t)pick[i]];
+    sub[2 * (size_t)i + 1] = pl->pairs_h[2 * (size_t)pick[i] + 1];
+    cap += pl->info[pick[i]].nA;
+  }
+  cashash_plan* sp = nullptr;
+  int st = cashash_plan_create(c, &pl->set, sub.data(), S, &sp);
+  if (st != CASHASH_OK) return st;
+  double* dF = nullptr;
+  uint64_t* dmo = nullptr;
+  uint32_t* dmt = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  uint64_t c1 = 0, c2 = 0, c3 = 0;
+  st = grow(dmo, c1, (uint64_t)S + 1);
+  if (st == CASHASH_OK) st = grow(dmt, c2, 2 * std::max<uint64_t>(cap, 1));
+  if (st == CASHASH_OK && F_dev && c->p.epi_px >= 0.0) {
+    st = grow(dF, c3, 9 * (uint64_t)S);
+    for (uint32_t i = 0; st == CASHASH_OK && i < S; ++i)
+      st = cuda_err(cudaMemcpyAsync(dF + 9 * (size_t)i, F_dev + 9 * (size_t)pick[i], 9 * sizeof(double),
+                                    cudaMemcpyDeviceToDevice, stream));
+  }
+  if (st == CASHASH_OK) st = cuda_err(cudaEventCreate(&e0));
+  if (st == CASHASH_OK) st = cuda_err(cudaEventCreate(&e1));
+  const int prof = c->profiling;
+  c->profiling = 0;
+  std::vector<cashash_tuning> cand;
+  for (uint32_t ctas : {0u, 1u})
+    for (uint32_t tile : {4u, 2u}) {
+      cashash_tuning t{};
+      t.kernel = CASHASH_KERNEL_JOIN;
+      t.tile = tile;
+      t.ctas_per_sm = ctas;
+      cand.push_back(t);
+    }
+  for (uint32_t tile : {512u, 256u}) {
+    cashash_tuning t{};
+    t.kernel = CASHASH_KERNEL_QUERY;
+    t.tile = tile;
+    cand.push_back(t);
+  }
+  // the first applicable candidate is the plan's default; another replaces it
+  // only when it is more than 3 % faster on the sample
+  cashash_tuning best{};
+  double best_ms = -1.0, def_ms = -1.0;
+  for (const cashash_tuning& t0 : cand) {
+    if (st != CASHASH_OK) break;
+    const int cs = plan_configure(sp, t0);
+    if (cs == CASHASH_ENOTSUP) continue;
+    if (cs != CASHASH_OK) {
+      st = cs;
+      break;
+    }
+    if (t0.kernel == CASHASH_KERNEL_QUERY && sp->tune.tile != t0.tile) continue;  // normalised to another candidate
+    // fresh thresholds: two untimed runs calibrate them, three timed runs follow
+    st = cuda_err(cudaMemsetAsync(sp->d_tau, 0, sizeof(uint32_t) * S, stream));
+    if (st == CASHASH_OK && sp->d_jhist)
+      st = cuda_err(cudaMemsetAsync(sp->d_jhist, 0, sizeof(uint32_t) * (size_t)S * HBINS, stream));
+    float ms = 0.f;
+    for (int r = 0; r < 5 && st == CASHASH_OK; ++r) {
+      if (r == 2) st = cuda_err(cudaEventRecord(e0, stream));
+      if (st == CASHASH_OK) st = enqueue_match(c, sp, dF, dmo, dmt, cap, stream, false);
+    }
+    if (st == CASHASH_OK) st = cuda_err(cudaEventRecord(e1, stream));
+    if (st == CASHASH_OK) st = cuda_err(cudaEventSynchronize(e1));
+    if (st == CASHASH_OK) st = cuda_err(cudaEventElapsedTime(&ms, e0, e1));
+    if (st != CASHASH_OK) break;
+    const double t_ms = ms / 3.0;
+    if (def_ms < 0.0) {
+      def_ms = best_ms = t_ms;
+      best = sp->tune;
+    } else if (t_ms < 0.97 * def_ms && t_ms < best_ms) {
+      best_ms = t_ms;
+      best = sp->tune;
+    }
+  }
+  c->profiling = prof;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  dfree(dF);
+  dfree(dmo);
+  dfree(dmt);
+  cashash_plan_destroy(sp);
+  if (st != CASHASH_OK) return st;
+  if (best_ms < 0.0) return CASHASH_OK;
+  st = plan_configure(pl, best);
+  if (st == CASHASH_OK) pl->tune.ms_sample = best_ms;
+  return st;
 }
 
 int cashash_match_pairs(cashash_ctx* c, const cashash_set* s, const uint32_t* pairs_host, uint32_t P,

@@ -162,16 +162,20 @@ struct MatchArgs {
 // Bucket-join matching (batched schedule): calibration of missing per-pair
 // thresholds (launch_join_calibrate), then the join kernel over items = pairs.
 cudaError_t launch_join_calibrate(const MatchArgs& a, cudaStream_t s);
-cudaError_t launch_join(const MatchArgs& a, uint32_t grid, cudaStream_t s);
-// Resident CTAs of the join for n_items pairs; 0 when the join does not apply
-// (band filter on, or the largest query image exceeds its shared memory).
-uint32_t join_grid(const KParams& kp, uint32_t na_max, uint32_t n_items);
+// ntc: candidate tiles of 8 columns held in registers (2 or 4).
+cudaError_t launch_join(const MatchArgs& a, uint32_t grid, uint32_t ntc, cudaStream_t s);
+// Resident CTAs of the join for n_items pairs (at most ctas_per_sm per SM when
+// non-zero); 0 when the join does not apply (band filter on, or the largest
+// query image exceeds its shared memory).
+uint32_t join_grid(const KParams& kp, uint32_t na_max, uint32_t n_items, uint32_t ntc, uint32_t ctas_per_sm);
 // Matching kernel launch.  spec = 0: direct register top-k (one pair per
 // launch); spec = 1: survivor queues with a speculative threshold (batched).
-cudaError_t launch_match(const MatchArgs& a, int spec, uint32_t grid, cudaStream_t s);
+// tile: queries per CTA of the speculative form (256, or 512 when k <= 16; 0 = default).
+cudaError_t launch_match(const MatchArgs& a, int spec, uint32_t grid, cudaStream_t s, uint32_t tile = 0);
 // Largest useful grid (resident CTAs) for a launch over n_items items.
-uint32_t match_grid(uint32_t top_k, int spec, bool epi, uint32_t n_tables, uint32_t n_items);
-int match_tile_size(uint32_t top_k, int spec);
+uint32_t match_grid(uint32_t top_k, int spec, bool epi, uint32_t n_tables, uint32_t n_items, uint32_t tile = 0);
+// Queries per CTA (= per work item) of a form; tile 0 = default.
+int match_tile_size(uint32_t top_k, int spec, uint32_t tile = 0);
 // Exact re-matching of the queries the speculative kernel left PENDING.
 cudaError_t launch_match_fallback(const MatchArgs& a, cudaStream_t s);
 cudaError_t launch_scan_counts(const unsigned long long* pair_cnt, uint32_t P, uint64_t* match_off,

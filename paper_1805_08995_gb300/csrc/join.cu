@@ -36,7 +36,6 @@ namespace chx {
 constexpr int JT = 256;            // threads of a join CTA
 constexpr int CAL_SAMPLES = 128;   // calibration: sampled queries per pair
 constexpr uint32_t CAL_MARGIN = 1; // calibration: Hamming margin over the second largest sample
-constexpr int NTC = 4;             // candidate tiles (of 8) held in registers at a time
 
 template <int KC>
 __device__ __forceinline__ void jt_insert(uint32_t (&top)[KC], uint32_t k) {
@@ -166,7 +165,8 @@ __device__ __forceinline__ void load_offsets(const uint8_t* join, const PairInfo
   }
 }
 
-template <int KC, bool TAU>
+// NTC: candidate tiles (of 8 columns) held in registers at a time.
+template <int KC, bool TAU, int NTC>
 __global__ void __launch_bounds__(JT, 2) k_join(MatchArgs a) {
   extern __shared__ __align__(16) uint8_t jsm[];
   __shared__ uint32_t s_item, s_tau, s_task;
@@ -510,7 +510,7 @@ __global__ void __launch_bounds__(CAL_SAMPLES) k_join_calibrate(MatchArgs a) {
 // ---------------------------------------------------------------------------
 namespace {
 
-template <int KC, bool TAU>
+template <int KC, bool TAU, int NTC>
 cudaError_t run_join(const MatchArgs* a, uint32_t grid, cudaStream_t s, uint32_t* occ, uint32_t na_max,
                      bool calibrate) {
   static int attr_dev = -1;
@@ -521,14 +521,14 @@ cudaError_t run_join(const MatchArgs* a, uint32_t grid, cudaStream_t s, uint32_t
     int optin = 0;
     e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_join<KC, TAU>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - 2048);
+    e = cudaFuncSetAttribute(k_join<KC, TAU, NTC>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - 2048);
     if (e != cudaSuccess) return e;
     attr_dev = dev;
   }
   const size_t smem = join_smem_bytes(KC, na_max);
   if (occ) {
     int nb = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_join<KC, TAU>, JT, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_join<KC, TAU, NTC>, JT, smem);
     *occ = (uint32_t)(nb > 0 ? nb : 0);
     return e;
   }
@@ -539,53 +539,62 @@ cudaError_t run_join(const MatchArgs* a, uint32_t grid, cudaStream_t s, uint32_t
     k_join_calibrate<KC, TAU><<<want < (uint32_t)nsm * 8 ? want : (uint32_t)nsm * 8, CAL_SAMPLES, 0, s>>>(*a);
     return cudaGetLastError();
   }
-  k_join<KC, TAU><<<grid, JT, smem, s>>>(*a);
+  k_join<KC, TAU, NTC><<<grid, JT, smem, s>>>(*a);
   return cudaGetLastError();
 }
 
-template <int KC>
-cudaError_t run_join_kc(const MatchArgs* a, bool tau, uint32_t grid, cudaStream_t s, uint32_t* occ, uint32_t na_max,
-                        bool cal) {
-  return tau ? run_join<KC, true>(a, grid, s, occ, na_max, cal) : run_join<KC, false>(a, grid, s, occ, na_max, cal);
+template <int KC, bool TAU>
+cudaError_t run_join_nt(const MatchArgs* a, uint32_t ntc, uint32_t grid, cudaStream_t s, uint32_t* occ,
+                        uint32_t na_max, bool cal) {
+  return ntc <= 2 ? run_join<KC, TAU, 2>(a, grid, s, occ, na_max, cal)
+                  : run_join<KC, TAU, 4>(a, grid, s, occ, na_max, cal);
 }
 
-cudaError_t join_dispatch(uint32_t k, const MatchArgs* a, bool tau, uint32_t grid, cudaStream_t s, uint32_t* occ,
-                          uint32_t na_max, bool cal) {
-  if (k <= 4) return run_join_kc<4>(a, tau, grid, s, occ, na_max, cal);
-  if (k <= 8) return run_join_kc<8>(a, tau, grid, s, occ, na_max, cal);
-  if (k <= 10) return run_join_kc<10>(a, tau, grid, s, occ, na_max, cal);
-  if (k <= 16) return run_join_kc<16>(a, tau, grid, s, occ, na_max, cal);
-  return run_join_kc<32>(a, tau, grid, s, occ, na_max, cal);
+template <int KC>
+cudaError_t run_join_kc(const MatchArgs* a, bool tau, uint32_t ntc, uint32_t grid, cudaStream_t s, uint32_t* occ,
+                        uint32_t na_max, bool cal) {
+  return tau ? run_join_nt<KC, true>(a, ntc, grid, s, occ, na_max, cal)
+             : run_join_nt<KC, false>(a, ntc, grid, s, occ, na_max, cal);
+}
+
+cudaError_t join_dispatch(uint32_t k, const MatchArgs* a, bool tau, uint32_t ntc, uint32_t grid, cudaStream_t s,
+                          uint32_t* occ, uint32_t na_max, bool cal) {
+  if (k <= 4) return run_join_kc<4>(a, tau, ntc, grid, s, occ, na_max, cal);
+  if (k <= 8) return run_join_kc<8>(a, tau, ntc, grid, s, occ, na_max, cal);
+  if (k <= 10) return run_join_kc<10>(a, tau, ntc, grid, s, occ, na_max, cal);
+  if (k <= 16) return run_join_kc<16>(a, tau, ntc, grid, s, occ, na_max, cal);
+  return run_join_kc<32>(a, tau, ntc, grid, s, occ, na_max, cal);
 }
 
 int kc_of(uint32_t k) { return k <= 4 ? 4 : k <= 8 ? 8 : k <= 10 ? 10 : k <= 16 ? 16 : 32; }
 
 }  // namespace
 
-uint32_t join_grid(const KParams& kp, uint32_t na_max, uint32_t n_items) {
-  if (kp.epi_px >= 0.0) return 0;  // the band form is matched by the speculative kernel
+uint32_t join_grid(const KParams& kp, uint32_t na_max, uint32_t n_items, uint32_t ntc, uint32_t ctas_per_sm) {
+  if (kp.epi_px >= 0.0) return 0;  // the band form is matched by the per-query kernels
   int dev = 0, nsm = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (join_smem_bytes(kc_of(kp.top_k), na_max) + 4096 > (size_t)optin) return 0;
   uint32_t occ = 0;
-  if (join_dispatch(kp.top_k, nullptr, kp.tau < kp.code_bits, 0, 0, &occ, na_max, false) != cudaSuccess) {
+  if (join_dispatch(kp.top_k, nullptr, kp.tau < kp.code_bits, ntc, 0, 0, &occ, na_max, false) != cudaSuccess) {
     cudaGetLastError();
     occ = 0;
   }
+  if (ctas_per_sm && ctas_per_sm < occ) occ = ctas_per_sm;
   const uint64_t gr = (uint64_t)nsm * occ;
   return (uint32_t)(n_items < gr ? n_items : gr);
 }
 
 cudaError_t launch_join_calibrate(const MatchArgs& a, cudaStream_t s) {
   if (a.n_pairs == 0) return cudaSuccess;
-  return join_dispatch(a.kp.top_k, &a, a.kp.tau < a.kp.code_bits, 0, s, nullptr, a.na_max, true);
+  return join_dispatch(a.kp.top_k, &a, a.kp.tau < a.kp.code_bits, 4, 0, s, nullptr, a.na_max, true);
 }
 
-cudaError_t launch_join(const MatchArgs& a, uint32_t grid, cudaStream_t s) {
+cudaError_t launch_join(const MatchArgs& a, uint32_t grid, uint32_t ntc, cudaStream_t s) {
   if (a.n_items == 0 || grid == 0) return cudaSuccess;
-  return join_dispatch(a.kp.top_k, &a, a.kp.tau < a.kp.code_bits, grid, s, nullptr, a.na_max, false);
+  return join_dispatch(a.kp.top_k, &a, a.kp.tau < a.kp.code_bits, ntc, grid, s, nullptr, a.na_max, false);
 }
 
 }  // namespace chx

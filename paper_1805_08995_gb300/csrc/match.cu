@@ -75,6 +75,48 @@ __device__ __forceinline__ bool epi_keep(double la, double lb, double lc, double
   return __dmul_rn(num, num) <= rhs;
 }
 
+// The band test of one query: the FP64 line and right-hand side exactly as
+// the definition above computes them, and their FP32 roundings.
+struct EpiQ {
+  double la, lb, lc, rhs;
+  float a, b, c, r;
+};
+
+__device__ __forceinline__ EpiQ epi_query(const double* F, float2 pq, double dd) {
+  EpiQ e;
+  epi_line(F, pq, dd, e.la, e.lb, e.lc, e.rhs);
+  e.a = __double2float_rn(e.la);
+  e.b = __double2float_rn(e.lb);
+  e.c = __double2float_rn(e.lc);
+  e.r = __double2float_rn(e.rhs);
+  return e;
+}
+
+// The FP64 decision as a real call: inlined, the compiler may predicate it and
+// run it for every candidate, which makes the FP64 pipe the limit.
+__device__ __noinline__ bool epi_keep_fp64(const EpiQ& e, float2 pc) {
+  return epi_keep(e.la, e.lb, e.lc, e.rhs, pc);
+}
+
+// epi_keep, decided in FP32 when the FP32 difference r - n^2 clears a bound on
+// its distance from the FP64 difference, else by epi_keep itself.  With
+// u = 2^-24: a, b, c carry one rounding each and n two FMA roundings, so
+// |n32 - n64| <= 3.01 u S, S = |a x'| + |b y'| + |c| (the FP64 evaluation's own
+// error, ~3 * 2^-53 S, is inside the slack); then |(r - n^2)32 - (rhs - num^2)64|
+// <= 2u r + 3u n^2 + e_n (2|n| + e_n).  The margins below are 6.7u and 8.4u, plus
+// an absolute 1e-30 for underflow; overflow or NaN fails both comparisons.
+__device__ __forceinline__ bool epi_keep_fast(const EpiQ& e, float2 pc) {
+  const float n = fmaf(e.a, pc.x, fmaf(e.b, pc.y, e.c));
+  const float S = fmaf(fabsf(e.a), fabsf(pc.x), fmaf(fabsf(e.b), fabsf(pc.y), fabsf(e.c)));
+  const float lhs = n * n;
+  const float diff = e.r - lhs;
+  const float en = 4.0e-7f * S;
+  const float err = fmaf(en, fmaf(2.0f, fabsf(n), en), fmaf(5.0e-7f, e.r + lhs, 1.0e-30f));
+  if (diff > err) return true;
+  if (diff < -err) return false;
+  return epi_keep_fp64(e, pc);
+}
+
 __device__ __forceinline__ uint32_t hamming128(uint4 a, uint4 b) {
   return __popc(a.x ^ b.x) + __popc(a.y ^ b.y) + __popc(a.z ^ b.z) + __popc(a.w ^ b.w);
 }
@@ -119,12 +161,11 @@ __global__ void __launch_bounds__(TPB, (TPB <= 512 ? 2 : 1)) k_match(MatchArgs a
     const bool valid = q < P.nA;
     uint4 qc = make_uint4(0u, 0u, 0u, 0u);
     uint2 qb = make_uint2(0u, 0u);
-    double la = 0.0, lb = 0.0, lc = 0.0, rhs = 0.0;
+    EpiQ eq{};
     if (valid) {
       qc = __ldg(reinterpret_cast<const uint4*>(a.codes) + P.a0 + q);
       qb = __ldg(reinterpret_cast<const uint2*>(a.buckets) + P.a0 + q);
-      if (EPI) epi_line(a.F + 9 * (size_t)item.x, __ldg(reinterpret_cast<const float2*>(a.kpts) + P.a0 + q), dd, la, lb,
-                        lc, rhs);
+      if (EPI) eq = epi_query(a.F + 9 * (size_t)item.x, __ldg(reinterpret_cast<const float2*>(a.kpts) + P.a0 + q), dd);
     }
     uint32_t top[KC];
 #pragma unroll
@@ -174,7 +215,7 @@ __global__ void __launch_bounds__(TPB, (TPB <= 512 ? 2 : 1)) k_match(MatchArgs a
             const uint32_t h = hamming128(codes_s[jl], qc);
             uint32_t key = (h << 24) | (cb + jl);
             if (key >= thr_user) key = KEY_INF;                                 // Sec. 5
-            if (EPI && key != KEY_INF && !epi_keep(la, lb, lc, rhs, kp_s[jl])) key = KEY_INF;  // Sec. 6.2
+            if (EPI && key != KEY_INF && !epi_keep_fast(eq, kp_s[jl])) key = KEY_INF;  // Sec. 6.2
             if (SPEC) {
               if (filtered && key == KEY_INF) --nlook;
               if (key < thr) {
@@ -339,10 +380,8 @@ __global__ void __launch_bounds__(128) k_match_fallback(MatchArgs a) {
         const uint32_t q = (uint32_t)(g - P.qbase);
         const uint4 qc = __ldg(reinterpret_cast<const uint4*>(a.codes) + P.a0 + q);
         const uint2 qb = __ldg(reinterpret_cast<const uint2*>(a.buckets) + P.a0 + q);
-        double la = 0.0, lb = 0.0, lc = 0.0, rhs = 0.0;
-        if (EPI)
-          epi_line(a.F + 9 * (size_t)lo, __ldg(reinterpret_cast<const float2*>(a.kpts) + P.a0 + q), dd, la, lb, lc,
-                   rhs);
+        EpiQ eq{};
+        if (EPI) eq = epi_query(a.F + 9 * (size_t)lo, __ldg(reinterpret_cast<const float2*>(a.kpts) + P.a0 + q), dd);
         uint32_t top[KC];
 #pragma unroll
         for (int s = 0; s < KC; ++s) top[s] = KEY_INF;
@@ -359,8 +398,7 @@ __global__ void __launch_bounds__(128) k_match_fallback(MatchArgs a) {
               const uint32_t jl = il[pos];
               const uint32_t key = (hamming128(__ldg(gc + jl), qc) << 24) | (c * JC + jl);
               if (key >= thr_user) continue;
-              if (EPI && !epi_keep(la, lb, lc, rhs,
-                                   __ldg(reinterpret_cast<const float2*>(a.kpts) + P.b0 + (uint64_t)c * JC + jl)))
+              if (EPI && !epi_keep_fast(eq, __ldg(reinterpret_cast<const float2*>(a.kpts) + P.b0 + (uint64_t)c * JC + jl)))
                 continue;
               if (key < top[KC - 1]) topk_insert<KC>(top, key);
             }
@@ -457,7 +495,14 @@ cudaError_t run_kc(const MatchArgs* a, int spec, bool epi, uint32_t grid, cudaSt
   return epi ? run_match<KC, TPB, true, false>(a, grid, s, occ) : run_match<KC, TPB, false, false>(a, grid, s, occ);
 }
 
-cudaError_t dispatch(uint32_t k, const MatchArgs* a, int spec, bool epi, uint32_t grid, cudaStream_t s, uint32_t* occ) {
+// Queries per CTA of the speculative form: 512 (k <= 16 only) or 256.
+uint32_t spec_tpb(uint32_t k, uint32_t tile) {
+  if (k > 16) return 256;
+  return tile == 256 ? 256u : 512u;
+}
+
+cudaError_t dispatch(uint32_t k, const MatchArgs* a, int spec, bool epi, uint32_t grid, cudaStream_t s, uint32_t* occ,
+                     uint32_t tile) {
   if (!spec) {
     if (k <= 4) return run_kc<4, 256>(a, 0, epi, grid, s, occ);
     if (k <= 8) return run_kc<8, 256>(a, 0, epi, grid, s, occ);
@@ -465,26 +510,32 @@ cudaError_t dispatch(uint32_t k, const MatchArgs* a, int spec, bool epi, uint32_
     if (k <= 16) return run_kc<16, 256>(a, 0, epi, grid, s, occ);
     return run_kc<32, 256>(a, 0, epi, grid, s, occ);
   }
+  if (spec_tpb(k, tile) == 256) {
+    if (k <= 4) return run_kc<4, 256>(a, 1, epi, grid, s, occ);
+    if (k <= 8) return run_kc<8, 256>(a, 1, epi, grid, s, occ);
+    if (k <= 10) return run_kc<10, 256>(a, 1, epi, grid, s, occ);
+    if (k <= 16) return run_kc<16, 256>(a, 1, epi, grid, s, occ);
+    return run_kc<32, 256>(a, 1, epi, grid, s, occ);
+  }
   if (k <= 4) return run_kc<4, 512>(a, 1, epi, grid, s, occ);
   if (k <= 8) return run_kc<8, 512>(a, 1, epi, grid, s, occ);
   if (k <= 10) return run_kc<10, 512>(a, 1, epi, grid, s, occ);
-  if (k <= 16) return run_kc<16, 512>(a, 1, epi, grid, s, occ);
-  return run_kc<32, 256>(a, 1, epi, grid, s, occ);
+  return run_kc<16, 512>(a, 1, epi, grid, s, occ);
 }
 
 }  // namespace
 
-int match_tile_size(uint32_t top_k, int spec) {
+int match_tile_size(uint32_t top_k, int spec, uint32_t tile) {
   if (!spec) return 256;
-  return top_k <= 16 ? 512 : 256;
+  return (int)spec_tpb(top_k, tile);
 }
 
-uint32_t match_grid(uint32_t top_k, int spec, bool epi, uint32_t n_tables, uint32_t n_items) {
+uint32_t match_grid(uint32_t top_k, int spec, bool epi, uint32_t n_tables, uint32_t n_items, uint32_t tile) {
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   uint32_t occ = n_tables;
-  if (dispatch(top_k, nullptr, spec, epi, 0, 0, &occ) != cudaSuccess) {
+  if (dispatch(top_k, nullptr, spec, epi, 0, 0, &occ, tile) != cudaSuccess) {
     cudaGetLastError();
     occ = 1;
   }
@@ -492,9 +543,9 @@ uint32_t match_grid(uint32_t top_k, int spec, bool epi, uint32_t n_tables, uint3
   return (uint32_t)(n_items < g ? n_items : g);
 }
 
-cudaError_t launch_match(const MatchArgs& a, int spec, uint32_t grid, cudaStream_t s) {
+cudaError_t launch_match(const MatchArgs& a, int spec, uint32_t grid, cudaStream_t s, uint32_t tile) {
   if (grid == 0 || a.n_items == 0) return cudaSuccess;
-  return dispatch(a.kp.top_k, &a, spec, a.kp.epi_px >= 0.0, grid, s, nullptr);
+  return dispatch(a.kp.top_k, &a, spec, a.kp.epi_px >= 0.0, grid, s, nullptr, tile);
 }
 
 cudaError_t launch_match_fallback(const MatchArgs& a, cudaStream_t s) {

@@ -87,6 +87,18 @@ def test_create_rejects_bad_arguments_before_touching_a_device(lib):
     assert e.value.status == ch.CASHASH_EINVAL
 
 
+def test_tuning_calls_reject_null_arguments(lib):
+    """The plan tuning entry points check their arguments before any CUDA call."""
+    import ctypes as C
+    import paper_1805_08995_gb300 as ch
+    L = ch._load()
+    t = ch.cashash_tuning()
+    assert L.cashash_plan_get_tuning(None, C.byref(t)) == ch.CASHASH_EINVAL
+    assert L.cashash_plan_set_tuning(None, C.byref(t)) == ch.CASHASH_EINVAL
+    assert L.cashash_plan_autotune(None, None, None, 0, None) == ch.CASHASH_EINVAL
+    assert C.sizeof(ch.cashash_tuning) == 24
+
+
 def test_package_fails_loudly_without_library(tmp_path):
     """The product path has no CPU fallback: without libcashash.so it raises."""
     import sys

@@ -211,6 +211,84 @@ def test_batched_kernel_choice(ch, orc, case):
     ctx.close()
 
 
+def test_every_tuning_and_the_autotuner(ch, orc):
+    """Every kernel configuration of a batched plan reproduces the oracle's
+    lists (twice: direct launch, then graph replay); the autotuner keeps one
+    of them and reports its sample time."""
+    sizes = [3000, 4100, 900, 5200, 0]
+    s = synth.random_set(909, sizes)
+    pairs = _pairs(sizes)
+    p = ch.cashash_default_params(schedule=1)
+    ctx = ch.cashash_create(p, s.R)
+    ds = ch.DeviceSet(p, s.img_off, s.desc)
+    ch.cashash_build_codes(ctx, ds)
+    po = orc.params()
+    mu, codes, buckets = oracle_codes(orc, s.desc, s.R, po)
+    eoff, emt = orc.match_pairs(s.desc, s.img_off, codes, buckets, pairs, po)
+    plan = ch.cashash_plan_create(ctx, ds, pairs)
+    t0 = ch.cashash_plan_get_tuning(plan)
+    assert (t0["kernel"], t0["tile"], t0["ctas_per_sm"]) == (ch.CASHASH_KERNEL_JOIN, 4, 0)
+    P = len(pairs)
+    cap = int(s.sizes()[pairs[:, 0]].sum())
+    moff = torch.zeros(P + 1, dtype=torch.int64, device="cuda")
+    mt = torch.zeros((cap, 2), dtype=torch.int32, device="cuda")
+
+    def check():
+        for _ in range(2):
+            ch.cashash_match_plan(ctx, plan, moff, mt, cap)
+            assert ch.cashash_sync_status(ctx) == ch.CASHASH_OK
+            off = moff.cpu().numpy().astype(np.uint64)
+            assert np.array_equal(off, eoff)
+            assert np.array_equal(mt[:int(off[-1])].cpu().numpy().view(np.uint32), emt)
+
+    J, Q = ch.CASHASH_KERNEL_JOIN, ch.CASHASH_KERNEL_QUERY
+    for kern, tile, ctas in [(J, 4, 0), (J, 2, 0), (J, 4, 1), (J, 2, 1), (Q, 512, 0), (Q, 256, 0)]:
+        ch.cashash_plan_set_tuning(plan, kern, tile, ctas)
+        t = ch.cashash_plan_get_tuning(plan)
+        assert (t["kernel"], t["tile"], t["ctas_per_sm"]) == (kern, tile, ctas)
+        check()
+    t = ch.cashash_plan_autotune(ctx, plan, max_pairs=5)
+    assert t["kernel"] in (J, Q) and t["ms_sample"] > 0
+    check()
+    plan.close()
+    ctx.close()
+
+
+def test_autotuner_with_the_band(ch, orc):
+    """With the band on the join does not apply: forcing it is refused and the
+    autotuner chooses among the per-query tiles; results stay exact."""
+    import math
+    s = synth.epipolar_set(44, n_views=4, n_points=9000, arc=2 * math.pi * 4 / 250, z_max=0.355)
+    pairs = np.concatenate([s.pairs, s.pairs[:, ::-1]])
+    s.F = np.concatenate([s.F, s.F.reshape(-1, 3, 3).transpose(0, 2, 1).reshape(-1, 9)])
+    pk = dict(schedule=1, epi_px=4.0)
+    p = ch.cashash_default_params(**pk)
+    ctx = ch.cashash_create(p, s.R)
+    ds = ch.DeviceSet(p, s.img_off, s.desc, s.kpts)
+    ch.cashash_build_codes(ctx, ds)
+    plan = ch.cashash_plan_create(ctx, ds, pairs)
+    assert ch.cashash_plan_get_tuning(plan)["kernel"] == ch.CASHASH_KERNEL_QUERY
+    with pytest.raises(ch.CashashError):
+        ch.cashash_plan_set_tuning(plan, ch.CASHASH_KERNEL_JOIN, 4, 0)
+    F = torch.from_numpy(np.ascontiguousarray(s.F)).cuda()
+    t = ch.cashash_plan_autotune(ctx, plan, F=F, max_pairs=3)
+    assert t["kernel"] == ch.CASHASH_KERNEL_QUERY and t["ms_sample"] > 0
+    P = len(pairs)
+    cap = int(s.sizes()[pairs[:, 0]].sum())
+    moff = torch.zeros(P + 1, dtype=torch.int64, device="cuda")
+    mt = torch.zeros((cap, 2), dtype=torch.int32, device="cuda")
+    ch.cashash_match_plan(ctx, plan, moff, mt, cap, F=F)
+    assert ch.cashash_sync_status(ctx) == ch.CASHASH_OK
+    po = oparams(orc, pk)
+    mu, codes, buckets = oracle_codes(orc, s.desc, s.R, po)
+    eoff, emt = orc.match_pairs(s.desc, s.img_off, codes, buckets, pairs, po, F=s.F, kpts=s.kpts)
+    off = moff.cpu().numpy().astype(np.uint64)
+    assert np.array_equal(off, eoff)
+    assert np.array_equal(mt[:int(off[-1])].cpu().numpy().view(np.uint32), emt)
+    plan.close()
+    ctx.close()
+
+
 def test_lookup_tables_are_the_bucket_sets(ch, orc):
     sizes = [5000, 10, 0, 3968, 7937]
     s = synth.random_set(303, sizes)
@@ -311,6 +389,44 @@ def test_epipolar_band(ch, orc, sched):
     both = np.concatenate([s.pairs, s.pairs[:, ::-1]])
     s.F = np.concatenate([s.F, s.F.reshape(-1, 3, 3).transpose(0, 2, 1).reshape(-1, 9)])
     check_case(ch, orc, s, both, schedule=sched, epi_px=4.0)
+
+
+@pytest.mark.parametrize("sched", [0, 1])
+def test_band_edge_decisions(ch, orc, sched):
+    """Sec. 6.2 at the edge of the band: candidate j is a copy of query j (so it
+    shares every bucket) placed on one of the two lines at 4 px from the
+    query's epipolar line, moved by a few ulps or not at all.  The kernels'
+    FP32 pre-test must defer these to the FP64 predicate and agree with the
+    oracle on every one."""
+    import math
+    rng = np.random.default_rng(515)
+    nA = 1200
+    A = synth.sift_like(rng, nA)
+    desc = np.concatenate([A, A])
+    img_off = np.array([0, nA, 2 * nA], np.uint64)
+    M = rng.standard_normal((3, 3))
+    U, S, Vt = np.linalg.svd(M)
+    S[2] = 0.0
+    F = (U * S) @ Vt
+    F /= np.linalg.norm(F)
+    kA = (rng.random((nA, 2)) * [1920.0, 1080.0]).astype(np.float32)
+    kB = np.empty((nA, 2), np.float32)
+    d = 4.0
+    for j in range(nA):
+        x, y = float(kA[j, 0]), float(kA[j, 1])
+        a = (F[0, 0] * x + F[0, 1] * y) + F[0, 2]
+        b = (F[1, 0] * x + F[1, 1] * y) + F[1, 2]
+        c = (F[2, 0] * x + F[2, 1] * y) + F[2, 2]
+        nrm = math.hypot(a, b)
+        t = rng.uniform(-60.0, 60.0) if j % 2 else rng.uniform(-900.0, 900.0)
+        p0 = np.array([-c * a, -c * b]) / nrm ** 2 + t * np.array([-b, a]) / nrm
+        off = rng.choice([-1.0, 1.0]) * d * (1.0 + rng.choice([-3e-7, -1e-7, 0.0, 1e-7, 3e-7]))
+        kB[j] = (p0 + off * np.array([a, b]) / nrm).astype(np.float32)
+    kpts = np.concatenate([kA, kB])
+    pairs = np.array([[0, 1]], np.uint32)
+    s = synth.ImageSet(desc, img_off, pairs, synth.projection_matrix(515), "band edge", F=F.reshape(1, 9),
+                       kpts=kpts)
+    check_case(ch, orc, s, pairs, schedule=sched, epi_px=d)
 
 
 def test_many_pairs_medium(ch, orc):
