@@ -39,7 +39,11 @@ POPC_PER_CLK_SM = 16          # 32-bit population counts per clock per SM (measu
 L2_FLUSH_BYTES = 256 << 20
 # DRAM traffic per lookup entry of the matching kernel, from the ncu capture
 # summarised in profiles/ (valid only for the kernel source it was taken on).
-PROFILED_TRAFFIC = {}
+PROFILED_TRAFFIC = {
+    "k_join": {"source": "paper_1805_08995_gb300/csrc/join.cu",
+               "sha256": "5fb1fa9ae0015ec55e6b8dbc09c52ecee4b8addc259f1f9c759591d585ed0456",
+               "bytes_per_entry": 3.597602e9 / 861951265},
+}
 
 
 def source_sha256(rel: str):
