@@ -294,7 +294,8 @@ def run_ours(args):
     F_dev = torch.from_numpy(np.ascontiguousarray(s.F)).to(dev) if band else None
     tuning = ch.cashash_plan_get_tuning(plan)
     if sched == ch.CASHASH_SCHED_PERSISTENT and not args.no_autotune:
-        tuning = ch.cashash_plan_autotune(ctx, plan, F=F_dev, max_pairs=512, stream=stream)
+        ch.cashash_build_codes(ctx, ds, stream=stream)  # the tuner matches the set's current codes
+        tuning = ch.cashash_plan_autotune(ctx, plan, F=F_dev, max_pairs=0, stream=stream)
     ch.cashash_set_profiling(ctx, True)
     for _ in range(args.warmup):
         flush.zero_()

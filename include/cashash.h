@@ -207,12 +207,19 @@ int cashash_plan_get_tuning(const cashash_plan* plan, cashash_tuning* out);
  * ENOTSUP (the join does not apply to this plan), ENOMEM, ECUDA. */
 int cashash_plan_set_tuning(cashash_plan* plan, const cashash_tuning* t);
 
-/* Autotuner: times every applicable configuration on a sample of at most
- * max_pairs of the plan's pairs (0 = 512; spread over the pairs' N_A * N_B
- * cost order), three runs each after two untimed ones, and keeps the plan's
- * default configuration unless another is more than 3 % faster (then the
- * fastest).  F_dev as for cashash_match_plan.  Synchronises `stream`;
- * allocates temporary device buffers.  Errors: EINVAL, ENOMEM, ECUDA. */
+/* Autotuner: times every applicable configuration (three runs after two
+ * untimed ones, in two interleaved rounds; a configuration more than 25 %
+ * behind after the first round is not timed again; each keeps its minimum) and
+ * keeps the plan's default configuration unless another is more than 3 %
+ * faster (then the fastest).  max_pairs == 0 (or >= the plan's
+ * pairs): on the plan itself, which is exact about locality and tails but
+ * costs up to about 60 plan runs; else on a sample of the plan's pairs spread over
+ * their N_A * N_B cost order, max(max_pairs, 16 per SM) pairs so that the
+ * tails of the persistent kernels weigh roughly as in the full run.  F_dev as
+ * for cashash_match_plan.  Call it after cashash_build_codes for the plan's
+ * set: the timed runs match the set's current codes.  Synchronises `stream`;
+ * allocates temporary device buffers (outputs of the timed runs); the plan's
+ * thresholds start afresh.  Errors: EINVAL, ENOMEM, ECUDA. */
 int cashash_plan_autotune(cashash_ctx* ctx, cashash_plan* plan, const double* F_dev, uint32_t max_pairs,
                           cashash_stream_t stream);
 

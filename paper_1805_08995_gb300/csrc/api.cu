@@ -878,24 +878,37 @@ int cashash_plan_autotune(cashash_ctx* c, cashash_plan* pl, const double* F_dev,
   CK(cudaSetDevice(c->device));
   CK(cudaStreamSynchronize(stream));
   const uint32_t P = pl->P;
-  const uint32_t S = std::min<uint32_t>(P, max_pairs ? max_pairs : 512u);
-  // the sample: S pairs spread over the plan's cost order
-  std::vector<uint32_t> order(P);
-  for (uint32_t i = 0; i < P; ++i) order[i] = i;
-  std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
-    return (uint64_t)pl->info[x].nA * pl->info[x].nB > (uint64_t)pl->info[y].nA * pl->info[y].nB;
-  });
-  std::vector<uint32_t> pick(S), sub(2 * (size_t)S);
+  // max_pairs == 0 (or >= P): the candidates run on the plan itself.  Else on a
+  // sample spread over the plan's cost order, with enough pairs per SM that the
+  // persistent kernels' tails weigh as in the full run (a join item is a pair).
+  const bool whole = max_pairs == 0 || max_pairs >= P;
+  int nsm = 0;
+  CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
+  const uint32_t S = whole ? P : std::min<uint32_t>(P, std::max<uint32_t>(max_pairs, 16u * (uint32_t)nsm));
+  std::vector<uint32_t> pick;
   uint64_t cap = 0;
-  for (uint32_t i = 0; i < S; ++i) {
-    pick[i] = order[(uint32_t)(((uint64_t)i * P) / S)];
-    sub[2 * (size_t)i] = pl->pairs_h[2 * (size_t)pick[i]];
-    sub[2 * (size_t)i + 1] = pl->pairs_h[2 * (size_t)pick[i] + 1];
-    cap += pl->info[pick[i]].nA;
+  cashash_plan* sp = pl;
+  int st = CASHASH_OK;
+  if (!whole) {
+    std::vector<uint32_t> order(P);
+    for (uint32_t i = 0; i < P; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
+      return (uint64_t)pl->info[x].nA * pl->info[x].nB > (uint64_t)pl->info[y].nA * pl->info[y].nB;
+    });
+    pick.resize(S);
+    std::vector<uint32_t> sub(2 * (size_t)S);
+    for (uint32_t i = 0; i < S; ++i) {
+      pick[i] = order[(uint32_t)(((uint64_t)i * P) / S)];
+      sub[2 * (size_t)i] = pl->pairs_h[2 * (size_t)pick[i]];
+      sub[2 * (size_t)i + 1] = pl->pairs_h[2 * (size_t)pick[i] + 1];
+      cap += pl->info[pick[i]].nA;
+    }
+    sp = nullptr;
+    st = cashash_plan_create(c, &pl->set, sub.data(), S, &sp);
+    if (st != CASHASH_OK) return st;
+  } else {
+    cap = pl->n_res;
   }
-  cashash_plan* sp = nullptr;
-  int st = cashash_plan_create(c, &pl->set, sub.data(), S, &sp);
-  if (st != CASHASH_OK) return st;
   double* dF = nullptr;
   uint64_t* dmo = nullptr;
   uint32_t* dmt = nullptr;
@@ -903,11 +916,13 @@ int cashash_plan_autotune(cashash_ctx* c, cashash_plan* pl, const double* F_dev,
   uint64_t c1 = 0, c2 = 0, c3 = 0;
   st = grow(dmo, c1, (uint64_t)S + 1);
   if (st == CASHASH_OK) st = grow(dmt, c2, 2 * std::max<uint64_t>(cap, 1));
-  if (st == CASHASH_OK && F_dev && c->p.epi_px >= 0.0) {
+  const double* Fs = whole ? F_dev : nullptr;
+  if (!whole && st == CASHASH_OK && F_dev && c->p.epi_px >= 0.0) {
     st = grow(dF, c3, 9 * (uint64_t)S);
     for (uint32_t i = 0; st == CASHASH_OK && i < S; ++i)
       st = cuda_err(cudaMemcpyAsync(dF + 9 * (size_t)i, F_dev + 9 * (size_t)pick[i], 9 * sizeof(double),
                                     cudaMemcpyDeviceToDevice, stream));
+    Fs = dF;
   }
   if (st == CASHASH_OK) st = cuda_err(cudaEventCreate(&e0));
   if (st == CASHASH_OK) st = cuda_err(cudaEventCreate(&e1));
@@ -928,39 +943,57 @@ int cashash_plan_autotune(cashash_ctx* c, cashash_plan* pl, const double* F_dev,
     t.tile = tile;
     cand.push_back(t);
   }
-  // the first applicable candidate is the plan's default; another replaces it
-  // only when it is more than 3 % faster on the sample
+  // Two interleaved rounds (so that clock and cache drift hit every candidate),
+  // each candidate's time the minimum of its rounds; a candidate more than 25 %
+  // behind the best after the first round is not timed again.  The first
+  // applicable candidate is the plan's default; another replaces it only when
+  // it is more than 3 % faster.
+  const size_t nc = cand.size();
+  std::vector<double> tbest(nc, -1.0);
+  std::vector<cashash_tuning> tnorm(nc);
+  for (int round = 0; round < 2 && st == CASHASH_OK; ++round) {
+    double lead = -1.0;
+    for (size_t ci = 0; ci < nc && round == 1; ++ci)
+      if (tbest[ci] >= 0.0 && (lead < 0.0 || tbest[ci] < lead)) lead = tbest[ci];
+    for (size_t ci = 0; ci < nc; ++ci) {
+      if (st != CASHASH_OK) break;
+      if (round == 1 && (tbest[ci] < 0.0 || tbest[ci] > 1.25 * lead)) continue;
+      const cashash_tuning& t0 = cand[ci];
+      const int cs = plan_configure(sp, t0);
+      if (cs == CASHASH_ENOTSUP) continue;
+      if (cs != CASHASH_OK) {
+        st = cs;
+        break;
+      }
+      if (t0.kernel == CASHASH_KERNEL_QUERY && sp->tune.tile != t0.tile) continue;  // normalised to another one
+      // fresh thresholds: two untimed runs calibrate them, three timed runs follow
+      st = cuda_err(cudaMemsetAsync(sp->d_tau, 0, sizeof(uint32_t) * S, stream));
+      if (st == CASHASH_OK && sp->d_jhist)
+        st = cuda_err(cudaMemsetAsync(sp->d_jhist, 0, sizeof(uint32_t) * (size_t)S * HBINS, stream));
+      float ms = 0.f;
+      for (int r = 0; r < 5 && st == CASHASH_OK; ++r) {
+        if (r == 2) st = cuda_err(cudaEventRecord(e0, stream));
+        if (st == CASHASH_OK) st = enqueue_match(c, sp, Fs, dmo, dmt, cap, stream, false);
+      }
+      if (st == CASHASH_OK) st = cuda_err(cudaEventRecord(e1, stream));
+      if (st == CASHASH_OK) st = cuda_err(cudaEventSynchronize(e1));
+      if (st == CASHASH_OK) st = cuda_err(cudaEventElapsedTime(&ms, e0, e1));
+      if (st != CASHASH_OK) break;
+      const double t_ms = ms / 3.0;
+      tnorm[ci] = sp->tune;
+      if (tbest[ci] < 0.0 || t_ms < tbest[ci]) tbest[ci] = t_ms;
+    }
+  }
   cashash_tuning best{};
   double best_ms = -1.0, def_ms = -1.0;
-  for (const cashash_tuning& t0 : cand) {
-    if (st != CASHASH_OK) break;
-    const int cs = plan_configure(sp, t0);
-    if (cs == CASHASH_ENOTSUP) continue;
-    if (cs != CASHASH_OK) {
-      st = cs;
-      break;
-    }
-    if (t0.kernel == CASHASH_KERNEL_QUERY && sp->tune.tile != t0.tile) continue;  // normalised to another candidate
-    // fresh thresholds: two untimed runs calibrate them, three timed runs follow
-    st = cuda_err(cudaMemsetAsync(sp->d_tau, 0, sizeof(uint32_t) * S, stream));
-    if (st == CASHASH_OK && sp->d_jhist)
-      st = cuda_err(cudaMemsetAsync(sp->d_jhist, 0, sizeof(uint32_t) * (size_t)S * HBINS, stream));
-    float ms = 0.f;
-    for (int r = 0; r < 5 && st == CASHASH_OK; ++r) {
-      if (r == 2) st = cuda_err(cudaEventRecord(e0, stream));
-      if (st == CASHASH_OK) st = enqueue_match(c, sp, dF, dmo, dmt, cap, stream, false);
-    }
-    if (st == CASHASH_OK) st = cuda_err(cudaEventRecord(e1, stream));
-    if (st == CASHASH_OK) st = cuda_err(cudaEventSynchronize(e1));
-    if (st == CASHASH_OK) st = cuda_err(cudaEventElapsedTime(&ms, e0, e1));
-    if (st != CASHASH_OK) break;
-    const double t_ms = ms / 3.0;
+  for (size_t ci = 0; ci < nc; ++ci) {
+    if (tbest[ci] < 0.0) continue;
     if (def_ms < 0.0) {
-      def_ms = best_ms = t_ms;
-      best = sp->tune;
-    } else if (t_ms < 0.97 * def_ms && t_ms < best_ms) {
-      best_ms = t_ms;
-      best = sp->tune;
+      def_ms = best_ms = tbest[ci];
+      best = tnorm[ci];
+    } else if (tbest[ci] < 0.97 * def_ms && tbest[ci] < best_ms) {
+      best_ms = tbest[ci];
+      best = tnorm[ci];
     }
   }
   c->profiling = prof;
@@ -969,11 +1002,15 @@ int cashash_plan_autotune(cashash_ctx* c, cashash_plan* pl, const double* F_dev,
   dfree(dF);
   dfree(dmo);
   dfree(dmt);
-  cashash_plan_destroy(sp);
+  if (!whole) cashash_plan_destroy(sp);
   if (st != CASHASH_OK) return st;
   if (best_ms < 0.0) return CASHASH_OK;
   st = plan_configure(pl, best);
   if (st == CASHASH_OK) pl->tune.ms_sample = best_ms;
+  if (st == CASHASH_OK && whole) {  // thresholds are learned afresh by the chosen kernel
+    st = cuda_err(cudaMemset(pl->d_tau, 0, sizeof(uint32_t) * P));
+    if (st == CASHASH_OK && pl->d_jhist) st = cuda_err(cudaMemset(pl->d_jhist, 0, sizeof(uint32_t) * (size_t)P * HBINS));
+  }
   return st;
 }
 

@@ -240,10 +240,13 @@ cudaError_t launch_project_fp32(const uint8_t* desc, uint64_t n, const float* R3
 // ---------------------------------------------------------------------------
 // Exact re-evaluation of flagged (feature, row) projections: the double
 // sequence t = x_j - mu_j, p = R_bj * t, s = s + p for j = 0..127, each
-// rounded to nearest (explicit _rn intrinsics, so no contraction).  One
-// flagged feature per thread, so a warp runs 32 independent chains; within a
-// chain the products are formed ahead of the (ordered) additions.  Bits that
-// come out 1 are ORed into the codes / bucket bytes (they were written as 0).
+// rounded to nearest (explicit _rn intrinsics, so no contraction).  A warp
+// takes 32 flagged features and evaluates their flagged rows 32 at a time,
+// one (feature, row) per lane, so every FP64 instruction runs with full lanes
+// (a feature has one to a few flagged rows; an FP64 instruction costs the
+// pipe the same with 6 active lanes as with 32).  Within a chain the products
+// are formed ahead of the (ordered) additions.  Bits that come out 1 are ORed
+// into the codes / bucket bytes (they were written as 0).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_fix_fp64(const uint8_t* __restrict__ desc, const double* __restrict__ mu,
                                                   const double* __restrict__ R, KParams kp,
@@ -256,50 +259,86 @@ __global__ void __launch_bounds__(256) k_fix_fp64(const uint8_t* __restrict__ de
   __shared__ double mu_s[DIM];
   for (int i = threadIdx.x; i < DIM; i += blockDim.x) mu_s[i] = mu[i];
   __syncthreads();
+  const int lane = threadIdx.x & 31;
   uint64_t nf = *nflag_feat;
   if (nf > max_feat) nf = max_feat;
+  const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nwarp = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   unsigned long long done = 0;
-  for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < nf;
-       idx += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t f = flaglist[idx];
-    const uint4* xr = reinterpret_cast<const uint4*>(desc + f * DIM);
+  for (uint64_t base = warp * 32; base < nf; base += nwarp * 32) {
+    // this lane's feature and its flagged rows (bit r of word k: row 32 k + r)
+    const uint64_t idx = base + lane;
+    const bool valid = idx < nf;
+    const uint32_t f = valid ? flaglist[idx] : 0u;
+    uint32_t m[6], cnt = 0;
+#pragma unroll
     for (int k = 0; k < 6; ++k) {
-      uint32_t m = flagmask[f * 6 + k];
-      while (m) {
-        const uint32_t row = 32 * k + (__ffs(m) - 1);
-        m &= m - 1;
-        ++done;
-        const double* Rr = R + (size_t)row * DIM;
-        double s = 0.0;
-        for (int c = 0; c < 8; ++c) {  // 16 descriptor bytes per step
-          const uint4 v = __ldg(xr + c);
-          const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-          double p[16];
+      m[k] = valid ? flagmask[(uint64_t)f * 6 + k] : 0u;
+      cnt += __popc(m[k]);
+    }
+    uint32_t incl = cnt;
 #pragma unroll
-          for (int e = 0; e < 16; ++e) {
-            const int j = 16 * c + e;
-            const double t = __dsub_rn((double)((w[e >> 2] >> (8 * (e & 3))) & 0xFFu), mu_s[j]);
-            p[e] = __dmul_rn(__ldg(Rr + j), t);
-          }
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t o = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+      if (lane >= d) incl += o;
+    }
+    const uint32_t excl = incl - cnt;
+    const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    for (uint32_t r0 = 0; r0 < total; r0 += 32) {
+      const uint32_t r = r0 + lane;
+      // owner: the lane whose rows [excl, incl) hold r (incl is non-decreasing)
+      uint32_t owner = 0;
 #pragma unroll
-          for (int e = 0; e < 16; ++e) s = __dadd_rn(s, p[e]);
+      for (uint32_t st = 16; st >= 1; st >>= 1) {
+        const uint32_t v = __shfl_sync(0xFFFFFFFFu, incl, owner + st - 1);
+        if (v <= r) owner += st;
+      }
+      owner = min(owner, 31u);
+      uint32_t k = r - __shfl_sync(0xFFFFFFFFu, excl, owner);
+      const uint32_t fo = __shfl_sync(0xFFFFFFFFu, f, owner);
+      uint32_t row = 0xFFFFFFFFu;
+#pragma unroll
+      for (int w = 0; w < 6; ++w) {
+        const uint32_t mw = __shfl_sync(0xFFFFFFFFu, m[w], owner);
+        const uint32_t c = __popc(mw);
+        if (row == 0xFFFFFFFFu) {
+          if (k < c) row = 32u * w + __fns(mw, 0u, (int)k + 1);
+          else k -= c;
         }
-        if (s > 0.0) {
-          if (row < kp.code_bits) {
-            atomicOr(&codes[f * 4 + (row >> 5)], 1u << (row & 31));
-          } else {
-            const uint32_t rt = row - kp.code_bits;
-            const uint32_t t = rt / kp.bits_per_table, i = rt % kp.bits_per_table;
-            const uint64_t byte = f * 8 + t;
-            atomicOr(reinterpret_cast<uint32_t*>(buckets) + (byte >> 2), 1u << (8 * (byte & 3) + i));
-          }
+      }
+      if (r >= total || row == 0xFFFFFFFFu) continue;
+      ++done;
+      const uint4* xr = reinterpret_cast<const uint4*>(desc + (uint64_t)fo * DIM);
+      const double* Rr = R + (size_t)row * DIM;
+      double s = 0.0;
+      for (int c = 0; c < 8; ++c) {  // 16 descriptor bytes per step
+        const uint4 v = __ldg(xr + c);
+        const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
+        double p[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          const int j = 16 * c + e;
+          const double t = __dsub_rn((double)((w4[e >> 2] >> (8 * (e & 3))) & 0xFFu), mu_s[j]);
+          p[e] = __dmul_rn(__ldg(Rr + j), t);
+        }
+#pragma unroll
+        for (int e = 0; e < 16; ++e) s = __dadd_rn(s, p[e]);
+      }
+      if (s > 0.0) {
+        if (row < kp.code_bits) {
+          atomicOr(&codes[(uint64_t)fo * 4 + (row >> 5)], 1u << (row & 31));
+        } else {
+          const uint32_t rt = row - kp.code_bits;
+          const uint32_t t = rt / kp.bits_per_table, i = rt % kp.bits_per_table;
+          const uint64_t byte = (uint64_t)fo * 8 + t;
+          atomicOr(reinterpret_cast<uint32_t*>(buckets) + (byte >> 2), 1u << (8 * (byte & 3) + i));
         }
       }
     }
   }
   // one counter update per warp
   for (int o = 16; o > 0; o >>= 1) done += __shfl_xor_sync(0xFFFFFFFFu, done, o);
-  if ((threadIdx.x & 31) == 0 && done) atomicAdd(n_reeval, done);
+  if (lane == 0 && done) atomicAdd(n_reeval, done);
 }
 
 cudaError_t launch_fix_fp64(const uint8_t* desc, const double* mu, const double* R, const KParams& kp,

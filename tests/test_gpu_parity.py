@@ -247,9 +247,10 @@ def test_every_tuning_and_the_autotuner(ch, orc):
         t = ch.cashash_plan_get_tuning(plan)
         assert (t["kernel"], t["tile"], t["ctas_per_sm"]) == (kern, tile, ctas)
         check()
-    t = ch.cashash_plan_autotune(ctx, plan, max_pairs=5)
-    assert t["kernel"] in (J, Q) and t["ms_sample"] > 0
-    check()
+    for mp in (5, 0):  # a sample, then the plan itself
+        t = ch.cashash_plan_autotune(ctx, plan, max_pairs=mp)
+        assert t["kernel"] in (J, Q) and t["ms_sample"] > 0
+        check()
     plan.close()
     ctx.close()
 
