@@ -163,9 +163,10 @@ void cashash_plan_destroy(cashash_plan* plan);
  * match_off is still complete, nothing beyond cap is written and
  * cashash_sync_status() returns EOVERFLOW.  Asynchronous on `stream`.
  * With the persistent schedule all pairs are matched by one batched kernel:
- * a bucket join whose Hamming distances come from the tensor cores when the
- * band is off and every query image fits its shared-memory counters (at
- * least 40,000 features), else a speculative per-query kernel; the launch sequence
+ * by default a bucket join whose Hamming distances come from the tensor cores
+ * when every query image fits its shared-memory counters (at least 40,000
+ * features), else a speculative per-query kernel (cashash_plan_autotune may
+ * choose otherwise); the launch sequence
  * is captured once as a CUDA graph (per set of output pointers, F and
  * profiling setting) and replayed on `stream`; calls on the same plan must
  * not overlap.
@@ -187,10 +188,11 @@ int cashash_plan_set_threshold_hint(cashash_plan* plan, uint32_t hamming, int fi
  * counterpart (it runs one kernel shape). */
 enum { CASHASH_KERNEL_JOIN = 1, CASHASH_KERNEL_QUERY = 2 };
 typedef struct {
-  uint32_t kernel;       /* CASHASH_KERNEL_JOIN: tensor-core bucket join (band off, query images that
-                            fit its shared-memory counters); CASHASH_KERNEL_QUERY: per-query
-                            speculative kernel over shared-memory staged table chunks */
-  uint32_t tile;         /* JOIN: candidate tiles of 8 columns held in registers (2 or 4);
+  uint32_t kernel;       /* CASHASH_KERNEL_JOIN: tensor-core bucket join (query images that fit its
+                            shared-memory counters); CASHASH_KERNEL_QUERY: per-query speculative
+                            kernel over shared-memory staged table chunks */
+  uint32_t tile;         /* JOIN: candidate tiles of 8 columns held in registers (2 or 4; 4 with
+                            the band);
                             QUERY: queries per CTA (256, or 512 when top_k <= 16) */
   uint32_t ctas_per_sm;  /* JOIN: resident CTAs per SM, 0 = as many as fit; QUERY: ignored */
   uint32_t reserved;
@@ -204,7 +206,8 @@ int cashash_plan_get_tuning(const cashash_plan* plan, cashash_tuning* out);
 
 /* Forces a configuration (fields normalised to supported values; the plan's
  * captured graph is dropped).  Errors: EINVAL (not a batched plan),
- * ENOTSUP (the join does not apply to this plan), ENOMEM, ECUDA. */
+ * ENOTSUP (the join does not apply to this plan: a query image exceeds its
+ * shared-memory counters), ENOMEM, ECUDA. */
 int cashash_plan_set_tuning(cashash_plan* plan, const cashash_tuning* t);
 
 /* Autotuner: times every applicable configuration (three runs after two

@@ -95,7 +95,8 @@ struct cashash_plan {
   cashash_tuning tune{};               // persistent schedule: kernel configuration
   uint32_t na_max = 1;                 // largest query image (bucket-join scratch)
   uint32_t* d_jhist = nullptr;         // bucket join: per-pair histogram of k-th Hamming distances
-  uint64_t cap_items = 0, cap_queue = 0;
+  float4* d_jline = nullptr;           // bucket join with the band: per-CTA query lines
+  uint64_t cap_items = 0, cap_queue = 0, cap_jline = 0;
   std::vector<uint32_t> first, count;  // per-pair item ranges (per-pair schedule)
   std::vector<PairInfo> info;          // host copies: pair records, pair list, the set and its offsets
   std::vector<uint32_t> pairs_h;
@@ -529,6 +530,7 @@ void cashash_plan_destroy(cashash_plan* pl) {
   dfree(pl->d_queue);
   dfree(pl->d_tau);
   dfree(pl->d_jhist);
+  dfree(pl->d_jline);
   if (pl->gexec) cudaGraphExecDestroy(pl->gexec);
   if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
   delete pl;
@@ -560,7 +562,7 @@ int plan_configure(cashash_plan* pl, cashash_tuning t) {
     pl->occ_grid = match_grid(c->p.top_k, 0, epi, c->p.n_tables, 0xFFFFFFFFu);
     t = cashash_tuning{};
   } else if (t.kernel == CASHASH_KERNEL_JOIN) {
-    t.tile = t.tile <= 2 ? 2u : 4u;
+    t.tile = (t.tile <= 2 && !epi) ? 2u : 4u;  // the band form has 4 candidate tiles only
     grid = join_grid(c->kp, pl->na_max, P, t.tile, t.ctas_per_sm);
     if (P && !grid) return CASHASH_ENOTSUP;
     join = true;
@@ -603,6 +605,8 @@ int plan_configure(cashash_plan* pl, cashash_tuning t) {
     const uint64_t q = join ? (uint64_t)grid * pl->na_max * JSEG : (uint64_t)grid * t.tile * QCAP;
     st = grow(pl->d_queue, pl->cap_queue, std::max<uint64_t>(q, 1));
   }
+  if (st == CASHASH_OK && join && epi)
+    st = grow(pl->d_jline, pl->cap_jline, std::max<uint64_t>((uint64_t)grid * pl->na_max, 1));
   if (st == CASHASH_OK && join && !pl->d_jhist) {
     uint64_t cap = 0;
     st = grow(pl->d_jhist, cap, std::max<uint64_t>((uint64_t)P * HBINS, 1));
@@ -740,6 +744,7 @@ int enqueue_match(cashash_ctx* c, cashash_plan* pl, const double* F_dev, uint64_
   a.join = pl->tables;
   a.jqueue = pl->d_queue;
   a.jhist = pl->d_jhist;
+  a.jline = pl->d_jline;
   a.na_max = pl->na_max;
   a.kp = c->kp;
   CK(cudaMemsetAsync(pl->d_item_ctr, 0, sizeof(unsigned int) * ((size_t)P + 1), stream));
@@ -747,7 +752,7 @@ int enqueue_match(cashash_ctx* c, cashash_plan* pl, const double* F_dev, uint64_
     a.items = pl->d_items;
     a.n_items = pl->n_items;
     a.item_ctr = pl->d_item_ctr + P;
-    if (pl->join) {
+    if (pl->join && c->p.epi_px < 0.0) {
       StageTimer tm(c, CASHASH_STAGE_CALIBRATE, stream, capturing);
       CK(launch_join_calibrate(a, stream));
     }
@@ -781,8 +786,9 @@ int enqueue_match(cashash_ctx* c, cashash_plan* pl, const double* F_dev, uint64_
 uint64_t match_launches(const cashash_plan* pl) {
   uint64_t n = pl->P ? 2 : 1;  // scan + compaction
   if (pl->persistent) {
-    // calibration + join, or the speculative kernel; then the fallback
-    n += (pl->grid ? (pl->join ? 2 : 1) : 0) + (pl->n_res ? 1 : 0);
+    // calibration (not with the band) + join, or the speculative kernel; then the fallback
+    const bool cal = pl->join && pl->ctx->p.epi_px < 0.0 && pl->P;
+    n += (pl->grid ? (cal ? 2 : 1) : 0) + (pl->n_res ? 1 : 0);
   } else {
     for (uint32_t i = 0; i < pl->P; ++i) n += pl->count[i] ? 1 : 0;
   }
@@ -829,7 +835,7 @@ int cashash_match_plan(cashash_ctx* c, cashash_plan* pl, const double* F_dev, ui
     if (c->profiling)  // the graph holds the stage events as external event-record nodes
       c->ev_used[CASHASH_STAGE_MATCH] = c->ev_used[CASHASH_STAGE_COMPACT] = 1;
       c->ev_used[CASHASH_STAGE_FALLBACK] = 1;
-      if (pl->join) c->ev_used[CASHASH_STAGE_CALIBRATE] = 1;
+      if (pl->join && c->p.epi_px < 0.0) c->ev_used[CASHASH_STAGE_CALIBRATE] = 1;
   } else {
     const int st = enqueue_match(c, pl, F_dev, match_off, matches, cap, stream, false);
     if (st != CASHASH_OK) return st;

@@ -107,6 +107,80 @@ __device__ __forceinline__ void write_feature(uint64_t f, const uint32_t* bits, 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Sec. 6.2 band test, shared by the matching kernels.
+// ---------------------------------------------------------------------------
+// The epipolar line of the query, l = F p_q, and d^2 (a^2 + b^2), in FP64.
+__device__ __forceinline__ void epi_line(const double* F, float2 pq, double dd, double& la, double& lb, double& lc,
+                                         double& rhs) {
+  const double x = (double)pq.x, y = (double)pq.y;
+  la = __dadd_rn(__dadd_rn(__dmul_rn(F[0], x), __dmul_rn(F[1], y)), F[2]);
+  lb = __dadd_rn(__dadd_rn(__dmul_rn(F[3], x), __dmul_rn(F[4], y)), F[5]);
+  lc = __dadd_rn(__dadd_rn(__dmul_rn(F[6], x), __dmul_rn(F[7], y)), F[8]);
+  rhs = __dmul_rn(dd, __dadd_rn(__dmul_rn(la, la), __dmul_rn(lb, lb)));
+}
+
+// Eq. 1-2, squared: keep p' iff (a x' + b y' + c)^2 <= d^2 (a^2 + b^2).
+__device__ __forceinline__ bool epi_keep(double la, double lb, double lc, double rhs, float2 pc) {
+  const double num = __dadd_rn(__dadd_rn(__dmul_rn(la, (double)pc.x), __dmul_rn(lb, (double)pc.y)), lc);
+  return __dmul_rn(num, num) <= rhs;
+}
+
+// The band test of one query: the FP64 line and right-hand side exactly as
+// epi_line computes them, and their FP32 roundings.
+struct EpiQ {
+  double la, lb, lc, rhs;
+  float a, b, c, r;
+};
+
+__device__ __forceinline__ EpiQ epi_query(const double* F, float2 pq, double dd) {
+  EpiQ e;
+  epi_line(F, pq, dd, e.la, e.lb, e.lc, e.rhs);
+  e.a = __double2float_rn(e.la);
+  e.b = __double2float_rn(e.lb);
+  e.c = __double2float_rn(e.lc);
+  e.r = __double2float_rn(e.rhs);
+  return e;
+}
+
+// epi_keep decided in FP32 from the FP32 roundings (a, b, c, r) of the line
+// and right-hand side: 1 keep, 0 drop, 2 undecided (decide in FP64).  The
+// FP32 difference r - n^2 is trusted when it clears a bound on its distance
+// from the FP64 difference.  With u = 2^-24: a, b, c carry one rounding each
+// and n two FMA roundings, so |n32 - n64| <= 3.01 u S, S = |a x'| + |b y'| + |c|
+// (the FP64 evaluation's own error, ~3 * 2^-53 S, is inside the slack); then
+// |(r - n^2)32 - (rhs - num^2)64| <= 2u r + 3u n^2 + e_n (2|n| + e_n).  The
+// margins below are 6.7u and 8.4u, plus an absolute 1e-30 for underflow;
+// overflow or NaN fails both comparisons.
+__device__ __forceinline__ int epi_test32(float a, float b, float c, float r, float2 pc) {
+  const float n = fmaf(a, pc.x, fmaf(b, pc.y, c));
+  const float S = fmaf(fabsf(a), fabsf(pc.x), fmaf(fabsf(b), fabsf(pc.y), fabsf(c)));
+  const float lhs = n * n;
+  const float diff = r - lhs;
+  const float en = 4.0e-7f * S;
+  const float err = fmaf(en, fmaf(2.0f, fabsf(n), en), fmaf(5.0e-7f, r + lhs, 1.0e-30f));
+  if (diff > err) return 1;
+  if (diff < -err) return 0;
+  return 2;
+}
+
+// The FP64 decisions as real calls: inlined, the compiler may predicate them
+// and run them for every candidate, which makes the FP64 pipe the limit.
+static __device__ __noinline__ bool epi_keep_fp64(const EpiQ& e, float2 pc) {
+  return epi_keep(e.la, e.lb, e.lc, e.rhs, pc);
+}
+
+static __device__ __noinline__ bool epi_keep_fp64_F(const double* F, float2 pq, double dd, float2 pc) {
+  double la, lb, lc, rhs;
+  epi_line(F, pq, dd, la, lb, lc, rhs);
+  return epi_keep(la, lb, lc, rhs, pc);
+}
+
+__device__ __forceinline__ bool epi_keep_fast(const EpiQ& e, float2 pc) {
+  const int d = epi_test32(e.a, e.b, e.c, e.r, pc);
+  return d == 2 ? epi_keep_fp64(e, pc) : d == 1;
+}
+
 #endif
 
 // ---- launchers (return cudaError_t of the launch) ----
@@ -156,6 +230,7 @@ struct MatchArgs {
   const uint8_t* join;       // bucket join: table buffer holding the bucket-sorted tables
   uint32_t* jqueue;          // bucket join: [grid][na_max][JSEG] survivor lists
   uint32_t* jhist;           // bucket join: [P][HBINS] k-th Hamming distances seen per pair
+  float4* jline;             // bucket join with the band: [grid][na_max] FP32 a, b, c, r per query
   uint32_t na_max;           // bucket join: largest query image of the plan
   KParams kp;
 };
@@ -165,8 +240,8 @@ cudaError_t launch_join_calibrate(const MatchArgs& a, cudaStream_t s);
 // ntc: candidate tiles of 8 columns held in registers (2 or 4).
 cudaError_t launch_join(const MatchArgs& a, uint32_t grid, uint32_t ntc, cudaStream_t s);
 // Resident CTAs of the join for n_items pairs (at most ctas_per_sm per SM when
-// non-zero); 0 when the join does not apply (band filter on, or the largest
-// query image exceeds its shared memory).
+// non-zero); 0 when the join does not apply (the largest query image exceeds
+// its shared memory).  The band form runs with 4 candidate tiles.
 uint32_t join_grid(const KParams& kp, uint32_t na_max, uint32_t n_items, uint32_t ntc, uint32_t ctas_per_sm);
 // Matching kernel launch.  spec = 0: direct register top-k (one pair per
 // launch); spec = 1: survivor queues with a speculative threshold (batched).

@@ -27,6 +27,11 @@
 // query whose list overflowed, or that holds fewer than k distinct survivors
 // while the guess turned some candidate away, is left PENDING for the exact
 // fallback kernel, so results never depend on the guess.
+//
+// With the Sec. 6.2 band (EPI) a candidate outside the band is no candidate at
+// all, so there is no Hamming guess: each entry is tested against the query's
+// epipolar line (FP32 roundings of the FP64 line, computed once per query and
+// pair; undecided entries in FP64) and only entries inside the band survive.
 #include <cuda_fp16.h>
 
 #include "internal.h"
@@ -166,7 +171,7 @@ __device__ __forceinline__ void load_offsets(const uint8_t* join, const PairInfo
 }
 
 // NTC: candidate tiles (of 8 columns) held in registers at a time.
-template <int KC, bool TAU, int NTC>
+template <int KC, bool TAU, int NTC, bool EPI>
 __global__ void __launch_bounds__(JT, 2) k_join(MatchArgs a) {
   extern __shared__ __align__(16) uint8_t jsm[];
   __shared__ uint32_t s_item, s_tau, s_task;
@@ -181,6 +186,9 @@ __global__ void __launch_bounds__(JT, 2) k_join(MatchArgs a) {
   uint32_t* dist_s = key_s + KC * JT;
   uint32_t* seg = a.jqueue + (size_t)blockIdx.x * a.na_max * JSEG;
   const uint32_t h_user = TAU ? kp.tau : 128u;  // Sec. 5: keys with H > tau are no candidates
+  float4* lines = EPI ? a.jline + (size_t)blockIdx.x * a.na_max : nullptr;  // per query: FP32 a, b, c, r
+  const double dd = kp.epi_px * kp.epi_px;
+  const float2* kpts = reinterpret_cast<const float2*>(a.kpts);
 
   for (;;) {
     __syncthreads();
@@ -203,11 +211,18 @@ __global__ void __launch_bounds__(JT, 2) k_join(MatchArgs a) {
       if (lane == 0) s_tau = gs;
     }
     const PairInfo P = s_P;
-    for (uint32_t q = tid; q < P.nA; q += JT) cnt_s[q] = 0;
+    const double* Fp = EPI ? a.F + 9 * (size_t)it : nullptr;
+    for (uint32_t q = tid; q < P.nA; q += JT) {
+      cnt_s[q] = 0;
+      if constexpr (EPI) {
+        const EpiQ e = epi_query(Fp, __ldg(kpts + P.a0 + q), dd);
+        lines[q] = make_float4(e.a, e.b, e.c, e.r);
+      }
+    }
     __syncthreads();
     // survivors: H <= h_thr
     uint32_t h_thr = h_user;
-    {
+    if (!EPI) {
       const uint32_t ts = s_tau;  // 0: no guess; else threshold + 1
       if (ts != 0 && ts - 1u < h_thr) h_thr = ts - 1u;
     }
@@ -295,6 +310,32 @@ __global__ void __launch_bounds__(JT, 2) k_join(MatchArgs a) {
           uint32_t ka = (acc_a | (acc_a >> 16)) & 0xFFu, kb = (acc_b | (acc_b >> 16)) & 0xFFu;
           ka &= va ? jok : 0u;
           kb &= vb ? jok : 0u;
+          if constexpr (EPI) {  // Sec. 6.2: only candidates inside the band
+            const float4 La = va ? lines[qa_c] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 Lb = vb ? lines[qb_c] : make_float4(0.f, 0.f, 0.f, 0.f);
+            uint32_t ba = 0, bb = 0;
+#pragma unroll
+            for (int n = 0; n < NTC; ++n)
+#pragma unroll
+              for (int c = 0; c < 2; ++c) {
+                const int bit = 2 * n + c;
+                if (((ka | kb) >> bit) & 1u) {
+                  const float2 pc = __ldg(kpts + P.b0 + jc[n][c]);
+                  if ((ka >> bit) & 1u) {
+                    int d = epi_test32(La.x, La.y, La.z, La.w, pc);
+                    if (d == 2) d = epi_keep_fp64_F(Fp, __ldg(kpts + P.a0 + qa_c), dd, pc) ? 1 : 0;
+                    ba |= (uint32_t)d << bit;
+                  }
+                  if ((kb >> bit) & 1u) {
+                    int d = epi_test32(Lb.x, Lb.y, Lb.z, Lb.w, pc);
+                    if (d == 2) d = epi_keep_fp64_F(Fp, __ldg(kpts + P.a0 + qb_c), dd, pc) ? 1 : 0;
+                    bb |= (uint32_t)d << bit;
+                  }
+                }
+              }
+            ka &= ba;
+            kb &= bb;
+          }
           if (ka | kb) {
             // one counter update per row, then the row's survivors at consecutive slots
             uint32_t pa = ka ? atomicAdd(cnt_s + qa_c, (uint32_t)__popc(ka)) : 0u;
@@ -359,7 +400,7 @@ __global__ void __launch_bounds__(JT, 2) k_join(MatchArgs a) {
           }
           pending = nlook > n;
         }
-        if (!pending && kth != KEY_INF && !a.tau_fixed) atomicAdd(s_hist + (kth >> 24), 1u);
+        if (!EPI && !pending && kth != KEY_INF && !a.tau_fixed) atomicAdd(s_hist + (kth >> 24), 1u);
       }
 #pragma unroll
       for (int s = 0; s < KC; ++s) key_s[s * JT + tid] = (valid && !pending) ? top[s] : KEY_INF;
@@ -510,7 +551,7 @@ __global__ void __launch_bounds__(CAL_SAMPLES) k_join_calibrate(MatchArgs a) {
 // ---------------------------------------------------------------------------
 namespace {
 
-template <int KC, bool TAU, int NTC>
+template <int KC, bool TAU, int NTC, bool EPI>
 cudaError_t run_join(const MatchArgs* a, uint32_t grid, cudaStream_t s, uint32_t* occ, uint32_t na_max,
                      bool calibrate) {
   static int attr_dev = -1;
@@ -521,14 +562,14 @@ cudaError_t run_join(const MatchArgs* a, uint32_t grid, cudaStream_t s, uint32_t
     int optin = 0;
     e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_join<KC, TAU, NTC>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - 2048);
+    e = cudaFuncSetAttribute(k_join<KC, TAU, NTC, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - 2048);
     if (e != cudaSuccess) return e;
     attr_dev = dev;
   }
   const size_t smem = join_smem_bytes(KC, na_max);
   if (occ) {
     int nb = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_join<KC, TAU, NTC>, JT, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_join<KC, TAU, NTC, EPI>, JT, smem);
     *occ = (uint32_t)(nb > 0 ? nb : 0);
     return e;
   }
@@ -539,31 +580,33 @@ cudaError_t run_join(const MatchArgs* a, uint32_t grid, cudaStream_t s, uint32_t
     k_join_calibrate<KC, TAU><<<want < (uint32_t)nsm * 8 ? want : (uint32_t)nsm * 8, CAL_SAMPLES, 0, s>>>(*a);
     return cudaGetLastError();
   }
-  k_join<KC, TAU, NTC><<<grid, JT, smem, s>>>(*a);
+  k_join<KC, TAU, NTC, EPI><<<grid, JT, smem, s>>>(*a);
   return cudaGetLastError();
 }
 
+// The band form is built with 4 candidate tiles only.
 template <int KC, bool TAU>
-cudaError_t run_join_nt(const MatchArgs* a, uint32_t ntc, uint32_t grid, cudaStream_t s, uint32_t* occ,
+cudaError_t run_join_nt(const MatchArgs* a, uint32_t ntc, bool epi, uint32_t grid, cudaStream_t s, uint32_t* occ,
                         uint32_t na_max, bool cal) {
-  return ntc <= 2 ? run_join<KC, TAU, 2>(a, grid, s, occ, na_max, cal)
-                  : run_join<KC, TAU, 4>(a, grid, s, occ, na_max, cal);
+  if (epi) return run_join<KC, TAU, 4, true>(a, grid, s, occ, na_max, cal);
+  return ntc <= 2 ? run_join<KC, TAU, 2, false>(a, grid, s, occ, na_max, cal)
+                  : run_join<KC, TAU, 4, false>(a, grid, s, occ, na_max, cal);
 }
 
 template <int KC>
-cudaError_t run_join_kc(const MatchArgs* a, bool tau, uint32_t ntc, uint32_t grid, cudaStream_t s, uint32_t* occ,
-                        uint32_t na_max, bool cal) {
-  return tau ? run_join_nt<KC, true>(a, ntc, grid, s, occ, na_max, cal)
-             : run_join_nt<KC, false>(a, ntc, grid, s, occ, na_max, cal);
+cudaError_t run_join_kc(const MatchArgs* a, bool tau, uint32_t ntc, bool epi, uint32_t grid, cudaStream_t s,
+                        uint32_t* occ, uint32_t na_max, bool cal) {
+  return tau ? run_join_nt<KC, true>(a, ntc, epi, grid, s, occ, na_max, cal)
+             : run_join_nt<KC, false>(a, ntc, epi, grid, s, occ, na_max, cal);
 }
 
-cudaError_t join_dispatch(uint32_t k, const MatchArgs* a, bool tau, uint32_t ntc, uint32_t grid, cudaStream_t s,
-                          uint32_t* occ, uint32_t na_max, bool cal) {
-  if (k <= 4) return run_join_kc<4>(a, tau, ntc, grid, s, occ, na_max, cal);
-  if (k <= 8) return run_join_kc<8>(a, tau, ntc, grid, s, occ, na_max, cal);
-  if (k <= 10) return run_join_kc<10>(a, tau, ntc, grid, s, occ, na_max, cal);
-  if (k <= 16) return run_join_kc<16>(a, tau, ntc, grid, s, occ, na_max, cal);
-  return run_join_kc<32>(a, tau, ntc, grid, s, occ, na_max, cal);
+cudaError_t join_dispatch(uint32_t k, const MatchArgs* a, bool tau, uint32_t ntc, bool epi, uint32_t grid,
+                          cudaStream_t s, uint32_t* occ, uint32_t na_max, bool cal) {
+  if (k <= 4) return run_join_kc<4>(a, tau, ntc, epi, grid, s, occ, na_max, cal);
+  if (k <= 8) return run_join_kc<8>(a, tau, ntc, epi, grid, s, occ, na_max, cal);
+  if (k <= 10) return run_join_kc<10>(a, tau, ntc, epi, grid, s, occ, na_max, cal);
+  if (k <= 16) return run_join_kc<16>(a, tau, ntc, epi, grid, s, occ, na_max, cal);
+  return run_join_kc<32>(a, tau, ntc, epi, grid, s, occ, na_max, cal);
 }
 
 int kc_of(uint32_t k) { return k <= 4 ? 4 : k <= 8 ? 8 : k <= 10 ? 10 : k <= 16 ? 16 : 32; }
@@ -571,14 +614,14 @@ int kc_of(uint32_t k) { return k <= 4 ? 4 : k <= 8 ? 8 : k <= 10 ? 10 : k <= 16 
 }  // namespace
 
 uint32_t join_grid(const KParams& kp, uint32_t na_max, uint32_t n_items, uint32_t ntc, uint32_t ctas_per_sm) {
-  if (kp.epi_px >= 0.0) return 0;  // the band form is matched by the per-query kernels
   int dev = 0, nsm = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (join_smem_bytes(kc_of(kp.top_k), na_max) + 4096 > (size_t)optin) return 0;
   uint32_t occ = 0;
-  if (join_dispatch(kp.top_k, nullptr, kp.tau < kp.code_bits, ntc, 0, 0, &occ, na_max, false) != cudaSuccess) {
+  if (join_dispatch(kp.top_k, nullptr, kp.tau < kp.code_bits, ntc, kp.epi_px >= 0.0, 0, 0, &occ, na_max, false) !=
+      cudaSuccess) {
     cudaGetLastError();
     occ = 0;
   }
@@ -588,13 +631,14 @@ uint32_t join_grid(const KParams& kp, uint32_t na_max, uint32_t n_items, uint32_
 }
 
 cudaError_t launch_join_calibrate(const MatchArgs& a, cudaStream_t s) {
-  if (a.n_pairs == 0) return cudaSuccess;
-  return join_dispatch(a.kp.top_k, &a, a.kp.tau < a.kp.code_bits, 4, 0, s, nullptr, a.na_max, true);
+  if (a.n_pairs == 0 || a.kp.epi_px >= 0.0) return cudaSuccess;  // the band form uses no threshold guess
+  return join_dispatch(a.kp.top_k, &a, a.kp.tau < a.kp.code_bits, 4, false, 0, s, nullptr, a.na_max, true);
 }
 
 cudaError_t launch_join(const MatchArgs& a, uint32_t grid, uint32_t ntc, cudaStream_t s) {
   if (a.n_items == 0 || grid == 0) return cudaSuccess;
-  return join_dispatch(a.kp.top_k, &a, a.kp.tau < a.kp.code_bits, ntc, grid, s, nullptr, a.na_max, false);
+  return join_dispatch(a.kp.top_k, &a, a.kp.tau < a.kp.code_bits, ntc, a.kp.epi_px >= 0.0, grid, s, nullptr,
+                       a.na_max, false);
 }
 
 }  // namespace chx

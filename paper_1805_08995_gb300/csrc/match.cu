@@ -59,64 +59,6 @@ __host__ __device__ inline size_t match_smem_bytes(uint32_t T, bool epi, int KC,
   return scan > fin ? scan : fin;
 }
 
-// Sec. 6.2: the epipolar line of the query, l = F p_q, and d^2 (a^2 + b^2).
-__device__ __forceinline__ void epi_line(const double* F, float2 pq, double dd, double& la, double& lb, double& lc,
-                                         double& rhs) {
-  const double x = (double)pq.x, y = (double)pq.y;
-  la = __dadd_rn(__dadd_rn(__dmul_rn(F[0], x), __dmul_rn(F[1], y)), F[2]);
-  lb = __dadd_rn(__dadd_rn(__dmul_rn(F[3], x), __dmul_rn(F[4], y)), F[5]);
-  lc = __dadd_rn(__dadd_rn(__dmul_rn(F[6], x), __dmul_rn(F[7], y)), F[8]);
-  rhs = __dmul_rn(dd, __dadd_rn(__dmul_rn(la, la), __dmul_rn(lb, lb)));
-}
-
-// Eq. 1-2, squared: keep p' iff (a x' + b y' + c)^2 <= d^2 (a^2 + b^2).
-__device__ __forceinline__ bool epi_keep(double la, double lb, double lc, double rhs, float2 pc) {
-  const double num = __dadd_rn(__dadd_rn(__dmul_rn(la, (double)pc.x), __dmul_rn(lb, (double)pc.y)), lc);
-  return __dmul_rn(num, num) <= rhs;
-}
-
-// The band test of one query: the FP64 line and right-hand side exactly as
-// the definition above computes them, and their FP32 roundings.
-struct EpiQ {
-  double la, lb, lc, rhs;
-  float a, b, c, r;
-};
-
-__device__ __forceinline__ EpiQ epi_query(const double* F, float2 pq, double dd) {
-  EpiQ e;
-  epi_line(F, pq, dd, e.la, e.lb, e.lc, e.rhs);
-  e.a = __double2float_rn(e.la);
-  e.b = __double2float_rn(e.lb);
-  e.c = __double2float_rn(e.lc);
-  e.r = __double2float_rn(e.rhs);
-  return e;
-}
-
-// The FP64 decision as a real call: inlined, the compiler may predicate it and
-// run it for every candidate, which makes the FP64 pipe the limit.
-__device__ __noinline__ bool epi_keep_fp64(const EpiQ& e, float2 pc) {
-  return epi_keep(e.la, e.lb, e.lc, e.rhs, pc);
-}
-
-// epi_keep, decided in FP32 when the FP32 difference r - n^2 clears a bound on
-// its distance from the FP64 difference, else by epi_keep itself.  With
-// u = 2^-24: a, b, c carry one rounding each and n two FMA roundings, so
-// |n32 - n64| <= 3.01 u S, S = |a x'| + |b y'| + |c| (the FP64 evaluation's own
-// error, ~3 * 2^-53 S, is inside the slack); then |(r - n^2)32 - (rhs - num^2)64|
-// <= 2u r + 3u n^2 + e_n (2|n| + e_n).  The margins below are 6.7u and 8.4u, plus
-// an absolute 1e-30 for underflow; overflow or NaN fails both comparisons.
-__device__ __forceinline__ bool epi_keep_fast(const EpiQ& e, float2 pc) {
-  const float n = fmaf(e.a, pc.x, fmaf(e.b, pc.y, e.c));
-  const float S = fmaf(fabsf(e.a), fabsf(pc.x), fmaf(fabsf(e.b), fabsf(pc.y), fabsf(e.c)));
-  const float lhs = n * n;
-  const float diff = e.r - lhs;
-  const float en = 4.0e-7f * S;
-  const float err = fmaf(en, fmaf(2.0f, fabsf(n), en), fmaf(5.0e-7f, e.r + lhs, 1.0e-30f));
-  if (diff > err) return true;
-  if (diff < -err) return false;
-  return epi_keep_fp64(e, pc);
-}
-
 __device__ __forceinline__ uint32_t hamming128(uint4 a, uint4 b) {
   return __popc(a.x ^ b.x) + __popc(a.y ^ b.y) + __popc(a.z ^ b.z) + __popc(a.w ^ b.w);
 }

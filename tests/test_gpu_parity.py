@@ -172,10 +172,11 @@ def test_speculative_threshold_never_changes_results(ch, orc, hint, fixed):
 
 @pytest.mark.parametrize("case", ["join", "large_image", "band"])
 def test_batched_kernel_choice(ch, orc, case):
-    """The batched schedule runs the tensor-core bucket join (calibration +
-    join + fallback + scan + compaction = 5 launches) unless the band is on or
-    a query image exceeds the join's shared-memory counters; then the
-    speculative per-query kernel (4 launches).  Both match the oracle."""
+    """The batched schedule runs the tensor-core bucket join by default
+    (calibration + join + fallback + scan + compaction = 5 launches; with the
+    band no calibration, 4) unless a query image exceeds the join's
+    shared-memory counters; then the speculative per-query kernel (4
+    launches).  Both match the oracle."""
     import math
     pk = dict(schedule=1)
     if case == "band":
@@ -201,6 +202,8 @@ def test_batched_kernel_choice(ch, orc, case):
     ch.cashash_match_plan(ctx, plan, moff, mt, cap, F=F)
     assert ch.cashash_sync_status(ctx) == ch.CASHASH_OK
     assert ch.cashash_get_stats(ctx)["n_launches"] - n0 == (5 if case == "join" else 4)
+    kern = ch.cashash_plan_get_tuning(plan)["kernel"]
+    assert kern == (ch.CASHASH_KERNEL_QUERY if case == "large_image" else ch.CASHASH_KERNEL_JOIN)
     po = oparams(orc, pk)
     mu, codes, buckets = oracle_codes(orc, s.desc, s.R, po)
     eoff, emt = orc.match_pairs(s.desc, s.img_off, codes, buckets, pairs, po, F=s.F, kpts=s.kpts)
@@ -255,9 +258,10 @@ def test_every_tuning_and_the_autotuner(ch, orc):
     ctx.close()
 
 
-def test_autotuner_with_the_band(ch, orc):
-    """With the band on the join does not apply: forcing it is refused and the
-    autotuner chooses among the per-query tiles; results stay exact."""
+def test_band_kernels_and_the_autotuner(ch, orc):
+    """With the band every kernel configuration (the join with its band test,
+    the per-query kernel with either tile) gives the oracle's lists; a 2-tile
+    join request is normalised to 4 tiles; the autotuner keeps one."""
     import math
     s = synth.epipolar_set(44, n_views=4, n_points=9000, arc=2 * math.pi * 4 / 250, z_max=0.355)
     pairs = np.concatenate([s.pairs, s.pairs[:, ::-1]])
@@ -268,24 +272,34 @@ def test_autotuner_with_the_band(ch, orc):
     ds = ch.DeviceSet(p, s.img_off, s.desc, s.kpts)
     ch.cashash_build_codes(ctx, ds)
     plan = ch.cashash_plan_create(ctx, ds, pairs)
-    assert ch.cashash_plan_get_tuning(plan)["kernel"] == ch.CASHASH_KERNEL_QUERY
-    with pytest.raises(ch.CashashError):
-        ch.cashash_plan_set_tuning(plan, ch.CASHASH_KERNEL_JOIN, 4, 0)
+    J, Q = ch.CASHASH_KERNEL_JOIN, ch.CASHASH_KERNEL_QUERY
+    t0 = ch.cashash_plan_get_tuning(plan)
+    assert (t0["kernel"], t0["tile"]) == (J, 4)
     F = torch.from_numpy(np.ascontiguousarray(s.F)).cuda()
-    t = ch.cashash_plan_autotune(ctx, plan, F=F, max_pairs=3)
-    assert t["kernel"] == ch.CASHASH_KERNEL_QUERY and t["ms_sample"] > 0
     P = len(pairs)
     cap = int(s.sizes()[pairs[:, 0]].sum())
     moff = torch.zeros(P + 1, dtype=torch.int64, device="cuda")
     mt = torch.zeros((cap, 2), dtype=torch.int32, device="cuda")
-    ch.cashash_match_plan(ctx, plan, moff, mt, cap, F=F)
-    assert ch.cashash_sync_status(ctx) == ch.CASHASH_OK
     po = oparams(orc, pk)
     mu, codes, buckets = oracle_codes(orc, s.desc, s.R, po)
     eoff, emt = orc.match_pairs(s.desc, s.img_off, codes, buckets, pairs, po, F=s.F, kpts=s.kpts)
-    off = moff.cpu().numpy().astype(np.uint64)
-    assert np.array_equal(off, eoff)
-    assert np.array_equal(mt[:int(off[-1])].cpu().numpy().view(np.uint32), emt)
+
+    def check():
+        for _ in range(2):
+            ch.cashash_match_plan(ctx, plan, moff, mt, cap, F=F)
+            assert ch.cashash_sync_status(ctx) == ch.CASHASH_OK
+            off = moff.cpu().numpy().astype(np.uint64)
+            assert np.array_equal(off, eoff)
+            assert np.array_equal(mt[:int(off[-1])].cpu().numpy().view(np.uint32), emt)
+
+    for kern, tile, want in [(J, 2, 4), (J, 4, 4), (Q, 512, 512), (Q, 256, 256)]:
+        ch.cashash_plan_set_tuning(plan, kern, tile, 0)
+        t = ch.cashash_plan_get_tuning(plan)
+        assert (t["kernel"], t["tile"]) == (kern, want)
+        check()
+    t = ch.cashash_plan_autotune(ctx, plan, F=F, max_pairs=0)
+    assert t["kernel"] in (J, Q) and t["ms_sample"] > 0
+    check()
     plan.close()
     ctx.close()
 
