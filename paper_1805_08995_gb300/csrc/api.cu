@@ -567,20 +567,15 @@ int plan_configure(cashash_plan* pl, cashash_tuning t) {
     if (P && !grid) return CASHASH_ENOTSUP;
     join = true;
     // One item per pair.  The resident CTAs take consecutive items, so the
-    // pairs are ordered by tiles of S x S images (S^2 about the number of
-    // resident CTAs): the pairs in flight then share about 2 S images, whose
-    // descriptors and tables stay in L2.  Within a tile the largest
-    // (N_A * N_B) pairs come first.
-    const uint32_t S = std::max<uint32_t>(1, (uint32_t)std::lround(std::sqrt((double)grid)));
-    std::vector<uint64_t> tkey(P);
-    for (uint32_t i = 0; i < P; ++i) {
-      const uint32_t a = pl->pairs_h[2 * (size_t)i], b = pl->pairs_h[2 * (size_t)i + 1];
-      tkey[i] = ((uint64_t)(std::min(a, b) / S) << 32) | (std::max(a, b) / S);
-    }
+    // pairs are grouped by candidate image: the pairs in flight then share
+    // their candidate images, whose descriptors and tables stay in L2 (on an
+    // all-pairs set as fast as tiles of images, on a sparse neighbour graph
+    // clearly faster).  Within a group the largest (N_A * N_B) pairs come first.
     std::vector<uint32_t> order(P);
     for (uint32_t i = 0; i < P; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
-      if (tkey[x] != tkey[y]) return tkey[x] < tkey[y];
+      const uint32_t bx = pl->pairs_h[2 * (size_t)x + 1], by = pl->pairs_h[2 * (size_t)y + 1];
+      if (bx != by) return bx < by;
       return (uint64_t)info[x].nA * info[x].nB > (uint64_t)info[y].nA * info[y].nB;
     });
     for (uint32_t i : order) items.push_back(make_uint2(i, 0u));
