@@ -224,7 +224,9 @@ def run_reference(args):
     if rank != 0:
         return 0
     s, wdesc = workload(args.workload, 0)
-    sp = max(8, args.ref_pairs)
+    # each step times the oracle on a bounded sample; the --ref-pairs budget is
+    # split over all steps so that the whole run stays within a few minutes
+    sp = max(16, args.ref_pairs // max(1, args.steps + args.warmup))
     times = []
     for i in range(args.warmup + args.steps):
         v, cores, text, secs = oracle_sample(s, sp, seed=i)
