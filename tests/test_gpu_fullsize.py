@@ -43,11 +43,12 @@ def _oracle_codes(orc, desc, R, po, mu, threads=16):
     return codes, buckets
 
 
-def _run_gpu(ch, s, precision=0, repeats=2):
-    p = ch.cashash_default_params(precision=precision, schedule=ch.CASHASH_SCHED_PERSISTENT)
+def _run_gpu(ch, s, precision=0, repeats=2, **pk):
+    p = ch.cashash_default_params(precision=precision, schedule=ch.CASHASH_SCHED_PERSISTENT, **pk)
     ctx = ch.cashash_create(p, s.R)
-    ds = ch.DeviceSet(p, s.img_off, s.desc)
+    ds = ch.DeviceSet(p, s.img_off, s.desc, s.kpts if "epi_px" in pk else None)
     plan = ch.cashash_plan_create(ctx, ds, s.pairs)
+    F = torch.from_numpy(np.ascontiguousarray(s.F)).cuda() if "epi_px" in pk else None
     P = len(s.pairs)
     cap = int(s.sizes()[s.pairs[:, 0]].sum())
     moff = torch.zeros(P + 1, dtype=torch.int64, device="cuda")
@@ -55,7 +56,7 @@ def _run_gpu(ch, s, precision=0, repeats=2):
     outs = []
     for _ in range(repeats):  # the second pass replays the captured graph with learned thresholds
         ch.cashash_build_codes(ctx, ds)
-        ch.cashash_match_plan(ctx, plan, moff, mt, cap)
+        ch.cashash_match_plan(ctx, plan, moff, mt, cap, F=F)
         assert ch.cashash_sync_status(ctx) == ch.CASHASH_OK
         off = moff.cpu().numpy().astype(np.uint64)
         outs.append((off, mt[:int(off[-1])].cpu().numpy().view(np.uint32).copy()))
@@ -74,8 +75,8 @@ def _properties(s, off, mt):
             assert np.all(np.diff(seg[:, 0].astype(np.int64)) > 0)   # strictly ascending queries
 
 
-def _sample_check(orc, s, off, mt, codes_of, mu, n_sample, seed):
-    po = orc.params()
+def _sample_check(orc, s, off, mt, codes_of, mu, n_sample, seed, po=None):
+    po = po or orc.params()
     rng = np.random.default_rng(seed)
     pick = np.sort(rng.choice(len(s.pairs), size=min(n_sample, len(s.pairs)), replace=False))
     for i in pick:
@@ -84,7 +85,10 @@ def _sample_check(orc, s, off, mt, codes_of, mu, n_sample, seed):
         B = slice(int(s.img_off[b]), int(s.img_off[b + 1]))
         cA, bA = codes_of(a)
         cB, bB = codes_of(b)
-        m = orc.match_pair(s.desc[A], cA, bA, s.desc[B], cB, bB, po)
+        kw = {}
+        if s.F is not None:
+            kw = dict(F=s.F[i], kptsA=s.kpts[A], kptsB=s.kpts[B])
+        m = orc.match_pair(s.desc[A], cA, bA, s.desc[B], cB, bB, po, **kw)
         q = np.nonzero(m >= 0)[0]
         exp = np.stack([q, m[q]], axis=1).astype(np.uint32) if q.size else np.zeros((0, 2), np.uint32)
         assert np.array_equal(mt[int(off[i]):int(off[i + 1])], exp), "pair %d (%d, %d)" % (i, a, b)
@@ -134,5 +138,33 @@ def test_config3_full_size(ch, orc):
         return cache[i]
 
     _sample_check(orc, s, off2, mt2, codes_of, mu, 24, 6)
+    plan.close()
+    ctx.close()
+
+
+def test_config4_full_size(ch, orc):
+    """Config 4 (Sec. 6.2 band, 4 px): 500 views, 14,613 pairs, the batched
+    join with its band test as bench.py runs it; sampled images' codes and 24
+    sampled pairs entry for entry, every pair's list checked for properties."""
+    s = synth.config4()
+    ctx, ds, plan, outs, stats, mu = _run_gpu(ch, s, precision=1, epi_px=4.0)
+    assert ch.cashash_plan_get_tuning(plan)["kernel"] == ch.CASHASH_KERNEL_JOIN
+    po = orc.params(epi_px=4.0)
+    assert np.array_equal(mu, orc.mean(s.desc))
+    (off1, mt1), (off2, mt2) = outs
+    assert np.array_equal(off1, off2) and np.array_equal(mt1, mt2)
+    _properties(s, off2, mt2)
+    gcodes, gbuckets = ds.codes_np(), ds.buckets_np(6)
+    cache = {}
+
+    def codes_of(i):
+        if i not in cache:
+            a, b = int(s.img_off[i]), int(s.img_off[i + 1])
+            c, bk = orc.hash_codes(s.desc[a:b], mu, s.R, po)
+            assert np.array_equal(gcodes[a:b], c) and np.array_equal(gbuckets[a:b], bk)
+            cache[i] = (c, bk)
+        return cache[i]
+
+    _sample_check(orc, s, off2, mt2, codes_of, mu, 24, 7, po=po)
     plan.close()
     ctx.close()
