@@ -43,7 +43,10 @@ def build(force: bool = False) -> str:
 class Params(C.Structure):
     _fields_ = [("code_bits", C.c_uint32), ("n_tables", C.c_uint32), ("bits_per_table", C.c_uint32),
                 ("top_k", C.c_uint32), ("ratio_num", C.c_uint32), ("ratio_den", C.c_uint32),
-                ("tau", C.c_uint32), ("epi_px", C.c_double)]
+                ("tau", C.c_uint32), ("flags", C.c_uint32), ("epi_px", C.c_double)]
+
+
+MUTUAL, ACCEPT_SINGLE = 1, 2
 
 
 class QueryDetail(C.Structure):
@@ -52,9 +55,11 @@ class QueryDetail(C.Structure):
                 ("d1", C.c_int32), ("d2", C.c_int32)]
 
 
-def params(code_bits=128, n_tables=6, bits_per_table=8, top_k=10, ratio=(4, 5), tau=None, epi_px=-1.0):
+def params(code_bits=128, n_tables=6, bits_per_table=8, top_k=10, ratio=(4, 5), tau=None, epi_px=-1.0, flags=0):
+    """flags: MUTUAL (match_pairs keeps (q, j) only when the reverse match of j
+    is q) | ACCEPT_SINGLE (a query with exactly one ranked candidate matches it)."""
     return Params(code_bits, n_tables, bits_per_table, top_k, ratio[0], ratio[1],
-                  code_bits if tau is None else tau, float(epi_px))
+                  code_bits if tau is None else tau, int(flags), float(epi_px))
 
 
 def _load():

@@ -232,6 +232,8 @@ int64_t oracle_match_pair(const uint8_t* descA, const uint32_t* codesA, const ui
       const int64_t lhs = (int64_t)p->ratio_den * p->ratio_den * dd[0].d;
       const int64_t rhs = (int64_t)p->ratio_num * p->ratio_num * dd[1].d;
       if (lhs < rhs) mj = (int32_t)dd[0].j;
+    } else if (ntop == 1 && (p->flags & ORACLE_ACCEPT_SINGLE)) {
+      mj = (int32_t)dd[0].j;  /* the single-candidate reading, when asked for */
     }
     if (detail) {
       detail[q].match_j = mj;
@@ -285,6 +287,28 @@ static void* worker(void* arg) {
                                   J->desc + ob * ORACLE_DIM, J->codes + ob * 4, J->buckets + ob * T, nB, J->p,
                                   J->F ? J->F + 9 * (size_t)i : NULL, J->kpts ? J->kpts + 2 * oa : NULL,
                                   J->kpts ? J->kpts + 2 * ob : NULL, m, NULL);
+    if (r >= 0 && (J->p->flags & ORACLE_MUTUAL)) {
+      /* the reverse match: queries of B against candidates of A, F transposed */
+      double Ft[9];
+      if (J->F)
+        for (int u = 0; u < 3; ++u)
+          for (int v = 0; v < 3; ++v) Ft[3 * u + v] = J->F[9 * (size_t)i + 3 * v + u];
+      int32_t* mr = (int32_t*)malloc(sizeof(int32_t) * ((size_t)nB + 1));
+      const int64_t rr = oracle_match_pair(J->desc + ob * ORACLE_DIM, J->codes + ob * 4, J->buckets + ob * T, nB,
+                                           J->desc + oa * ORACLE_DIM, J->codes + oa * 4, J->buckets + oa * T, nA,
+                                           J->p, J->F ? Ft : NULL, J->kpts ? J->kpts + 2 * ob : NULL,
+                                           J->kpts ? J->kpts + 2 * oa : NULL, mr, NULL);
+      if (rr < 0) {
+        r = -1;
+      } else {
+        r = 0;
+        for (uint32_t q = 0; q < nA; ++q) {
+          if (m[q] >= 0 && mr[m[q]] != (int32_t)q) m[q] = -1;
+          if (m[q] >= 0) r++;
+        }
+      }
+      free(mr);
+    }
     if (r < 0) {
       pthread_mutex_lock(&J->mu);
       J->err = -1;

@@ -23,7 +23,10 @@
  * code-building call; the projection is evaluated in IEEE double precision
  * in a fixed order with no fused multiply-add; sign at exactly zero is bit 0;
  * ties in the ranking are broken by the smaller candidate index; the ratio
- * test is strict on distances; a query needs two ranked candidates to match.
+ * test is strict on distances; a query needs two ranked candidates to match
+ * (unless ORACLE_ACCEPT_SINGLE); the mutual check (ORACLE_MUTUAL) keeps (q, j)
+ * of pair (A, B) only when matching j of B against A, by the same procedure
+ * with F transposed, gives q.
  *
  * Parity pins (tests/test_oracle_*.py): exact rational arithmetic for the
  * mean and the projection sign, axis-aligned projections (closed form),
@@ -44,6 +47,10 @@ extern "C" {
 #define ORACLE_MAX_TABLES 8
 #define ORACLE_MAX_K 64
 
+/* oracle_params.flags */
+#define ORACLE_MUTUAL 1u         /* keep (q, j) only when the reverse match of j is q (oracle_match_pairs) */
+#define ORACLE_ACCEPT_SINGLE 2u  /* a query with exactly one ranked candidate matches it */
+
 typedef struct {
   uint32_t code_bits;       /* n of Step 2: length of the remapping code, 1..128 */
   uint32_t n_tables;        /* number of lookup tables of Step 1, 1..8 */
@@ -52,6 +59,7 @@ typedef struct {
   uint32_t ratio_num;       /* Lowe ratio as a fraction num/den (0.8 = 4/5) */
   uint32_t ratio_den;
   uint32_t tau;             /* Sec. 5 threshold; >= code_bits means off */
+  uint32_t flags;           /* ORACLE_MUTUAL | ORACLE_ACCEPT_SINGLE */
   double epi_px;            /* Sec. 6.2 threshold d in pixels; < 0 means off */
 } oracle_params;
 
@@ -91,6 +99,9 @@ int64_t oracle_match_pair(const uint8_t* descA, const uint32_t* codesA, const ui
 
 /* Many pairs over an image set stored back to back (img_off[i]..img_off[i+1]),
  * split across n_threads POSIX threads (pairs are independent, Sec. 1).
+ * With ORACLE_MUTUAL each pair (A, B) is also matched as (B, A) with F
+ * transposed (x_A^T F^T x_B = 0), and (q, j) is kept only if the reverse
+ * match of j is q.
  * Output: match_off[P+1] (prefix of per-pair counts) and matches[...][2] =
  * (query index in A, index in B) ascending in the query index; matches may be
  * NULL to only count.  F is [P][9] or NULL; kpts is [n_total][2] or NULL.

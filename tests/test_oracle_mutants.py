@@ -36,6 +36,11 @@ MUTANTS = {
                      "const double a = (F[0] * x + F[3] * y) + F[6];\n  const double b = (F[1] * x + F[4] * y) + F[7];\n  const double c = (F[2] * x + F[5] * y) + F[8];"),
     "distance order": ("if (a->d != b->d) return a->d < b->d ? -1 : 1;", "if (a->d != b->d) return a->d > b->d ? -1 : 1;"),
     "tau inclusive": ("if (cand[e].h <= p->tau)", "if (cand[e].h < p->tau)"),
+    "mutual reverse F not transposed": ("Ft[3 * u + v] = J->F[9 * (size_t)i + 3 * v + u];",
+                                        "Ft[3 * u + v] = J->F[9 * (size_t)i + 3 * u + v];"),
+    "mutual check dropped": ("if (m[q] >= 0 && mr[m[q]] != (int32_t)q) m[q] = -1;", ""),
+    "single accepted without the flag": ("} else if (ntop == 1 && (p->flags & ORACLE_ACCEPT_SINGLE)) {",
+                                         "} else if (ntop == 1) {"),
 }
 
 

@@ -438,3 +438,82 @@ def test_planted_copies_are_recovered(orc):
     good = sum(1 for q, r in truth.items() if m[q] == r)
     assert good / len(truth) > 0.95
     assert good / max(1, int((m >= 0).sum())) > 0.99
+
+
+# --------------------------------------------------------------------------
+# flags of the next scope row: single-candidate acceptance, mutual check
+# --------------------------------------------------------------------------
+
+def test_single_candidate_acceptance_against_bucket_counts(orc):
+    """ACCEPT_SINGLE changes exactly the queries with one candidate: each then
+    matches that candidate (counted by brute-force bucket equality); queries
+    with two or more candidates are unchanged, with none stay unmatched."""
+    p0 = orc.params(n_tables=1, bits_per_table=8, top_k=10)
+    p1 = orc.params(n_tables=1, bits_per_table=8, top_k=10, flags=orc.ACCEPT_SINGLE)
+    dA, cA, bA, dB, cB, bB = _pair(orc, 91, 300, 260, p0)
+    m0 = orc.match_pair(dA, cA, bA, dB, cB, bB, p0)
+    m1 = orc.match_pair(dA, cA, bA, dB, cB, bB, p1)
+    same = bA[:, 0][:, None] == bB[:, 0][None, :]
+    ncand = same.sum(axis=1)
+    one = ncand == 1
+    assert one.sum() > 20 and (ncand >= 2).sum() > 20
+    assert np.array_equal(m1[one], np.argmax(same[one], axis=1))
+    assert np.all(m0[one] == -1)
+    assert np.array_equal(m1[~one], m0[~one])
+
+
+@pytest.mark.parametrize("seed", [40, 41])
+def test_mutual_check_is_brute_force_cross_check(orc, seed):
+    """With one bucket (m = 0) and k >= both image sizes, matching is exact
+    nearest neighbour + ratio test in each direction; MUTUAL keeps (q, j)
+    exactly when the forward match of q is j and the backward match of j is
+    q, both computed here from the integer distance matrix."""
+    nA, nB = 45, 55
+    p = orc.params(n_tables=1, bits_per_table=0, top_k=64, flags=orc.MUTUAL)
+    s = synth.random_set(seed, [nA, nB])
+    s.desc[nA:nA + 30] = synth.noisy_copy(np.random.default_rng(seed), s.desc[:30], 4.0)  # some true pairs
+    codes, buckets = _hash(orc, s.desc, s.R[:p.code_bits + p.n_tables * p.bits_per_table], p)
+    off, mt = orc.match_pairs(s.desc, s.img_off, codes, buckets, np.array([[0, 1]], np.uint32), p)
+
+    def nn_ratio(X, Y):
+        D = ((X[:, None, :].astype(np.int64) - Y[None, :, :].astype(np.int64)) ** 2).sum(axis=2)
+        out = np.full(X.shape[0], -1)
+        for q in range(X.shape[0]):
+            order = np.lexsort((np.arange(Y.shape[0]), D[q]))
+            if 25 * D[q, order[0]] < 16 * D[q, order[1]]:
+                out[q] = order[0]
+        return out
+
+    A, B = s.desc[:nA], s.desc[nA:]
+    fw, bw = nn_ratio(A, B), nn_ratio(B, A)
+    exp = [(q, fw[q]) for q in range(nA) if fw[q] >= 0 and bw[fw[q]] == q]
+    assert [tuple(r) for r in mt.tolist()] == exp
+    assert len(exp) >= 10 and len(exp) < (fw >= 0).sum() + 1
+
+
+def test_mutual_check_with_the_band_is_symmetric(orc):
+    """Mutual lists of (A, B) under F are the transposed lists of (B, A) under
+    F^T: the reverse match must use the transposed fundamental matrix (and the
+    swapped key-points), or the two disagree."""
+    rng = np.random.default_rng(95)
+    x1, x2, F = _two_views(rng)
+    n = x1.shape[0]
+    base = synth.sift_like(rng, n)
+    desc = np.concatenate([synth.noisy_copy(rng, base, 6.0), synth.noisy_copy(rng, base, 6.0)])
+    kp = np.concatenate([x1, x2]).astype(np.float32) + rng.normal(0, 1, size=(2 * n, 2)).astype(np.float32)
+    img_off = np.array([0, n, 2 * n], np.uint64)
+    R = synth.projection_matrix(95)
+    p = orc.params(n_tables=6, bits_per_table=5, top_k=10, epi_px=4.0, flags=orc.MUTUAL)
+    codes, buckets = _hash(orc, desc, R[:p.code_bits + p.n_tables * p.bits_per_table], p)
+    Fs = np.stack([F.ravel(), F.T.ravel()])
+    off, mt = orc.match_pairs(desc, img_off, codes, buckets, np.array([[0, 1], [1, 0]], np.uint32), p,
+                              F=Fs, kpts=kp)
+    fw = mt[int(off[0]):int(off[1])]
+    bw = mt[int(off[1]):int(off[2])]
+    assert len(fw) > 50
+    assert sorted(map(tuple, fw.tolist())) == sorted((int(j), int(q)) for q, j in bw.tolist())
+    # a plain forward run keeps at least these, mostly more
+    p_plain = orc.params(n_tables=6, bits_per_table=5, top_k=10, epi_px=4.0)
+    off2, mt2 = orc.match_pairs(desc, img_off, codes, buckets, np.array([[0, 1]], np.uint32), p_plain,
+                                F=Fs[:1], kpts=kp)
+    assert set(map(tuple, fw.tolist())) <= set(map(tuple, mt2.tolist()))
