@@ -86,9 +86,18 @@ typedef struct {
   uint32_t precision;       /* CASHASH_FP32 (CUDA-core projection) or CASHASH_BF16 (tensor cores) */
   uint32_t schedule;        /* CASHASH_SCHED_PER_PAIR (one launch per pair) or
                                CASHASH_SCHED_PERSISTENT (one launch over the whole pair list) */
-  uint32_t reserved;
+  uint32_t flags;           /* CASHASH_FLAG_* below, ORed [0] */
   double epi_px;            /* Sec. 6.2 threshold d in pixels; < 0 turns the band off [-1] */
 } cashash_params;
+
+/* cashash_params.flags (readings beyond the paper, off by default):
+ * CASHASH_FLAG_MUTUAL: a match (q, j) of pair (A, B) is kept only when matching
+ *   j of B against A by the same procedure (Steps 1-4, tau, the band with F
+ *   transposed) gives q; every pair is matched in both directions.
+ * CASHASH_FLAG_ACCEPT_SINGLE: a query with exactly one ranked candidate
+ *   matches it (by default the ratio test needs a second neighbour). */
+#define CASHASH_FLAG_MUTUAL 1u
+#define CASHASH_FLAG_ACCEPT_SINGLE 2u
 
 /* Fills p with the defaults listed above. */
 void cashash_default_params(cashash_params* p);
@@ -274,7 +283,9 @@ int cashash_run_host(cashash_ctx* ctx, const uint8_t* desc_host, const uint64_t*
  * overlap on the GPU (other streams, other host threads) race and must be
  * serialised by the caller.
  * Errors: EINVAL (bad parameters or set, image index out of range, or
- * image_a larger than CASHASH_NOALLOC_MAX_QUERIES features), ECUDA. */
+ * image_a larger than CASHASH_NOALLOC_MAX_QUERIES features), ENOTSUP
+ * (CASHASH_FLAG_MUTUAL: the reverse match would need a second scratch),
+ * ECUDA. */
 int cashash_match_pair_noalloc(const cashash_params* p, const cashash_set* set, uint32_t image_a,
                                uint32_t image_b, const double* F_dev, uint64_t* match_off, uint32_t* matches,
                                uint64_t cap, cashash_stream_t stream);

@@ -24,6 +24,7 @@ CASHASH_FP32, CASHASH_BF16 = 0, 1
 CASHASH_SCHED_PER_PAIR, CASHASH_SCHED_PERSISTENT = 0, 1
 CASHASH_NOALLOC_MAX_QUERIES = 65536
 CASHASH_KERNEL_JOIN, CASHASH_KERNEL_QUERY = 1, 2
+CASHASH_FLAG_MUTUAL, CASHASH_FLAG_ACCEPT_SINGLE = 1, 2
 
 
 class CashashError(RuntimeError):
@@ -36,7 +37,7 @@ class cashash_params(C.Structure):
     _fields_ = [("code_bits", C.c_uint32), ("n_tables", C.c_uint32), ("bits_per_table", C.c_uint32),
                 ("top_k", C.c_uint32), ("ratio_num", C.c_uint32), ("ratio_den", C.c_uint32),
                 ("tau", C.c_uint32), ("precision", C.c_uint32), ("schedule", C.c_uint32),
-                ("reserved", C.c_uint32), ("epi_px", C.c_double)]
+                ("flags", C.c_uint32), ("epi_px", C.c_double)]
 
 
 class cashash_set(C.Structure):

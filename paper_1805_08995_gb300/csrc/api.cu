@@ -77,7 +77,10 @@ struct cashash_ctx {
 
 struct cashash_plan {
   cashash_ctx* ctx = nullptr;
-  uint32_t P = 0;
+  uint32_t P = 0;                      // pairs matched (with the mutual check: the user's pairs, then their reversals)
+  uint32_t P_out = 0;                  // pairs reported (the user's)
+  double* d_F2 = nullptr;              // mutual check with the band: F of every matched pair (F, then F^T)
+  uint64_t cap_F2 = 0;
   int persistent = 0;
   PairInfo* d_pairs = nullptr;
   uint2* d_items = nullptr;
@@ -144,6 +147,7 @@ int params_ok(const cashash_params* p) {
   if (p->top_k < 1 || p->top_k > CASHASH_MAX_K) return 0;
   if (p->ratio_den < 1 || p->ratio_den > 65535 || p->ratio_num > 65535) return 0;
   if (p->precision > CASHASH_BF16 || p->schedule > CASHASH_SCHED_PERSISTENT) return 0;
+  if (p->flags & ~(CASHASH_FLAG_MUTUAL | CASHASH_FLAG_ACCEPT_SINGLE)) return 0;
   if (std::isnan(p->epi_px) || std::isinf(p->epi_px)) return 0;
   return 1;
 }
@@ -362,6 +366,7 @@ int cashash_create(cashash_ctx** out, const cashash_params* p, const double* R_h
   c->kp.tau = std::min(p->tau, p->code_bits);
   c->kp.rows = rows;
   c->kp.epi_px = p->epi_px;
+  c->kp.flags = p->flags;
   int st = cuda_err(cudaGetDevice(&c->device));
   if (st == CASHASH_OK) st = cuda_err(cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device));
   // host-side constants: FP32 transposed copy of R and row norms (rounded up)
@@ -531,6 +536,7 @@ void cashash_plan_destroy(cashash_plan* pl) {
   dfree(pl->d_tau);
   dfree(pl->d_jhist);
   dfree(pl->d_jline);
+  dfree(pl->d_F2);
   if (pl->gexec) cudaGraphExecDestroy(pl->gexec);
   if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
   delete pl;
@@ -633,8 +639,25 @@ int cashash_plan_create(cashash_ctx* c, const cashash_set* s, const uint32_t* pa
   CK(cudaSetDevice(c->device));
   cashash_plan* pl = new (std::nothrow) cashash_plan();
   if (!pl) return CASHASH_ENOMEM;
+  // mutual check: pairs P..2P-1 are the reversals of the user's pairs
+  const uint32_t P_out = P;
+  std::vector<uint32_t> pairs_int;
+  if (c->p.flags & CASHASH_FLAG_MUTUAL) {
+    if ((uint64_t)P * 2 > 0xFFFFFFFFull) {
+      delete pl;
+      return CASHASH_EINVAL;
+    }
+    pairs_int.assign(pairs_host, pairs_host + 2 * (size_t)P);
+    for (uint32_t i = 0; i < P; ++i) {
+      pairs_int.push_back(pairs_host[2 * (size_t)i + 1]);
+      pairs_int.push_back(pairs_host[2 * (size_t)i]);
+    }
+    P = 2 * P;
+    pairs_host = pairs_int.data();
+  }
   pl->ctx = c;
   pl->P = P;
+  pl->P_out = P_out;
   pl->persistent = c->p.schedule == CASHASH_SCHED_PERSISTENT;
   pl->desc = s->desc;
   pl->codes = s->codes;
@@ -678,6 +701,8 @@ int cashash_plan_create(cashash_ctx* c, const cashash_set* s, const uint32_t* pa
   int st = grow(pl->d_pairs, cap, std::max<uint64_t>(P, 1));
   cap = 0;
   if (st == CASHASH_OK) st = grow(pl->d_res, cap, std::max<uint64_t>(qbase, 1));
+  if (st == CASHASH_OK && P != P_out && c->p.epi_px >= 0.0)
+    st = grow(pl->d_F2, pl->cap_F2, std::max<uint64_t>(9ull * P, 1));
   cap = 0;
   if (st == CASHASH_OK) st = grow(pl->d_pair_cnt, cap, std::max<uint64_t>(P, 1));
   cap = 0;
@@ -718,7 +743,12 @@ namespace {
 int enqueue_match(cashash_ctx* c, cashash_plan* pl, const double* F_dev, uint64_t* match_off, uint32_t* matches,
                   uint64_t cap, cudaStream_t stream, bool capturing) {
   const uint32_t P = pl->P;
+  const bool mutual = pl->P_out != pl->P;
   if (P) CK(cudaMemsetAsync(pl->d_pair_cnt, 0, sizeof(unsigned long long) * P, stream));
+  if (mutual && c->p.epi_px >= 0.0 && F_dev) {  // F of the reverse pairs: transposed
+    CK(launch_mutual_F(F_dev, pl->P_out, pl->d_F2, stream));
+    F_dev = pl->d_F2;
+  }
   MatchArgs a{};
   a.desc = pl->desc;
   a.codes = pl->codes;
@@ -772,14 +802,16 @@ int enqueue_match(cashash_ctx* c, cashash_plan* pl, const double* F_dev, uint64_
   }
   {
     StageTimer tm(c, CASHASH_STAGE_COMPACT, stream, capturing);
-    CK(launch_scan_counts(pl->d_pair_cnt, P, match_off, cap, c->d_status, c->d_cnt + 2, stream));
-    CK(launch_compact(pl->d_pairs, P, pl->d_res, match_off, matches, cap, stream));
+    if (mutual) CK(launch_mutual(pl->d_pairs, pl->P_out, pl->d_res, pl->d_pair_cnt, stream));
+    CK(launch_scan_counts(pl->d_pair_cnt, pl->P_out, match_off, cap, c->d_status, c->d_cnt + 2, stream));
+    CK(launch_compact(pl->d_pairs, pl->P_out, pl->d_res, match_off, matches, cap, stream));
   }
   return CASHASH_OK;
 }
 
 uint64_t match_launches(const cashash_plan* pl) {
   uint64_t n = pl->P ? 2 : 1;  // scan + compaction
+  if (pl->P_out != pl->P) n += 1 + (pl->ctx->p.epi_px >= 0.0 ? 1 : 0);  // mutual filter (+ transposed F)
   if (pl->persistent) {
     // calibration (not with the band) + join, or the speculative kernel; then the fallback
     const bool cal = pl->join && pl->ctx->p.epi_px < 0.0 && pl->P;
@@ -878,7 +910,7 @@ int cashash_plan_autotune(cashash_ctx* c, cashash_plan* pl, const double* F_dev,
   if (!pl->persistent || pl->P == 0) return CASHASH_OK;
   CK(cudaSetDevice(c->device));
   CK(cudaStreamSynchronize(stream));
-  const uint32_t P = pl->P;
+  const uint32_t P = pl->P_out;  // the user's pairs (a mutual plan matches them twice internally)
   // max_pairs == 0 (or >= P): the candidates run on the plan itself.  Else on a
   // sample spread over the plan's cost order, with enough pairs per SM that the
   // persistent kernels' tails weigh as in the full run (a join item is a pair).
@@ -968,9 +1000,9 @@ int cashash_plan_autotune(cashash_ctx* c, cashash_plan* pl, const double* F_dev,
       }
       if (t0.kernel == CASHASH_KERNEL_QUERY && sp->tune.tile != t0.tile) continue;  // normalised to another one
       // fresh thresholds: two untimed runs calibrate them, three timed runs follow
-      st = cuda_err(cudaMemsetAsync(sp->d_tau, 0, sizeof(uint32_t) * S, stream));
+      st = cuda_err(cudaMemsetAsync(sp->d_tau, 0, sizeof(uint32_t) * sp->P, stream));
       if (st == CASHASH_OK && sp->d_jhist)
-        st = cuda_err(cudaMemsetAsync(sp->d_jhist, 0, sizeof(uint32_t) * (size_t)S * HBINS, stream));
+        st = cuda_err(cudaMemsetAsync(sp->d_jhist, 0, sizeof(uint32_t) * (size_t)sp->P * HBINS, stream));
       float ms = 0.f;
       for (int r = 0; r < 5 && st == CASHASH_OK; ++r) {
         if (r == 2) st = cuda_err(cudaEventRecord(e0, stream));
@@ -1009,8 +1041,9 @@ int cashash_plan_autotune(cashash_ctx* c, cashash_plan* pl, const double* F_dev,
   st = plan_configure(pl, best);
   if (st == CASHASH_OK) pl->tune.ms_sample = best_ms;
   if (st == CASHASH_OK && whole) {  // thresholds are learned afresh by the chosen kernel
-    st = cuda_err(cudaMemset(pl->d_tau, 0, sizeof(uint32_t) * P));
-    if (st == CASHASH_OK && pl->d_jhist) st = cuda_err(cudaMemset(pl->d_jhist, 0, sizeof(uint32_t) * (size_t)P * HBINS));
+    st = cuda_err(cudaMemset(pl->d_tau, 0, sizeof(uint32_t) * pl->P));
+    if (st == CASHASH_OK && pl->d_jhist)
+      st = cuda_err(cudaMemset(pl->d_jhist, 0, sizeof(uint32_t) * (size_t)pl->P * HBINS));
   }
   return st;
 }

@@ -33,6 +33,7 @@ struct KParams {
   uint32_t code_bits, n_tables, bits_per_table, top_k;
   uint32_t ratio_num, ratio_den, tau, rows;
   double epi_px;
+  uint32_t flags, pad;
 };
 
 // One image pair of a plan.
@@ -105,6 +106,14 @@ __device__ __forceinline__ void write_feature(uint64_t f, const uint32_t* bits, 
     const unsigned long long slot = atomicAdd(nflag_feat, 1ull);
     flaglist[slot] = (uint32_t)f;  // features are < 2^32 per set (checked on the host)
   }
+}
+
+// Step 4 ratio test over nv ranked candidates with the two smallest squared
+// distances d1 <= d2: den^2 d1 < num^2 d2 in 64-bit integers (strict, on
+// distances); one ranked candidate matches only with CASHASH_FLAG_ACCEPT_SINGLE.
+__device__ __forceinline__ bool ratio_ok(const KParams& kp, uint32_t nv, uint32_t d1, uint32_t d2) {
+  if (nv == 1) return (kp.flags & CASHASH_FLAG_ACCEPT_SINGLE) != 0;
+  return nv >= 2 && (uint64_t)kp.ratio_den * kp.ratio_den * d1 < (uint64_t)kp.ratio_num * kp.ratio_num * d2;
 }
 
 // ---------------------------------------------------------------------------
@@ -253,6 +262,11 @@ uint32_t match_grid(uint32_t top_k, int spec, bool epi, uint32_t n_tables, uint3
 int match_tile_size(uint32_t top_k, int spec, uint32_t tile = 0);
 // Exact re-matching of the queries the speculative kernel left PENDING.
 cudaError_t launch_match_fallback(const MatchArgs& a, cudaStream_t s);
+// Mutual check: F2 = (F, F^T) for the P pairs and their reversals; then the
+// filter of the P forward pairs against the reverse results (pairs P..2P-1).
+cudaError_t launch_mutual_F(const double* F, uint32_t P, double* F2, cudaStream_t s);
+cudaError_t launch_mutual(const PairInfo* pairs, uint32_t P, uint32_t* res, unsigned long long* pair_cnt,
+                          cudaStream_t s);
 cudaError_t launch_scan_counts(const unsigned long long* pair_cnt, uint32_t P, uint64_t* match_off,
                                uint64_t cap, uint32_t* status, unsigned long long* total, cudaStream_t s);
 cudaError_t launch_compact(const PairInfo* pairs, uint32_t P, const uint32_t* res, const uint64_t* match_off,

@@ -469,7 +469,7 @@ __global__ void __launch_bounds__(JT, 2) k_join(MatchArgs a) {
             d2 = d;
           }
         }
-        matched = nv >= 2 && (uint64_t)kp.ratio_den * kp.ratio_den * d1 < (uint64_t)kp.ratio_num * kp.ratio_num * d2;
+        matched = ratio_ok(kp, nv, d1, d2);
         a.res[P.qbase + q] = pending ? PENDING : (matched ? j1 : NO_MATCH);
       }
       const uint32_t bal = __ballot_sync(0xFFFFFFFFu, matched);

@@ -258,7 +258,7 @@ __global__ void __launch_bounds__(TPB, (TPB <= 512 ? 2 : 1)) k_match(MatchArgs a
         }
       }
       // Lowe's ratio test on distances, strict: sqrt(d1) < (num/den) sqrt(d2)
-      matched = nv >= 2 && (uint64_t)kp.ratio_den * kp.ratio_den * d1 < (uint64_t)kp.ratio_num * kp.ratio_num * d2;
+      matched = ratio_ok(kp, nv, d1, d2);
       a.res[P.qbase + q] = pending ? PENDING : (matched ? j1 : NO_MATCH);
     }
     const uint32_t bal = __ballot_sync(0xFFFFFFFFu, matched);
@@ -389,8 +389,7 @@ __global__ void __launch_bounds__(128) k_match_fallback(MatchArgs a) {
         for (int o = 16; o > 0; o >>= 1) second = min(second, __shfl_xor_sync(0xFFFFFFFFu, second, o));
         if (lane == 0) {
           const uint32_t d1 = (uint32_t)(best >> 32), j1 = (uint32_t)best, d2 = (uint32_t)(second >> 32);
-          const bool matched =
-              nv >= 2 && (uint64_t)kp.ratio_den * kp.ratio_den * d1 < (uint64_t)kp.ratio_num * kp.ratio_num * d2;
+          const bool matched = ratio_ok(kp, nv, d1, d2);
           a.res[g] = matched ? j1 : NO_MATCH;
           if (matched) atomicAdd(a.pair_cnt + lo, 1ull);
         }

@@ -69,6 +69,8 @@ extern "C" int cashash_match_pair_noalloc(const cashash_params* p, const cashash
       p->ratio_num > 65535)
     return CASHASH_EINVAL;
   if (!(p->epi_px == p->epi_px) || p->epi_px > 1e300) return CASHASH_EINVAL;
+  if (p->flags & ~(CASHASH_FLAG_MUTUAL | CASHASH_FLAG_ACCEPT_SINGLE)) return CASHASH_EINVAL;
+  if (p->flags & CASHASH_FLAG_MUTUAL) return CASHASH_ENOTSUP;  // would need scratch for the reverse pair
   if (!s->img_off || image_a >= s->n_images || image_b >= s->n_images) return CASHASH_EINVAL;
   if (s->img_off[0] != 0 || s->img_off[s->n_images] != s->n_features) return CASHASH_EINVAL;
   const bool epi = p->epi_px >= 0.0;
@@ -112,6 +114,7 @@ extern "C" int cashash_match_pair_noalloc(const cashash_params* p, const cashash
   kp.tau = p->tau < p->code_bits ? p->tau : p->code_bits;
   kp.rows = p->code_bits + p->n_tables * p->bits_per_table;
   kp.epi_px = p->epi_px;
+  kp.flags = p->flags;
 
   PairInfo pi{};
   pi.a0 = s->img_off[image_a];

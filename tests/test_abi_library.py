@@ -99,6 +99,25 @@ def test_tuning_calls_reject_null_arguments(lib):
     assert C.sizeof(ch.cashash_tuning) == 24
 
 
+def test_flags_are_checked_before_touching_a_device(lib):
+    """Unknown flag bits are EINVAL for every entry point; the allocation-free
+    single-pair call has no scratch for a reverse pair, so MUTUAL is ENOTSUP."""
+    import ctypes as C
+    import paper_1805_08995_gb300 as ch
+    R = np.zeros((256, 128))
+    with pytest.raises(ch.CashashError) as e:
+        ch.cashash_create(ch.cashash_default_params(flags=4), R)
+    assert e.value.status == ch.CASHASH_EINVAL
+    L = ch._load()
+    st = ch.cashash_set()
+    off = np.zeros(2, np.uint64)
+    for flags, want in ((ch.CASHASH_FLAG_MUTUAL, ch.CASHASH_ENOTSUP), (8, ch.CASHASH_EINVAL)):
+        p = ch.cashash_default_params(flags=flags)
+        r = L.cashash_match_pair_noalloc(C.byref(p), C.byref(st), 0, 0, None, off.ctypes.data_as(C.c_void_p),
+                                         None, 0, None)
+        assert r == want
+
+
 def test_package_fails_loudly_without_library(tmp_path):
     """The product path has no CPU fallback: without libcashash.so it raises."""
     import sys

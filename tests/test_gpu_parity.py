@@ -74,7 +74,7 @@ def oparams(orc, pk):
     return orc.params(code_bits=pk.get("code_bits", 128), n_tables=pk.get("n_tables", 6),
                       bits_per_table=pk.get("bits_per_table", 8), top_k=pk.get("top_k", 10),
                       ratio=(pk.get("ratio_num", 4), pk.get("ratio_den", 5)), tau=pk.get("tau", None),
-                      epi_px=pk.get("epi_px", -1.0))
+                      epi_px=pk.get("epi_px", -1.0), flags=pk.get("flags", 0))
 
 
 def check_case(ch, orc, s, pairs, **pk):
@@ -128,6 +128,7 @@ def test_bf16_projection_row_counts(ch, orc, pk):
     dict(n_tables=8, bits_per_table=8), dict(n_tables=1, bits_per_table=5),
     dict(code_bits=64), dict(code_bits=32, n_tables=2), dict(code_bits=96, n_tables=4, bits_per_table=6),
     dict(tau=40), dict(tau=0), dict(ratio_num=9, ratio_den=10),
+    dict(flags=1), dict(flags=2), dict(flags=3), dict(flags=3, tau=50, top_k=4),
 ])
 @pytest.mark.parametrize("sched", [0, 1])
 def test_parameter_variants(ch, orc, pk, sched):
@@ -394,8 +395,9 @@ def test_identical_and_degenerate_descriptors(ch, orc):
         assert stats["n_reevaluated"] == 50 * 176
 
 
+@pytest.mark.parametrize("flags", [0, 1, 3])
 @pytest.mark.parametrize("sched", [0, 1])
-def test_epipolar_band(ch, orc, sched):
+def test_epipolar_band(ch, orc, sched, flags):
     """Sec. 6.2: candidates outside the 4 px band around the query's
     epipolar line are removed before ranking (small config-4 style set)."""
     import math
@@ -403,7 +405,7 @@ def test_epipolar_band(ch, orc, sched):
     assert len(s.pairs) >= 10 and s.kpts is not None
     both = np.concatenate([s.pairs, s.pairs[:, ::-1]])
     s.F = np.concatenate([s.F, s.F.reshape(-1, 3, 3).transpose(0, 2, 1).reshape(-1, 9)])
-    check_case(ch, orc, s, both, schedule=sched, epi_px=4.0)
+    check_case(ch, orc, s, both, schedule=sched, epi_px=4.0, flags=flags)
 
 
 @pytest.mark.parametrize("sched", [0, 1])
