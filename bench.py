@@ -176,7 +176,7 @@ def oracle_codes_parallel(orc, desc, R, po, mu, threads):
     return codes, buckets
 
 
-def oracle_sample(s, n_pairs: int, seed: int = 0):
+def oracle_sample(s, n_pairs: int, seed: int = 0, flags: int = 0):
     """Times the oracle on a bounded sample: the centre over the whole set,
     codes for the features of the images the sampled pairs touch, and the
     matching of n_pairs random pairs, all host cores.  Extrapolates to the
@@ -185,7 +185,7 @@ def oracle_sample(s, n_pairs: int, seed: int = 0):
     import oracle as orc
     cores = os.cpu_count() or 1
     band = s.F is not None
-    po = orc.params(epi_px=4.0) if band else orc.params()
+    po = orc.params(epi_px=4.0, flags=flags) if band else orc.params(flags=flags)
     rng = np.random.default_rng(seed)
     P = len(s.pairs)
     pick = np.sort(rng.choice(P, size=min(n_pairs, P), replace=False))
@@ -219,6 +219,11 @@ def oracle_sample(s, n_pairs: int, seed: int = 0):
     return P / job, cores, text, t_mean + t_hash + t_match
 
 
+def run_flags(args) -> int:
+    """The flags word of a run (1 = mutual check, 2 = single candidates accepted), same bits in the library."""
+    return (1 if args.mutual else 0) | (2 if args.accept_single else 0)
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -229,7 +234,7 @@ def run_reference(args):
     sp = max(16, args.ref_pairs // max(1, args.steps + args.warmup))
     times = []
     for i in range(args.warmup + args.steps):
-        v, cores, text, secs = oracle_sample(s, sp, seed=i)
+        v, cores, text, secs = oracle_sample(s, sp, seed=i, flags=run_flags(args))
         if i >= args.warmup:
             times.append(len(s.pairs) / v)
     job = statistics.mean(times)
@@ -277,7 +282,9 @@ def run_ours(args):
     prec = ch.CASHASH_BF16 if args.precision == "bf16" else ch.CASHASH_FP32
     sched = ch.CASHASH_SCHED_PERSISTENT if args.schedule == "persistent" else ch.CASHASH_SCHED_PER_PAIR
     band = s.F is not None
-    p = ch.cashash_default_params(precision=prec, schedule=sched, **(dict(epi_px=4.0) if band else {}))
+    flags = run_flags(args)
+    p = ch.cashash_default_params(precision=prec, schedule=sched, flags=flags,
+                                  **(dict(epi_px=4.0) if band else {}))
     ctx = ch.cashash_create(p, s.R)
     ds = ch.DeviceSet(p, s.img_off, s.desc, s.kpts if band else None)
     plan = ch.cashash_plan_create(ctx, ds, s.pairs)
@@ -416,7 +423,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, cores, text, secs = oracle_sample(s, args.ref_pairs)
+        v, cores, text, secs = oracle_sample(s, args.ref_pairs, flags=run_flags(args))
         cpu = {"value": v, "unit": "pairs/s", "cores": cores, "kind": "oracle", "sample": text,
                "seconds": secs}
 
@@ -430,7 +437,9 @@ def run_ours(args):
                 "config": {"workload": wdesc, "images": int(s.n_images), "features": int(s.desc.shape[0]),
                            "pairs": P, "precision": args.precision, "schedule": args.schedule,
                            "l2": "flushed: 256 MiB write between timed steps (outside the events)",
-                           "params": "n=128, 6 tables x 8 bits, k=10, ratio 0.8" + (", band 4 px" if band else ""),
+                           "params": "n=128, 6 tables x 8 bits, k=10, ratio 0.8" + (", band 4 px" if band else "") +
+                                     (", mutual check" if args.mutual else "") +
+                                     (", single candidates accepted" if args.accept_single else ""),
                            "kernel_tuning": {"kernel": {1: "join", 2: "query"}.get(tuning["kernel"], "per_pair"),
                                              "tile": tuning["tile"], "ctas_per_sm": tuning["ctas_per_sm"],
                                              "autotuned": tuning["ms_sample"] > 0},
@@ -460,6 +469,8 @@ def main():
     ap.add_argument("--thresholds", default="learned", choices=["learned", "fresh"],
                     help="fresh: clear the learned per-pair Hamming thresholds before every timed step")
     ap.add_argument("--no-autotune", action="store_true", help="keep the plan's default kernel configuration")
+    ap.add_argument("--mutual", action="store_true", help="mutual check (every pair matched in both directions)")
+    ap.add_argument("--accept-single", action="store_true", help="a single ranked candidate matches")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
