@@ -296,9 +296,19 @@ def run_ours(args):
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
+    chunk_matches = [0]
+
+    def count_chunk(first, off, m):
+        chunk_matches[0] += int(off[-1])
+        return False
+
     def step():
         ch.cashash_build_codes(ctx, ds, stream=stream)
-        ch.cashash_match_plan(ctx, plan, moff, mt, cap, F=F_dev, stream=stream)
+        if args.chunk_pairs:  # resumable chunked path: a plan per chunk, lists flushed to host per chunk
+            chunk_matches[0] = 0
+            ch.cashash_match_chunked(ctx, ds, s.pairs, args.chunk_pairs, count_chunk, F=F_dev, stream=stream)
+        else:
+            ch.cashash_match_plan(ctx, plan, moff, mt, cap, F=F_dev, stream=stream)
 
     F_dev = torch.from_numpy(np.ascontiguousarray(s.F)).to(dev) if band else None
     tuning = ch.cashash_plan_get_tuning(plan)
@@ -393,6 +403,8 @@ def run_ours(args):
                              "frac_of_hbm": touched / t_match / 1e9 / pk["hbm_gbs"],
                              "note": "bytes the method touches per query, mostly served from shared memory / L2"}}
 
+    if args.chunk_pairs:  # stage timers and counters cover the last chunk only: no kernel roofline
+        roofline = None
     # end-to-end through the C-ABI with host buffers (pinned descriptors)
     e2e = None
     if not args.no_e2e:
@@ -436,6 +448,8 @@ def run_ours(args):
                 "data": "synthetic",
                 "config": {"workload": wdesc, "images": int(s.n_images), "features": int(s.desc.shape[0]),
                            "pairs": P, "precision": args.precision, "schedule": args.schedule,
+                           "chunked": ("%d pairs per chunk, lists flushed to pinned host memory per chunk"
+                                       % args.chunk_pairs) if args.chunk_pairs else None,
                            "l2": "flushed: 256 MiB write between timed steps (outside the events)",
                            "params": "n=128, 6 tables x 8 bits, k=10, ratio 0.8" + (", band 4 px" if band else "") +
                                      (", mutual check" if args.mutual else "") +
@@ -443,7 +457,7 @@ def run_ours(args):
                            "kernel_tuning": {"kernel": {1: "join", 2: "query"}.get(tuning["kernel"], "per_pair"),
                                              "tile": tuning["tile"], "ctas_per_sm": tuning["ctas_per_sm"],
                                              "autotuned": tuning["ms_sample"] > 0},
-                           "matches_per_step": int(stats["n_matches"]),
+                           "matches_per_step": int(chunk_matches[0] if args.chunk_pairs else stats["n_matches"]),
                            "reevaluated_projections": int(stats["n_reevaluated"])},
                 "features_per_s": s.desc.shape[0] * world * args.steps / t_max,
                 "stages_ms": stages, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
@@ -470,6 +484,8 @@ def main():
                     help="fresh: clear the learned per-pair Hamming thresholds before every timed step")
     ap.add_argument("--no-autotune", action="store_true", help="keep the plan's default kernel configuration")
     ap.add_argument("--mutual", action="store_true", help="mutual check (every pair matched in both directions)")
+    ap.add_argument("--chunk-pairs", type=int, default=0,
+                    help="time the resumable chunked path (cashash_match_chunked) with this many pairs per chunk")
     ap.add_argument("--accept-single", action="store_true", help="a single ranked candidate matches")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -290,6 +290,29 @@ int cashash_match_pair_noalloc(const cashash_params* p, const cashash_set* set, 
                                uint32_t image_b, const double* F_dev, uint64_t* match_off, uint32_t* matches,
                                uint64_t cap, cashash_stream_t stream);
 
+/* Resumable chunked matching of long pair lists (out-of-core outputs; the
+ * paper has no counterpart, its loader streams inputs).  The callback of one
+ * chunk: pairs [first, first + count) of the caller's list were matched;
+ * match_off (HOST [count + 1], starting at 0 for this chunk) and matches
+ * (HOST [match_off[count]][2], as in cashash_match_plan) are valid during the
+ * call only.  Return 0 to continue, non-zero to stop after this chunk. */
+typedef int (*cashash_chunk_fn)(void* user, uint64_t first, uint32_t count, const uint64_t* match_off,
+                                const uint32_t* matches);
+
+/* Matches pairs_host[*cursor .. P) (HOST [P][2]) against the resident set
+ * `set` in chunks of chunk_pairs pairs (one plan per chunk, with the context's
+ * schedule), copies each chunk's lists to pinned host buffers and calls fn.
+ * *cursor advances past every chunk whose callback has returned, so a run
+ * stopped by the callback, or failed, resumes by calling again with the same
+ * cursor.  F_dev: DEVICE [P][9] for the whole list when epi_px >= 0, else
+ * NULL.  Synchronous on `stream`.  Returns OK when the list is done or the
+ * callback stopped it (then *cursor < P).  Errors: EINVAL (cursor > P, bad
+ * pair, chunk_pairs 0, NULL callback), ENOMEM, ECUDA, EDEVICE; the cursor then
+ * still points at the chunk that failed. */
+int cashash_match_chunked(cashash_ctx* ctx, const cashash_set* set, const uint32_t* pairs_host, uint64_t P,
+                          const double* F_dev, uint32_t chunk_pairs, uint64_t* cursor, cashash_chunk_fn fn,
+                          void* user, cashash_stream_t stream);
+
 /* Stage ids of cashash_stats.ms_stage. */
 enum {
   CASHASH_STAGE_CENTRE = 0,     /* column sums, centre and per-row constants */

@@ -61,6 +61,8 @@ class cashash_tuning(C.Structure):
                 ("ms_sample", C.c_double)]
 
 
+CHUNK_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_uint64, C.c_uint32, C.POINTER(C.c_uint64), C.POINTER(C.c_uint32))
+
 _lib = None
 
 
@@ -95,6 +97,7 @@ def _load():
             "cashash_plan_get_tuning": ([vp, P(cashash_tuning)], C.c_int),
             "cashash_plan_set_tuning": ([vp, P(cashash_tuning)], C.c_int),
             "cashash_plan_autotune": ([vp, vp, vp, u32, vp], C.c_int),
+            "cashash_match_chunked": ([vp, P(cashash_set), vp, u64, vp, u32, P(u64), CHUNK_FN, vp, vp], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -111,7 +114,7 @@ def exported_symbols():
             "cashash_plan_destroy", "cashash_match_plan", "cashash_match_pairs", "cashash_sync_status",
             "cashash_run_host", "cashash_get_stats", "cashash_set_profiling", "cashash_match_pair_noalloc",
             "cashash_plan_set_threshold_hint", "cashash_plan_get_tuning", "cashash_plan_set_tuning",
-            "cashash_plan_autotune"]
+            "cashash_plan_autotune", "cashash_match_chunked"]
 
 
 def _check(st, what):
@@ -323,6 +326,35 @@ def cashash_match_pair_noalloc(params: cashash_params, dset: DeviceSet, image_a:
     _check(_load().cashash_match_pair_noalloc(C.byref(params), C.byref(dset.c), int(image_a), int(image_b),
                                               _dptr(F), _dptr(match_off), _dptr(matches), int(cap),
                                               _stream(stream)), "cashash_match_pair_noalloc")
+
+
+def cashash_match_chunked(ctx: Context, dset: DeviceSet, pairs, chunk_pairs: int, on_chunk, cursor: int = 0,
+                          F=None, stream=None) -> int:
+    """Resumable chunked matching (see include/cashash.h).  on_chunk(first,
+    match_off, matches) receives numpy copies of one chunk's lists (match_off
+    relative to the chunk) and returns True to stop.  Returns the cursor: the
+    index of the first pair not yet flushed (len(pairs) when done)."""
+    pairs = np.ascontiguousarray(pairs, np.uint32).reshape(-1, 2)
+    cur = C.c_uint64(int(cursor))
+    errors = []
+
+    def cb(user, first, count, moff, mt):
+        try:
+            off = np.ctypeslib.as_array(moff, shape=(count + 1,)).copy()
+            n = int(off[-1])
+            m = np.ctypeslib.as_array(mt, shape=(max(n, 1), 2))[:n].copy() if n else np.zeros((0, 2), np.uint32)
+            return 1 if on_chunk(int(first), off, m) else 0
+        except Exception as e:  # an exception stops the run; it is raised after the C call returns
+            errors.append(e)
+            return 1
+
+    fn = CHUNK_FN(cb)
+    st = _load().cashash_match_chunked(ctx.handle, C.byref(dset.c), _hptr(pairs), pairs.shape[0], _dptr(F),
+                                       int(chunk_pairs), C.byref(cur), fn, None, _stream(stream))
+    if errors:
+        raise errors[0]
+    _check(st, "cashash_match_chunked")
+    return int(cur.value)
 
 
 def cashash_run_host(ctx: Context, desc: np.ndarray, img_off: np.ndarray, pairs: np.ndarray, cap: int,

@@ -118,6 +118,31 @@ def test_flags_are_checked_before_touching_a_device(lib):
         assert r == want
 
 
+def test_chunked_matching_rejects_bad_arguments_on_the_host(lib):
+    """cashash_match_chunked checks its cursor, chunk size, callback and pairs
+    before any CUDA call."""
+    import ctypes as C
+    import paper_1805_08995_gb300 as ch
+    L = ch._load()
+    st = ch.cashash_set()
+    st.n_images = 2
+    off = np.array([0, 3, 5], np.uint64)
+    st.img_off = off.ctypes.data_as(C.c_void_p)
+    pairs = np.array([[0, 1], [1, 0]], np.uint32)
+    fn = ch.CHUNK_FN(lambda *a: 0)
+    ctx = C.c_void_p(1)  # never dereferenced: every case fails its argument checks first
+
+    def call(cursor, chunk, f, pr=pairs):
+        cur = C.c_uint64(cursor)
+        return L.cashash_match_chunked(ctx, C.byref(st), pr.ctypes.data_as(C.c_void_p), pr.shape[0], None, chunk,
+                                       C.byref(cur), f, None, None)
+
+    assert call(3, 1, fn) == ch.CASHASH_EINVAL            # cursor beyond the list
+    assert call(0, 0, fn) == ch.CASHASH_EINVAL            # empty chunks
+    assert call(0, 1, ch.CHUNK_FN()) == ch.CASHASH_EINVAL  # no callback
+    assert call(0, 1, fn, np.array([[0, 2]], np.uint32)) == ch.CASHASH_EINVAL  # image out of range
+
+
 def test_package_fails_loudly_without_library(tmp_path):
     """The product path has no CPU fallback: without libcashash.so it raises."""
     import sys

@@ -305,6 +305,53 @@ def test_band_kernels_and_the_autotuner(ch, orc):
     ctx.close()
 
 
+@pytest.mark.parametrize("case", ["plain_persistent", "plain_per_pair", "band"])
+def test_chunked_matching_resumes(ch, orc, case):
+    """A long pair list matched in chunks: the callback stops the run after two
+    chunks, a second call resumes at the returned cursor, and the chunks
+    joined equal the oracle's lists for the whole list."""
+    import math
+    pk = dict(schedule=0 if case == "plain_per_pair" else 1)
+    if case == "band":
+        s = synth.epipolar_set(46, n_views=6, n_points=9000, arc=2 * math.pi * 6 / 250, z_max=0.355)
+        pairs = np.concatenate([s.pairs, s.pairs[:, ::-1]])
+        s.F = np.concatenate([s.F, s.F.reshape(-1, 3, 3).transpose(0, 2, 1).reshape(-1, 9)])
+        pk["epi_px"] = 4.0
+    else:
+        sizes = [900, 1400, 0, 300, 2100, 700, 1200]
+        s = synth.random_set(606, sizes)
+        pairs = np.array([(i, k) for i in range(len(sizes)) for k in range(len(sizes)) if i != k], np.uint32)
+    p = ch.cashash_default_params(**pk)
+    ctx = ch.cashash_create(p, s.R)
+    ds = ch.DeviceSet(p, s.img_off, s.desc, s.kpts)
+    ch.cashash_build_codes(ctx, ds)
+    F = torch.from_numpy(np.ascontiguousarray(s.F)).cuda() if s.F is not None else None
+    got = {}
+    seen = []
+
+    def stop_after_two(first, off, m):
+        got[first] = (off, m)
+        seen.append(first)
+        return len(seen) == 2
+
+    chunk = 5
+    cur = ch.cashash_match_chunked(ctx, ds, pairs, chunk, stop_after_two, F=F)
+    assert cur == min(2 * chunk, len(pairs)) and len(seen) == min(2, -(-len(pairs) // chunk))
+    cur = ch.cashash_match_chunked(ctx, ds, pairs, chunk, lambda first, off, m: got.__setitem__(first, (off, m)),
+                                   cursor=cur, F=F)
+    assert cur == len(pairs)
+    po = oparams(orc, pk)
+    mu, codes, buckets = oracle_codes(orc, s.desc, s.R, po)
+    eoff, emt = orc.match_pairs(s.desc, s.img_off, codes, buckets, pairs, po, F=s.F, kpts=s.kpts)
+    assert sorted(got) == list(range(0, len(pairs), chunk))
+    for first, (off, m) in got.items():
+        n = off.shape[0] - 1
+        e0, e1 = int(eoff[first]), int(eoff[first + n])
+        assert np.array_equal(off.astype(np.uint64), eoff[first:first + n + 1] - eoff[first])
+        assert np.array_equal(m, emt[e0:e1])
+    ctx.close()
+
+
 def test_lookup_tables_are_the_bucket_sets(ch, orc):
     sizes = [5000, 10, 0, 3968, 7937]
     s = synth.random_set(303, sizes)
