@@ -506,8 +506,9 @@ int cashash_build_codes(cashash_ctx* c, const cashash_set* s, const double* mean
       StageTimer tm(c, CASHASH_STAGE_TABLES, stream);
       CK(launch_build_tables(s->buckets, c->d_chunk_feat0, c->d_chunk_len, (uint32_t)n_chunks, c->p.n_tables,
                              s->tables, stream));
+      const uint32_t n_max = inn.empty() ? 0u : *std::max_element(inn.begin(), inn.end());
       CK(launch_build_join(s->buckets, s->codes, c->d_img_f0, c->d_img_n, c->d_img_join, s->n_images, c->p.n_tables,
-                           s->tables, stream));
+                           n_max, s->tables, stream));
     }
     c->n_launches += 4;
   }

@@ -213,7 +213,7 @@ cudaError_t launch_build_tables(const uint8_t* buckets, const uint64_t* chunk_fe
                                 uint32_t n_chunks, uint32_t n_tables, uint8_t* tables, cudaStream_t s);
 cudaError_t launch_build_join(const uint8_t* buckets, const uint32_t* codes, const uint64_t* img_f0,
                               const uint32_t* img_n, const uint64_t* img_join, uint32_t n_images, uint32_t n_tables,
-                              uint8_t* join, cudaStream_t s);
+                              uint32_t n_max, uint8_t* join, cudaStream_t s);
 
 struct MatchArgs {
   const uint8_t* desc;

@@ -171,13 +171,14 @@ def test_speculative_threshold_never_changes_results(ch, orc, hint, fixed):
     ctx.close()
 
 
-@pytest.mark.parametrize("case", ["join", "large_image", "band"])
+@pytest.mark.parametrize("case", ["join", "large_image", "huge_candidate", "band"])
 def test_batched_kernel_choice(ch, orc, case):
     """The batched schedule runs the tensor-core bucket join by default
     (calibration + join + fallback + scan + compaction = 5 launches; with the
     band no calibration, 4) unless a query image exceeds the join's
     shared-memory counters; then the speculative per-query kernel (4
-    launches).  Both match the oracle."""
+    launches).  Both match the oracle.  A candidate image of more than 65,535
+    features takes the join tables' global-scatter builder."""
     import math
     pk = dict(schedule=1)
     if case == "band":
@@ -186,9 +187,10 @@ def test_batched_kernel_choice(ch, orc, case):
         s.F = np.concatenate([s.F, s.F.reshape(-1, 3, 3).transpose(0, 2, 1).reshape(-1, 9)])
         pk["epi_px"] = 4.0
     else:
-        sizes = [3000, 2500, 700] if case == "join" else [56000, 1500]
+        sizes = {"join": [3000, 2500, 700], "large_image": [56000, 1500], "huge_candidate": [70000, 1500]}[case]
         s = synth.random_set(808, sizes)
-        pairs = _pairs(sizes) if case == "join" else np.array([[0, 1], [1, 0]], np.uint32)
+        pairs = {"join": _pairs(sizes), "large_image": np.array([[0, 1], [1, 0]], np.uint32),
+                 "huge_candidate": np.array([[1, 0]], np.uint32)}[case]
     p = ch.cashash_default_params(**pk)
     ctx = ch.cashash_create(p, s.R)
     ds = ch.DeviceSet(p, s.img_off, s.desc, s.kpts)
@@ -202,7 +204,7 @@ def test_batched_kernel_choice(ch, orc, case):
     n0 = ch.cashash_get_stats(ctx)["n_launches"]
     ch.cashash_match_plan(ctx, plan, moff, mt, cap, F=F)
     assert ch.cashash_sync_status(ctx) == ch.CASHASH_OK
-    assert ch.cashash_get_stats(ctx)["n_launches"] - n0 == (5 if case == "join" else 4)
+    assert ch.cashash_get_stats(ctx)["n_launches"] - n0 == (4 if case in ("large_image", "band") else 5)
     kern = ch.cashash_plan_get_tuning(plan)["kernel"]
     assert kern == (ch.CASHASH_KERNEL_QUERY if case == "large_image" else ch.CASHASH_KERNEL_JOIN)
     po = oparams(orc, pk)
