@@ -68,6 +68,7 @@ class ImageSet:
     F: np.ndarray | None = None      # [P][9] float64, x_B^T F x_A = 0
     kpts: np.ndarray | None = None   # [N_total][2] float32
     truth: dict | None = None        # planted correspondences, for statistics only
+    scale: np.ndarray | None = None  # [N_total] float32 key-point scale (SIFT sigma), pixels
 
     @property
     def n_images(self) -> int:
@@ -231,7 +232,10 @@ def epipolar_set(seed: int = 4, n_views: int = 500, n_points: int = 200_000, rad
     visible set; F (x_cand^T F x_query = 0) is the ground truth of each pair.
     """
     rng = np.random.default_rng(np.random.SeedSequence([seed, 4]))
+    srng = np.random.default_rng(np.random.SeedSequence([seed, 4, 1]))  # key-point scales only
     X = rng.random((n_points, 3))
+    # a point's scale at unit depth: 1.6 px x 2^E, E ~ Exp(1) capped at 5 octaves
+    s_unit = 1.6 * 2.0 ** np.minimum(srng.exponential(1.0, n_points), 5.0) * 0.2
     templates = sift_like(rng, n_points)
     Kc = np.array([[focal, 0, width / 2.0], [0, focal, height / 2.0], [0, 0, 1.0]])
     centre = np.array([0.5, 0.5, 0.5])
@@ -250,6 +254,7 @@ def epipolar_set(seed: int = 4, n_views: int = 500, n_points: int = 200_000, rad
         cams.append((Rw, t))
     vis = []
     proj = []
+    depth = []
     for Rw, t in cams:
         Y = X @ Rw.T + t
         z = Y[:, 2]
@@ -259,6 +264,7 @@ def epipolar_set(seed: int = 4, n_views: int = 500, n_points: int = 200_000, rad
         ok &= (uv[:, 0] >= 0) & (uv[:, 0] < width) & (uv[:, 1] >= 0) & (uv[:, 1] < height)
         vis.append(np.nonzero(ok)[0])
         proj.append(uv)
+        depth.append(z)
     # pairs by overlap of visible sets
     import scipy.sparse as sp
     rows = np.concatenate([np.full(len(v), i) for i, v in enumerate(vis)])
@@ -271,7 +277,7 @@ def epipolar_set(seed: int = 4, n_views: int = 500, n_points: int = 200_000, rad
         if a < b and c >= min_overlap * max(1, min(nvis[a], nvis[b])):
             pairs.append((a, b))
     pairs = np.array(sorted(pairs), np.uint32).reshape(-1, 2)
-    descs, kps, sizes = [], [], []
+    descs, kps, sizes, scales = [], [], [], []
     for i in range(n_views):
         v = vis[i]
         n_real = len(v)
@@ -286,6 +292,11 @@ def epipolar_set(seed: int = 4, n_views: int = 500, n_points: int = 200_000, rad
         descs.append(d[perm])
         kps.append(k[perm].astype(np.float32))
         sizes.append(d.shape[0])
+        # scale: the point's unit-depth scale over its depth, times log-normal noise; clutter
+        # draws its own
+        sc_real = s_unit[v] / depth[i][v] * np.exp(srng.normal(0, 0.1, n_real))
+        sc_cl = 1.6 * 2.0 ** np.minimum(srng.exponential(1.0, n_cl), 5.0)
+        scales.append(np.concatenate([sc_real, sc_cl])[perm].astype(np.float32))
     Kinv = np.linalg.inv(Kc)
     F = np.zeros((len(pairs), 9))
     for n, (a, b) in enumerate(pairs):
@@ -298,7 +309,13 @@ def epipolar_set(seed: int = 4, n_views: int = 500, n_points: int = 200_000, rad
         F[n] = (Fm / np.linalg.norm(Fm)).ravel()
     return ImageSet(np.concatenate(descs), _offsets(sizes), pairs, projection_matrix(seed),
                     "epipolar:%d views, %d points" % (n_views, n_points), F=F,
-                    kpts=np.concatenate(kps).astype(np.float32))
+                    kpts=np.concatenate(kps).astype(np.float32), scale=np.concatenate(scales))
+
+
+def ransac_words(seed: int, n_pairs: int, n_hyp: int) -> np.ndarray:
+    """Random uint32 words for RANSAC sampling: [n_pairs][n_hyp][8]."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 5]))
+    return rng.integers(0, 2 ** 32, size=(n_pairs, n_hyp, 8), dtype=np.uint64).astype(np.uint32)
 
 
 def config4(seed: int = 4) -> ImageSet:

@@ -59,4 +59,35 @@ def test_pins_reject_mutant(name, tmp_path):
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                         os.path.join(ROOT, "tests", "test_oracle_pins.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
-    assert r.returncode != 0, "pins did not catch mutant '%s'" % name
+    assert r.returncode == 1 and " failed" in r.stdout, "pins did not catch mutant '%s'" % name
+
+
+GA_SRC = os.path.join(ROOT, "oracle", "ga.py")
+
+GA_MUTANTS = {
+    "design rows transposed": ('np.einsum("ni,nj->nij", xb, xa)', 'np.einsum("ni,nj->nij", xa, xb)'),
+    "rank 2 not enforced": ("S[2] = 0.0", "S[2] = S[2]"),
+    "normalisation scale": ("s = np.sqrt(2.0) / md", "s = 1.0 / md"),
+    "Sampson term dropped": (" + Ftx[:, 1] ** 2", ""),
+    "ties to the later hypothesis": ("if cnt > best:", "if cnt >= best:"),
+    "samples may repeat": ("if p <= v:", "if p < v:"),
+    "acceptance not inclusive": ("gp.inlier_den * n_in >= gp.inlier_num * m", "gp.inlier_den * n_in > gp.inlier_num * m"),
+    "no refit": ("if np.count_nonzero(inl) >= 8:", "if False:"),
+    "selection ties to the higher index": ("np.lexsort((np.arange(n), -s.astype(np.float64)))",
+                                           "np.lexsort((-np.arange(n), -s.astype(np.float64)))"),
+    "subset size rounded down": ("k = (n * pct + 99) // 100", "k = (n * pct) // 100"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(GA_MUTANTS))
+def test_ga_pins_reject_mutant(name, tmp_path):
+    old, new = GA_MUTANTS[name]
+    src = open(GA_SRC).read()
+    assert src.count(old) == 1, "mutation anchor not found exactly once: %s" % name
+    mut = tmp_path / "ga_mutant.py"
+    mut.write_text(src.replace(old, new))
+    env = dict(os.environ, CASHASH_ORACLE_GA=str(mut))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_ga.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 1 and " failed" in r.stdout, "pins did not catch mutant '%s'" % name
