@@ -348,6 +348,80 @@ int cashash_get_stats(cashash_ctx* ctx, cashash_stats* out);
 /* Static text for a status code. */
 const char* cashash_strerror(int status);
 
+/* ------------------------------------------------------------------------
+ * Ga-CasHash, first stage (Sec. 5.1).  The top 20 % of each image's features
+ * by SIFT scale are matched exhaustively with CasHash; a pair with at least
+ * 16 matches gets a fundamental matrix from the GPU, and goes on to the
+ * guided matching of Sec. 5.2 (the band, epi_px >= 0, with that F) when at
+ * least 2/3 of its matches are inliers.  The paper names no estimator: this
+ * is the normalised 8-point algorithm (Hartley 1997) inside RANSAC (Fischler
+ * and Bolles 1981) with the squared Sampson distance as the inlier test and a
+ * least-squares refit on the best hypothesis' inliers (at least 8), all in
+ * FP64.  The random draws are caller-given: word k (k = 0..7) of hypothesis h
+ * of pair p, u = words[(p * n_hyp + h) * 8 + k], picks r = floor(u (m - k) /
+ * 2^32), the r-th smallest of the m match indices not drawn before.
+ * Convention: x_B^T F x_A = 0 for the pair (A, B).  F is returned with unit
+ * Frobenius norm and its largest-magnitude entry (first on ties) positive.
+ * ------------------------------------------------------------------------ */
+#define CASHASH_GA_MAX_HYP 4096u
+
+typedef struct {
+  uint32_t top_pct;      /* 20: each image keeps ceil(n * top_pct / 100) features (1..100) */
+  uint32_t min_matches;  /* 16: pairs with fewer stage-1 matches get no F (>= 8) */
+  uint32_t n_hyp;        /* 256: RANSAC hypotheses per pair (1..CASHASH_GA_MAX_HYP) */
+  uint32_t inlier_num;   /* 2 */
+  uint32_t inlier_den;   /* 3: accepted when inlier_den * inliers >= inlier_num * matches */
+  uint32_t reserved;
+  double thresh_px;      /* 3.0: inlier when the Sampson distance is <= thresh_px pixels */
+} cashash_ga_params;
+
+typedef struct {
+  uint32_t n_matches;    /* stage-1 matches of the pair */
+  uint32_t n_inliers;    /* inliers of the returned F (0 when there is none) */
+  uint32_t best_hyp;     /* winning hypothesis, or 0xFFFFFFFF */
+  uint32_t accepted;     /* 1: the pair goes on to guided matching with F */
+} cashash_ga_info;
+
+/* Fills gp with the defaults listed above. */
+void cashash_ga_default_params(cashash_ga_params* gp);
+
+/* The parameters a context was created with (HOST out).  Errors: EINVAL. */
+int cashash_get_params(const cashash_ctx* ctx, cashash_params* out);
+
+/* HOST sub_off [n_images + 1] out: offsets of the selected subsets
+ * (image i keeps ceil(n_i * top_pct / 100) features).  Errors: EINVAL. */
+int cashash_ga_subset_offsets(const uint64_t* img_off, uint32_t n_images, uint32_t top_pct, uint64_t* sub_off);
+
+/* Selection by scale: DEVICE scale [n_features] (finite; -0 counts as 0),
+ * HOST img_off; DEVICE sel out [sub_off[n_images]]: the global indices of
+ * each image's ceil(n * top_pct / 100) features of largest scale (ties to the
+ * lower index), ascending within the image.  Sets of fewer than 2^32
+ * features.  Asynchronous on `stream`.  Errors: EINVAL, ENOMEM, ECUDA. */
+int cashash_ga_select(const float* scale, const uint64_t* img_off, uint32_t n_images, uint32_t top_pct,
+                      uint32_t* sel, cashash_stream_t stream);
+
+/* RANSAC F estimation for every pair from its match list: DEVICE kpts
+ * [N][2] (HOST img_off gives the images), HOST pairs [P][2], DEVICE
+ * match_off [P + 1] and matches [.][2] (query, candidate) local indices as
+ * written by cashash_match_plan, DEVICE words [P][n_hyp][8]; DEVICE out
+ * F [P][9] (row-major; zeros without an estimate) and info [P].  Reads
+ * match_off[P] on the host (synchronises `stream` once); the rest is
+ * asynchronous.  Errors: EINVAL, ENOMEM, ECUDA. */
+int cashash_estimate_F(const float* kpts, const uint64_t* img_off, uint32_t n_images, const uint32_t* pairs,
+                       uint32_t P, const uint64_t* match_off, const uint32_t* matches, const cashash_ga_params* gp,
+                       const uint32_t* words, double* F, cashash_ga_info* info, cashash_stream_t stream);
+
+/* The whole first stage for the pairs of `set` (its desc and kpts; codes,
+ * tables etc. are not used): selection, the subsets' codes with the caller's
+ * centre mean_host (HOST [128]: the full set's, e.g. from cashash_get_mean,
+ * so stage-1 codes are the full set's codes of the selected features),
+ * CasHash matching of the subsets with ctx (which must have epi_px < 0), then
+ * cashash_estimate_F.  Work buffers are allocated and released inside; the
+ * call synchronises `stream`.  Errors: EINVAL, ENOMEM, ECUDA, EDEVICE. */
+int cashash_ga_stage1(cashash_ctx* ctx, const cashash_set* set, const float* scale, const double* mean_host,
+                      const uint32_t* pairs, uint32_t P, const cashash_ga_params* gp, const uint32_t* words,
+                      double* F, cashash_ga_info* info, cashash_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

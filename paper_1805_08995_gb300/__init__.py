@@ -61,6 +61,15 @@ class cashash_tuning(C.Structure):
                 ("ms_sample", C.c_double)]
 
 
+class cashash_ga_params(C.Structure):
+    _fields_ = [("top_pct", C.c_uint32), ("min_matches", C.c_uint32), ("n_hyp", C.c_uint32),
+                ("inlier_num", C.c_uint32), ("inlier_den", C.c_uint32), ("reserved", C.c_uint32),
+                ("thresh_px", C.c_double)]
+
+
+GA_MAX_HYP = 4096
+GA_NONE = 0xFFFFFFFF
+
 CHUNK_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_uint64, C.c_uint32, C.POINTER(C.c_uint64), C.POINTER(C.c_uint32))
 
 _lib = None
@@ -98,6 +107,13 @@ def _load():
             "cashash_plan_set_tuning": ([vp, P(cashash_tuning)], C.c_int),
             "cashash_plan_autotune": ([vp, vp, vp, u32, vp], C.c_int),
             "cashash_match_chunked": ([vp, P(cashash_set), vp, u64, vp, u32, P(u64), CHUNK_FN, vp, vp], C.c_int),
+            "cashash_get_params": ([vp, P(cashash_params)], C.c_int),
+            "cashash_ga_default_params": ([P(cashash_ga_params)], None),
+            "cashash_ga_subset_offsets": ([vp, u32, u32, vp], C.c_int),
+            "cashash_ga_select": ([vp, vp, u32, u32, vp, vp], C.c_int),
+            "cashash_estimate_F": ([vp, vp, u32, vp, u32, vp, vp, P(cashash_ga_params), vp, vp, vp, vp], C.c_int),
+            "cashash_ga_stage1": ([vp, P(cashash_set), vp, vp, vp, u32, P(cashash_ga_params), vp, vp, vp, vp],
+                                  C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -114,7 +130,8 @@ def exported_symbols():
             "cashash_plan_destroy", "cashash_match_plan", "cashash_match_pairs", "cashash_sync_status",
             "cashash_run_host", "cashash_get_stats", "cashash_set_profiling", "cashash_match_pair_noalloc",
             "cashash_plan_set_threshold_hint", "cashash_plan_get_tuning", "cashash_plan_set_tuning",
-            "cashash_plan_autotune", "cashash_match_chunked"]
+            "cashash_plan_autotune", "cashash_match_chunked", "cashash_get_params", "cashash_ga_default_params",
+            "cashash_ga_subset_offsets", "cashash_ga_select", "cashash_estimate_F", "cashash_ga_stage1"]
 
 
 def _check(st, what):
@@ -381,3 +398,78 @@ def cashash_run_host(ctx: Context, desc: np.ndarray, img_off: np.ndarray, pairs:
         raise CashashError(st, "cashash_run_host")
     total = int(match_off[P])
     return st, match_off, matches[:min(total, int(cap))]
+
+
+# ---------------------------------------------------------------------------
+# Ga-CasHash first stage (Sec. 5.1)
+# ---------------------------------------------------------------------------
+
+def cashash_get_params(ctx: Context) -> cashash_params:
+    p = cashash_params()
+    _check(_load().cashash_get_params(ctx.handle, C.byref(p)), "cashash_get_params")
+    return p
+
+
+def cashash_ga_default_params(**over) -> cashash_ga_params:
+    g = cashash_ga_params()
+    _load().cashash_ga_default_params(C.byref(g))
+    for k, v in over.items():
+        setattr(g, k, v)
+    return g
+
+
+def cashash_ga_subset_offsets(img_off: np.ndarray, top_pct: int) -> np.ndarray:
+    off = np.ascontiguousarray(img_off, np.uint64)
+    sub = np.zeros(len(off), np.uint64)
+    _check(_load().cashash_ga_subset_offsets(_hptr(off), len(off) - 1, top_pct, _hptr(sub)),
+           "cashash_ga_subset_offsets")
+    return sub
+
+
+def cashash_ga_select(scale, img_off: np.ndarray, top_pct: int, stream=None):
+    """Selected global feature indices (torch int32 on the device, uint32 values)
+    and the subset offsets (numpy)."""
+    import torch
+    off = np.ascontiguousarray(img_off, np.uint64)
+    sub = cashash_ga_subset_offsets(off, top_pct)
+    sel = torch.empty((max(int(sub[-1]), 1),), dtype=torch.int32, device=scale.device)
+    _check(_load().cashash_ga_select(_dptr(scale), _hptr(off), len(off) - 1, top_pct, _dptr(sel), _stream(stream)),
+           "cashash_ga_select")
+    return sel[:int(sub[-1])], sub
+
+
+def _ga_out(P: int, device):
+    import torch
+    F = torch.empty((max(P, 1), 9), dtype=torch.float64, device=device)
+    info = torch.empty((max(P, 1), 4), dtype=torch.int32, device=device)
+    return F, info
+
+
+def cashash_estimate_F(kpts, img_off: np.ndarray, pairs, match_off, matches, words, gp: cashash_ga_params = None,
+                       stream=None):
+    """F [P][9] (float64) and info [P][4] (int32: n_matches, n_inliers, best_hyp,
+    accepted) on the device, from the match lists of cashash_match_plan."""
+    gp = gp or cashash_ga_default_params()
+    off = np.ascontiguousarray(img_off, np.uint64)
+    pr = np.ascontiguousarray(pairs, np.uint32).reshape(-1, 2)
+    P = len(pr)
+    F, info = _ga_out(P, kpts.device)
+    _check(_load().cashash_estimate_F(_dptr(kpts), _hptr(off), len(off) - 1, _hptr(pr), P, _dptr(match_off),
+                                      _dptr(matches), C.byref(gp), _dptr(words), _dptr(F), _dptr(info),
+                                      _stream(stream)), "cashash_estimate_F")
+    return F[:P], info[:P]
+
+
+def cashash_ga_stage1(ctx: Context, dset: DeviceSet, scale, mean: np.ndarray, pairs, words,
+                      gp: cashash_ga_params = None, stream=None):
+    """Selection, stage-1 CasHash matching of the subsets and F estimation;
+    returns (F [P][9], info [P][4]) on the device."""
+    gp = gp or cashash_ga_default_params()
+    pr = np.ascontiguousarray(pairs, np.uint32).reshape(-1, 2)
+    P = len(pr)
+    m = np.ascontiguousarray(mean, np.float64)
+    F, info = _ga_out(P, dset.desc.device)
+    _check(_load().cashash_ga_stage1(ctx.handle, C.byref(dset.c), _dptr(scale), _hptr(m), _hptr(pr), P,
+                                     C.byref(gp), _dptr(words), _dptr(F), _dptr(info), _stream(stream)),
+           "cashash_ga_stage1")
+    return F[:P], info[:P]

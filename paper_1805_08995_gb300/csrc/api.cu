@@ -322,6 +322,12 @@ uint64_t cashash_tables_bytes(const cashash_params* p, const uint64_t* img_off, 
   return std::max<uint64_t>(ch, 1) * chunk_bytes(p->n_tables) + jb;
 }
 
+int cashash_get_params(const cashash_ctx* c, cashash_params* out) {
+  if (!c || !out) return CASHASH_EINVAL;
+  *out = c->p;
+  return CASHASH_OK;
+}
+
 void cashash_destroy(cashash_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->device);

@@ -1,0 +1,709 @@
+// First stage of Ga-CasHash (Sec. 5.1): the top 20 % of each image's
+// features by SIFT scale are matched exhaustively with CasHash; a pair with
+// at least 16 matches gets a fundamental matrix estimated on the GPU, and it
+// goes on to the guided matching of Sec. 5.2 when at least 2/3 of its matches
+// are inliers of that F.
+//
+// The paper names no estimator.  Here: the normalised 8-point algorithm
+// (Hartley 1997) inside RANSAC (Fischler and Bolles 1981), the squared
+// Sampson distance (Hartley and Zisserman, Multiple View Geometry, 2nd ed.,
+// Sec. 11.4.3) as the inlier test, and a least-squares refit on the winning
+// hypothesis' inliers.  All geometry is FP64.  The random draws of RANSAC are
+// caller-given uint32 words; word k of a hypothesis picks r_k = floor(u_k (m -
+// k) / 2^32), the r_k-th smallest match index not drawn before.
+//
+// Kernels:
+//   k_ga_select   one CTA per image: radix select of the k-th largest scale
+//                 key (4 passes of 8 bits), then a stable compaction in
+//                 feature order (ties to the lower index);
+//   k_ga_gather   subset descriptors and key-points;
+//   k_ga_ransac   one CTA per pair: Hartley normalisation (block sums), one
+//                 hypothesis per thread (8 x 9 elimination with partial
+//                 pivoting for the null vector, rank 2 by a one-sided Jacobi
+//                 SVD of the 3 x 3, inlier count), block argmax, refit from
+//                 the 9 x 9 normal matrix (cyclic Jacobi), final count.
+#include <algorithm>
+#include <vector>
+
+#include "internal.h"
+
+namespace chx {
+
+constexpr int GA_T = 256;
+constexpr uint32_t GA_NONE = 0xFFFFFFFFu;
+
+// ---------------------------------------------------------------------------
+// selection by scale
+// ---------------------------------------------------------------------------
+
+// Order-preserving uint32 key of a float (total order on finite values; -0 as +0).
+__device__ __forceinline__ uint32_t scale_key(float s) {
+  uint32_t b = __float_as_uint(s);
+  if (b == 0x80000000u) b = 0u;
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+// Exclusive rank of this thread's flag among the CTA's flags, and the total.
+__device__ __forceinline__ uint32_t cta_scan(bool f, uint32_t* s_w, uint32_t& total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint32_t bal = __ballot_sync(0xFFFFFFFFu, f);
+  if (lane == 0) s_w[w] = __popc(bal);
+  __syncthreads();
+  uint32_t before = 0, tot = 0;
+  for (int k = 0; k < GA_T / 32; ++k) {
+    const uint32_t c = s_w[k];
+    if (k < w) before += c;
+    tot += c;
+  }
+  __syncthreads();
+  total = tot;
+  return before + __popc(bal & ((1u << lane) - 1u));
+}
+
+__global__ void __launch_bounds__(GA_T) k_ga_select(const float* __restrict__ scale, const uint64_t* __restrict__ off,
+                                                    const uint64_t* __restrict__ sub_off, uint32_t* __restrict__ sel) {
+  __shared__ uint32_t hist[256];
+  __shared__ uint32_t s_w[GA_T / 32];
+  __shared__ uint32_t s_digit, s_above;
+  const uint32_t i = blockIdx.x, tid = threadIdx.x;
+  const uint64_t a = off[i];
+  const uint32_t n = (uint32_t)(off[i + 1] - a);
+  const uint32_t k = (uint32_t)(sub_off[i + 1] - sub_off[i]);
+  uint32_t* out = sel + sub_off[i];
+  if (k == 0) return;
+  // the k-th largest key: thr; need = how many keys equal to thr are taken
+  uint32_t thr = 0, need = k;
+  if (k < n) {
+    uint32_t prefix = 0, pmask = 0;
+    for (int pass = 0; pass < 4; ++pass) {
+      const int shift = 24 - 8 * pass;
+      for (uint32_t d = tid; d < 256; d += GA_T) hist[d] = 0;
+      __syncthreads();
+      for (uint32_t j = tid; j < n; j += GA_T) {
+        const uint32_t key = scale_key(scale[a + j]);
+        if ((key & pmask) == prefix) atomicAdd(&hist[(key >> shift) & 255u], 1u);
+      }
+      __syncthreads();
+      if (tid == 0) {
+        uint32_t above = 0, d = 255;
+        for (;; --d) {
+          if (above + hist[d] >= need || d == 0) break;
+          above += hist[d];
+        }
+        s_digit = d;
+        s_above = above;
+      }
+      __syncthreads();
+      prefix |= s_digit << shift;
+      pmask |= 0xFFu << shift;
+      need -= s_above;
+      __syncthreads();
+    }
+    thr = prefix;
+  }
+  // stable compaction in feature order
+  uint32_t eq_before = 0, out_before = 0;
+  for (uint32_t j0 = 0; j0 < n; j0 += GA_T) {
+    const uint32_t j = j0 + tid;
+    const uint32_t key = j < n ? scale_key(scale[a + j]) : 0u;
+    const bool gt = j < n && (k == n || key > thr);
+    const bool eq = j < n && k < n && key == thr;
+    uint32_t eq_tot;
+    const uint32_t eq_rank = cta_scan(eq, s_w, eq_tot);
+    const bool take = gt || (eq && eq_before + eq_rank < need);
+    uint32_t tk_tot;
+    const uint32_t pos = cta_scan(take, s_w, tk_tot);
+    if (take) out[out_before + pos] = (uint32_t)(a + j);
+    eq_before += eq_tot;
+    out_before += tk_tot;
+  }
+}
+
+__global__ void k_ga_gather(const uint32_t* __restrict__ sel, uint64_t n_sub, const uint8_t* __restrict__ desc,
+                            const float2* __restrict__ kpts, uint8_t* __restrict__ desc_sub,
+                            float2* __restrict__ kpts_sub) {
+  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n_sub * 8;
+       e += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t r = e >> 3, c = e & 7;
+    const uint64_t f = sel[r];
+    reinterpret_cast<uint4*>(desc_sub)[r * 8 + c] = reinterpret_cast<const uint4*>(desc)[f * 8 + c];
+    if (c == 0) kpts_sub[r] = kpts[f];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// fundamental matrix
+// ---------------------------------------------------------------------------
+
+// One correspondence: key-point of the query (x, y) and of the candidate (z, w).
+struct alignas(32) GaPt {
+  double x, y, z, w;
+};
+
+struct GaArgs {
+  const float2* kpts;      // [N][2]
+  const uint64_t* img_off; // [n_images + 1]
+  const uint32_t* pairs;   // [P][2]
+  const uint64_t* moff;    // [P + 1]
+  const uint32_t* mt;      // [.][2] (q, j) local
+  const uint32_t* words;   // [P][n_hyp][8]
+  GaPt* pts;            // [total matches] scratch: (xa, ya, xb, yb)
+  uint8_t* inl;            // [total matches] scratch
+  double* F;               // [P][9] out
+  uint4* info;             // [P] out
+  uint32_t P, n_hyp, min_matches, num, den;
+  double t2;
+};
+
+__device__ double block_sum(double v, double* s_d) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+  if (lane == 0) s_d[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int k = 0; k < GA_T / 32; ++k) t += s_d[k];
+  __syncthreads();
+  return t;
+}
+
+// Squared Sampson distance <= t2 (x_B^T F x_A = 0).
+__device__ __forceinline__ bool ga_inlier(const double* F, const GaPt p, double t2) {
+  const double fx0 = F[0] * p.x + F[1] * p.y + F[2];
+  const double fx1 = F[3] * p.x + F[4] * p.y + F[5];
+  const double fx2 = F[6] * p.x + F[7] * p.y + F[8];
+  const double ft0 = F[0] * p.z + F[3] * p.w + F[6];
+  const double ft1 = F[1] * p.z + F[4] * p.w + F[7];
+  const double r = p.z * fx0 + p.w * fx1 + fx2;
+  const double e = (r * r) / (fx0 * fx0 + fx1 * fx1 + ft0 * ft0 + ft1 * ft1);
+  return e <= t2;
+}
+
+// One-sided Jacobi SVD of a 3 x 3 (columns orthogonalised); returns the right
+// singular vector of the smallest singular value in v.
+__device__ void smallest_right_sv3(const double* Fm, double* v) {
+  double U[9], V[9];
+  for (int e = 0; e < 9; ++e) {
+    U[e] = Fm[e];
+    V[e] = (e % 4 == 0) ? 1.0 : 0.0;
+  }
+  for (int sweep = 0; sweep < 30; ++sweep) {
+    bool rot = false;
+    for (int p = 0; p < 2; ++p)
+      for (int q = p + 1; q < 3; ++q) {
+        double al = 0.0, be = 0.0, ga = 0.0;
+        for (int r = 0; r < 3; ++r) {
+          al += U[3 * r + p] * U[3 * r + p];
+          be += U[3 * r + q] * U[3 * r + q];
+          ga += U[3 * r + p] * U[3 * r + q];
+        }
+        if (fabs(ga) <= 1e-300 || fabs(ga) <= 1e-15 * sqrt(al * be)) continue;
+        rot = true;
+        const double zeta = (be - al) / (2.0 * ga);
+        const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+        for (int r = 0; r < 3; ++r) {
+          const double up = U[3 * r + p], uq = U[3 * r + q];
+          U[3 * r + p] = c * up - s * uq;
+          U[3 * r + q] = s * up + c * uq;
+          const double vp = V[3 * r + p], vq = V[3 * r + q];
+          V[3 * r + p] = c * vp - s * vq;
+          V[3 * r + q] = s * vp + c * vq;
+        }
+      }
+    if (!rot) break;
+  }
+  int best = 0;
+  double bn = 0.0;
+  for (int col = 0; col < 3; ++col) {
+    const double nn = U[col] * U[col] + U[3 + col] * U[3 + col] + U[6 + col] * U[6 + col];
+    if (col == 0 || nn < bn) {
+      bn = nn;
+      best = col;
+    }
+  }
+  for (int r = 0; r < 3; ++r) v[r] = V[3 * r + best];
+}
+
+// F := F - (F v)(v^T) for the smallest right singular vector v (closest rank 2).
+__device__ void rank2(double* Fm) {
+  double v[3];
+  smallest_right_sv3(Fm, v);
+  for (int r = 0; r < 3; ++r) {
+    const double fv = Fm[3 * r] * v[0] + Fm[3 * r + 1] * v[1] + Fm[3 * r + 2] * v[2];
+    for (int c = 0; c < 3; ++c) Fm[3 * r + c] -= fv * v[c];
+  }
+}
+
+// F = Tb^T Fn Ta for T = [[s, 0, -s cx], [0, s, -s cy], [0, 0, 1]].
+__device__ void denormalise(const double* Fn, const double* Ta, const double* Tb, double* F) {
+  double G[9];  // Fn Ta
+  for (int r = 0; r < 3; ++r) {
+    G[3 * r + 0] = Fn[3 * r] * Ta[0];
+    G[3 * r + 1] = Fn[3 * r + 1] * Ta[0];
+    G[3 * r + 2] = Fn[3 * r] * Ta[1] + Fn[3 * r + 1] * Ta[2] + Fn[3 * r + 2];
+  }
+  for (int c = 0; c < 3; ++c) {
+    F[c] = Tb[0] * G[c];
+    F[3 + c] = Tb[0] * G[3 + c];
+    F[6 + c] = Tb[1] * G[c] + Tb[2] * G[3 + c] + G[6 + c];
+  }
+}
+
+// The design row of x_B^T F x_A = 0 (f = F row-major) in normalised coordinates.
+__device__ __forceinline__ void design_row(const GaPt p, const double* Ta, const double* Tb, double* row) {
+  const double xa = Ta[0] * p.x + Ta[1], ya = Ta[0] * p.y + Ta[2];
+  const double xb = Tb[0] * p.z + Tb[1], yb = Tb[0] * p.w + Tb[2];
+  row[0] = xb * xa;
+  row[1] = xb * ya;
+  row[2] = xb;
+  row[3] = yb * xa;
+  row[4] = yb * ya;
+  row[5] = yb;
+  row[6] = xa;
+  row[7] = ya;
+  row[8] = 1.0;
+}
+
+// Hypothesis h of the pair: 8 distinct matches from the words, the null vector
+// of the 8 x 9 system (partial pivoting, f_8 = 1), rank 2, denormalised.
+// false when the sample is degenerate or the result is not finite.
+__device__ bool hypothesis(const GaPt* pts, uint32_t m, const uint32_t* w, const double* Ta, const double* Tb,
+                           double* F) {
+  uint32_t idx[8];
+  for (int k = 0; k < 8; ++k) {
+    uint32_t v = (uint32_t)(((uint64_t)w[k] * (uint64_t)(m - k)) >> 32);
+    // walk the earlier picks in ascending order
+    uint32_t sorted[8];
+    for (int t = 0; t < k; ++t) sorted[t] = idx[t];
+    for (int t = 1; t < k; ++t)
+      for (int u = t; u > 0 && sorted[u - 1] > sorted[u]; --u) {
+        const uint32_t x = sorted[u];
+        sorted[u] = sorted[u - 1];
+        sorted[u - 1] = x;
+      }
+    for (int t = 0; t < k; ++t)
+      if (sorted[t] <= v) ++v;
+    idx[k] = v;
+  }
+  double A[8][9];
+  for (int r = 0; r < 8; ++r) design_row(pts[idx[r]], Ta, Tb, A[r]);
+  for (int c = 0; c < 8; ++c) {
+    int piv = c;
+    double pm = fabs(A[c][c]);
+    for (int r = c + 1; r < 8; ++r)
+      if (fabs(A[r][c]) > pm) {
+        pm = fabs(A[r][c]);
+        piv = r;
+      }
+    if (!(pm > 0.0)) return false;
+    if (piv != c)
+      for (int e = 0; e < 9; ++e) {
+        const double x = A[c][e];
+        A[c][e] = A[piv][e];
+        A[piv][e] = x;
+      }
+    for (int r = c + 1; r < 8; ++r) {
+      const double l = A[r][c] / A[c][c];
+      for (int e = c; e < 9; ++e) A[r][e] -= l * A[c][e];
+    }
+  }
+  double f[9];
+  f[8] = 1.0;
+  for (int c = 7; c >= 0; --c) {
+    double s = 0.0;
+    for (int e = c + 1; e < 9; ++e) s += A[c][e] * f[e];
+    f[c] = -s / A[c][c];
+  }
+  rank2(f);
+  denormalise(f, Ta, Tb, F);
+  for (int e = 0; e < 9; ++e)
+    if (!isfinite(F[e])) return false;
+  return true;
+}
+
+// Eigenvector of the smallest eigenvalue of a symmetric 9 x 9 (cyclic Jacobi).
+__device__ void smallest_eigvec9(double* M, double* v) {
+  double V[81];
+  for (int e = 0; e < 81; ++e) V[e] = (e % 10 == 0) ? 1.0 : 0.0;
+  for (int sweep = 0; sweep < 30; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int p = 0; p < 9; ++p)
+      for (int q = 0; q < 9; ++q) {
+        tot += M[9 * p + q] * M[9 * p + q];
+        if (p != q) off += M[9 * p + q] * M[9 * p + q];
+      }
+    if (off <= 1e-32 * tot) break;
+    for (int p = 0; p < 8; ++p)
+      for (int q = p + 1; q < 9; ++q) {
+        const double apq = M[9 * p + q];
+        if (fabs(apq) <= 1e-300) continue;
+        const double theta = (M[9 * q + q] - M[9 * p + p]) / (2.0 * apq);
+        const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+        const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+        for (int k = 0; k < 9; ++k) {  // columns p, q
+          const double mkp = M[9 * k + p], mkq = M[9 * k + q];
+          M[9 * k + p] = c * mkp - s * mkq;
+          M[9 * k + q] = s * mkp + c * mkq;
+        }
+        for (int k = 0; k < 9; ++k) {  // rows p, q
+          const double mpk = M[9 * p + k], mqk = M[9 * q + k];
+          M[9 * p + k] = c * mpk - s * mqk;
+          M[9 * q + k] = s * mpk + c * mqk;
+        }
+        for (int k = 0; k < 9; ++k) {
+          const double vkp = V[9 * k + p], vkq = V[9 * k + q];
+          V[9 * k + p] = c * vkp - s * vkq;
+          V[9 * k + q] = s * vkp + c * vkq;
+        }
+      }
+  }
+  int best = 0;
+  for (int p = 1; p < 9; ++p)
+    if (M[9 * p + p] < M[9 * best + best]) best = p;
+  for (int k = 0; k < 9; ++k) v[k] = V[9 * k + best];
+}
+
+__global__ void __launch_bounds__(GA_T) k_ga_ransac(GaArgs a) {
+  __shared__ double s_d[GA_T / 32];
+  __shared__ uint32_t s_best[GA_T / 32][2];
+  __shared__ double s_F[9], s_M[45];
+  __shared__ uint32_t s_bh;
+  const uint32_t p = blockIdx.x, tid = threadIdx.x;
+  const uint64_t m0 = a.moff[p];
+  const uint32_t m = (uint32_t)(a.moff[p + 1] - m0);
+  double* Fout = a.F + 9 * (size_t)p;
+  if (m < a.min_matches) {
+    if (tid < 9) Fout[tid] = 0.0;
+    if (tid == 0) a.info[p] = make_uint4(m, 0u, GA_NONE, 0u);
+    return;
+  }
+  const uint64_t A0 = a.img_off[a.pairs[2 * p]], B0 = a.img_off[a.pairs[2 * p + 1]];
+  GaPt* pts = a.pts + m0;
+  uint8_t* inl = a.inl + m0;
+  double sxa = 0.0, sya = 0.0, sxb = 0.0, syb = 0.0;
+  for (uint32_t i = tid; i < m; i += GA_T) {
+    const float2 pa = a.kpts[A0 + a.mt[2 * (m0 + i)]], pb = a.kpts[B0 + a.mt[2 * (m0 + i) + 1]];
+    const GaPt q = {(double)pa.x, (double)pa.y, (double)pb.x, (double)pb.y};
+    pts[i] = q;
+    sxa += q.x;
+    sya += q.y;
+    sxb += q.z;
+    syb += q.w;
+  }
+  const double cxa = block_sum(sxa, s_d) / m, cya = block_sum(sya, s_d) / m;
+  const double cxb = block_sum(sxb, s_d) / m, cyb = block_sum(syb, s_d) / m;
+  __syncthreads();  // pts visible to the whole CTA
+  double da = 0.0, db = 0.0;
+  for (uint32_t i = tid; i < m; i += GA_T) {
+    const GaPt q = pts[i];
+    da += sqrt((q.x - cxa) * (q.x - cxa) + (q.y - cya) * (q.y - cya));
+    db += sqrt((q.z - cxb) * (q.z - cxb) + (q.w - cyb) * (q.w - cyb));
+  }
+  const double sa = sqrt(2.0) / (block_sum(da, s_d) / m), sb = sqrt(2.0) / (block_sum(db, s_d) / m);
+  const double Ta[3] = {sa, -sa * cxa, -sa * cya}, Tb[3] = {sb, -sb * cxb, -sb * cyb};  // s, -s cx, -s cy
+
+  // hypotheses: thread h takes h, h + GA_T, ...; the most inliers win, ties to the lower h
+  uint32_t best_c = 0, best_h = GA_NONE;
+  for (uint32_t h = tid; h < a.n_hyp; h += GA_T) {
+    double F[9];
+    if (!hypothesis(pts, m, a.words + ((size_t)p * a.n_hyp + h) * 8, Ta, Tb, F)) continue;
+    uint32_t c = 0;
+    for (uint32_t i = 0; i < m; ++i) c += ga_inlier(F, pts[i], a.t2) ? 1u : 0u;
+    if (best_h == GA_NONE || c > best_c) {
+      best_c = c;
+      best_h = h;
+    }
+  }
+  {  // CTA argmax: key (count, -h), invalid lowest
+    const int lane = tid & 31, w = tid >> 5;
+    for (int o = 16; o > 0; o >>= 1) {
+      const uint32_t oc = __shfl_xor_sync(0xFFFFFFFFu, best_c, o), oh = __shfl_xor_sync(0xFFFFFFFFu, best_h, o);
+      const bool better = oh != GA_NONE && (best_h == GA_NONE || oc > best_c || (oc == best_c && oh < best_h));
+      if (better) {
+        best_c = oc;
+        best_h = oh;
+      }
+    }
+    if (lane == 0) {
+      s_best[w][0] = best_c;
+      s_best[w][1] = best_h;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      uint32_t bc = 0, bh = GA_NONE;
+      for (int k = 0; k < GA_T / 32; ++k) {
+        const uint32_t oc = s_best[k][0], oh = s_best[k][1];
+        if (oh != GA_NONE && (bh == GA_NONE || oc > bc || (oc == bc && oh < bh))) {
+          bc = oc;
+          bh = oh;
+        }
+      }
+      s_bh = bh;
+      if (bh != GA_NONE) hypothesis(pts, m, a.words + ((size_t)p * a.n_hyp + bh) * 8, Ta, Tb, s_F);
+    }
+    __syncthreads();
+  }
+  const uint32_t bh = s_bh;
+  if (bh == GA_NONE) {
+    if (tid < 9) Fout[tid] = 0.0;
+    if (tid == 0) a.info[p] = make_uint4(m, 0u, GA_NONE, 0u);
+    return;
+  }
+  double F[9];
+  for (int e = 0; e < 9; ++e) F[e] = s_F[e];
+  uint32_t cnt_local = 0;
+  for (uint32_t i = tid; i < m; i += GA_T) {
+    const bool in = ga_inlier(F, pts[i], a.t2);
+    inl[i] = in ? 1 : 0;
+    cnt_local += in ? 1u : 0u;
+  }
+  const uint32_t n_best = (uint32_t)block_sum((double)cnt_local, s_d);
+  __syncthreads();  // inlier flags visible
+  if (n_best >= 8) {
+    // normal matrix of the inliers' design rows, entries (r, c), r <= c, each summed in match order
+    if (tid < 45) {
+      uint32_t r = 0, t = tid;
+      while (t >= 9 - r) {
+        t -= 9 - r;
+        ++r;
+      }
+      const uint32_t c = r + t;
+      double s = 0.0;
+      for (uint32_t i = 0; i < m; ++i) {
+        if (!inl[i]) continue;
+        double row[9];
+        design_row(pts[i], Ta, Tb, row);
+        s += row[r] * row[c];
+      }
+      s_M[tid] = s;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double M[81], f[9];
+      for (uint32_t r = 0, e = 0; r < 9; ++r)
+        for (uint32_t c = r; c < 9; ++c, ++e) M[9 * r + c] = M[9 * c + r] = s_M[e];
+      smallest_eigvec9(M, f);
+      rank2(f);
+      denormalise(f, Ta, Tb, s_F);
+    }
+    __syncthreads();
+    for (int e = 0; e < 9; ++e) F[e] = s_F[e];
+  }
+  // unit Frobenius norm, largest-magnitude entry (first on ties) positive
+  double nn = 0.0, big = 0.0;
+  int bi = 0;
+  for (int e = 0; e < 9; ++e) {
+    nn += F[e] * F[e];
+    if (fabs(F[e]) > big) {
+      big = fabs(F[e]);
+      bi = e;
+    }
+  }
+  const double sc = (F[bi] > 0.0 ? 1.0 : -1.0) / sqrt(nn);
+  for (int e = 0; e < 9; ++e) F[e] *= sc;
+  uint32_t c2 = 0;
+  for (uint32_t i = tid; i < m; i += GA_T) c2 += ga_inlier(F, pts[i], a.t2) ? 1u : 0u;
+  const uint32_t n_in = (uint32_t)block_sum((double)c2, s_d);
+  if (tid < 9) Fout[tid] = F[tid];
+  if (tid == 0)
+    a.info[p] = make_uint4(m, n_in, bh, (uint64_t)a.den * n_in >= (uint64_t)a.num * m ? 1u : 0u);
+}
+
+}  // namespace chx
+
+using namespace chx;
+
+namespace {
+
+int err_of(cudaError_t e) {
+  if (e == cudaSuccess) return CASHASH_OK;
+  return e == cudaErrorMemoryAllocation ? CASHASH_ENOMEM : CASHASH_ECUDA;
+}
+
+bool ga_params_ok(const cashash_ga_params* gp) {
+  return gp && gp->top_pct >= 1 && gp->top_pct <= 100 && gp->min_matches >= 8 && gp->n_hyp >= 1 &&
+         gp->n_hyp <= CASHASH_GA_MAX_HYP && gp->inlier_den >= 1 && gp->inlier_num <= gp->inlier_den &&
+         gp->thresh_px > 0.0 && gp->thresh_px < 1e150;
+}
+
+// Device scratch released at the end of a call (stream-ordered).
+struct Scratch {
+  cudaStream_t s;
+  std::vector<void*> ptrs;
+  explicit Scratch(cudaStream_t st) : s(st) {}
+  ~Scratch() {
+    for (void* p : ptrs) cudaFreeAsync(p, s);
+  }
+  template <class T>
+  int get(T*& out, uint64_t n) {
+    void* p = nullptr;
+    const int st = err_of(cudaMallocAsync(&p, std::max<uint64_t>(n, 1) * sizeof(T), s));
+    if (st != CASHASH_OK) return st;
+    ptrs.push_back(p);
+    out = static_cast<T*>(p);
+    return CASHASH_OK;
+  }
+};
+
+}  // namespace
+
+extern "C" void cashash_ga_default_params(cashash_ga_params* gp) {
+  if (!gp) return;
+  gp->top_pct = 20;
+  gp->min_matches = 16;
+  gp->n_hyp = 256;
+  gp->inlier_num = 2;
+  gp->inlier_den = 3;
+  gp->reserved = 0;
+  gp->thresh_px = 3.0;
+}
+
+extern "C" int cashash_ga_subset_offsets(const uint64_t* img_off, uint32_t n_images, uint32_t top_pct,
+                                         uint64_t* sub_off) {
+  if ((n_images > 0 && !img_off) || !sub_off || top_pct < 1 || top_pct > 100) return CASHASH_EINVAL;
+  sub_off[0] = 0;
+  for (uint32_t i = 0; i < n_images; ++i) {
+    if (img_off[i + 1] < img_off[i]) return CASHASH_EINVAL;
+    const uint64_t n = img_off[i + 1] - img_off[i];
+    sub_off[i + 1] = sub_off[i] + (n * top_pct + 99) / 100;
+  }
+  return CASHASH_OK;
+}
+
+extern "C" int cashash_ga_select(const float* scale, const uint64_t* img_off, uint32_t n_images, uint32_t top_pct,
+                                 uint32_t* sel, cashash_stream_t stream_) {
+  if ((n_images > 0 && !img_off) || top_pct < 1 || top_pct > 100) return CASHASH_EINVAL;
+  if (n_images == 0) return CASHASH_OK;
+  const uint64_t N = img_off[n_images];
+  if (N >= (1ull << 32) || (N > 0 && (!scale || !sel))) return CASHASH_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_);
+  std::vector<uint64_t> sub(n_images + 1);
+  int st = cashash_ga_subset_offsets(img_off, n_images, top_pct, sub.data());
+  if (st != CASHASH_OK) return st;
+  if (sub[n_images] == 0) return CASHASH_OK;
+  Scratch sc(s);
+  uint64_t *d_off = nullptr, *d_sub = nullptr;
+  if ((st = sc.get(d_off, n_images + 1)) != CASHASH_OK || (st = sc.get(d_sub, n_images + 1)) != CASHASH_OK) return st;
+  if ((st = err_of(cudaMemcpyAsync(d_off, img_off, (n_images + 1) * 8ull, cudaMemcpyHostToDevice, s))) != CASHASH_OK)
+    return st;
+  if ((st = err_of(cudaMemcpyAsync(d_sub, sub.data(), (n_images + 1) * 8ull, cudaMemcpyHostToDevice, s))) !=
+      CASHASH_OK)
+    return st;
+  k_ga_select<<<n_images, GA_T, 0, s>>>(scale, d_off, d_sub, sel);
+  return err_of(cudaGetLastError());
+}
+
+extern "C" int cashash_estimate_F(const float* kpts, const uint64_t* img_off, uint32_t n_images,
+                                  const uint32_t* pairs_host, uint32_t P, const uint64_t* match_off,
+                                  const uint32_t* matches, const cashash_ga_params* gp, const uint32_t* words,
+                                  double* F_out, cashash_ga_info* info_out, cashash_stream_t stream_) {
+  if (!ga_params_ok(gp) || (n_images > 0 && !img_off) || (P > 0 && (!pairs_host || !match_off || !F_out ||
+                                                                    !info_out || !words || !kpts)))
+    return CASHASH_EINVAL;
+  if (P == 0) return CASHASH_OK;
+  for (uint64_t i = 0; i < 2ull * P; ++i)
+    if (pairs_host[i] >= n_images) return CASHASH_EINVAL;
+  for (uint32_t i = 0; i < n_images; ++i)
+    if (img_off[i + 1] < img_off[i]) return CASHASH_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_);
+  uint64_t total = 0;
+  int st = err_of(cudaMemcpyAsync(&total, match_off + P, sizeof total, cudaMemcpyDeviceToHost, s));
+  if (st == CASHASH_OK) st = err_of(cudaStreamSynchronize(s));
+  if (st != CASHASH_OK) return st;
+  if (total > 0 && !matches) return CASHASH_EINVAL;
+  Scratch sc(s);
+  uint64_t* d_off = nullptr;
+  uint32_t* d_pairs = nullptr;
+  GaPt* d_pts = nullptr;
+  uint8_t* d_inl = nullptr;
+  if ((st = sc.get(d_off, n_images + 1)) != CASHASH_OK || (st = sc.get(d_pairs, 2ull * P)) != CASHASH_OK ||
+      (st = sc.get(d_pts, total)) != CASHASH_OK || (st = sc.get(d_inl, total)) != CASHASH_OK)
+    return st;
+  if ((st = err_of(cudaMemcpyAsync(d_off, img_off, (n_images + 1) * 8ull, cudaMemcpyHostToDevice, s))) != CASHASH_OK)
+    return st;
+  if ((st = err_of(cudaMemcpyAsync(d_pairs, pairs_host, 8ull * P, cudaMemcpyHostToDevice, s))) != CASHASH_OK)
+    return st;
+  GaArgs a{};
+  a.kpts = reinterpret_cast<const float2*>(kpts);
+  a.img_off = d_off;
+  a.pairs = d_pairs;
+  a.moff = match_off;
+  a.mt = matches;
+  a.words = words;
+  a.pts = d_pts;
+  a.inl = d_inl;
+  a.F = F_out;
+  a.info = reinterpret_cast<uint4*>(info_out);
+  a.P = P;
+  a.n_hyp = gp->n_hyp;
+  a.min_matches = gp->min_matches;
+  a.num = gp->inlier_num;
+  a.den = gp->inlier_den;
+  a.t2 = gp->thresh_px * gp->thresh_px;
+  k_ga_ransac<<<P, GA_T, 0, s>>>(a);
+  return err_of(cudaGetLastError());
+}
+
+extern "C" int cashash_ga_stage1(cashash_ctx* ctx, const cashash_set* set, const float* scale,
+                                 const double* mean_host, const uint32_t* pairs_host, uint32_t P,
+                                 const cashash_ga_params* gp, const uint32_t* words, double* F_out,
+                                 cashash_ga_info* info_out, cashash_stream_t stream_) {
+  cashash_params cp;
+  if (!ctx || !set || !mean_host || !ga_params_ok(gp) || cashash_get_params(ctx, &cp) != CASHASH_OK)
+    return CASHASH_EINVAL;
+  if (cp.epi_px >= 0.0) return CASHASH_EINVAL;  // stage 1 runs without a band
+  const uint32_t n_images = set->n_images;
+  if ((n_images > 0 && !set->img_off) || (set->n_features > 0 && (!set->desc || !set->kpts || !scale)))
+    return CASHASH_EINVAL;
+  if (P > 0 && (!pairs_host || !words || !F_out || !info_out)) return CASHASH_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_);
+  std::vector<uint64_t> sub(n_images + 1, 0);
+  int st = cashash_ga_subset_offsets(set->img_off, n_images, gp->top_pct, sub.data());
+  if (st != CASHASH_OK) return st;
+  const uint64_t N = sub[n_images];
+  uint64_t cap = 0;
+  for (uint32_t i = 0; i < P; ++i) {
+    if (pairs_host[2 * (size_t)i] >= n_images || pairs_host[2 * (size_t)i + 1] >= n_images) return CASHASH_EINVAL;
+    cap += sub[pairs_host[2 * (size_t)i] + 1] - sub[pairs_host[2 * (size_t)i]];
+  }
+  Scratch sc(s);
+  uint32_t *sel = nullptr, *codes = nullptr, *sq = nullptr, *mt = nullptr;
+  uint8_t *desc = nullptr, *buckets = nullptr, *tables = nullptr;
+  float* kp = nullptr;
+  uint64_t* moff = nullptr;
+  const uint64_t tb = cashash_tables_bytes(&cp, sub.data(), n_images);
+  if ((st = sc.get(sel, N)) != CASHASH_OK || (st = sc.get(desc, N * 128)) != CASHASH_OK ||
+      (st = sc.get(kp, N * 2)) != CASHASH_OK || (st = sc.get(codes, N * 4)) != CASHASH_OK ||
+      (st = sc.get(buckets, N * 8)) != CASHASH_OK || (st = sc.get(sq, N)) != CASHASH_OK ||
+      (st = sc.get(tables, tb)) != CASHASH_OK || (st = sc.get(moff, (uint64_t)P + 1)) != CASHASH_OK ||
+      (st = sc.get(mt, 2 * std::max<uint64_t>(cap, 1))) != CASHASH_OK)
+    return st;
+  if ((st = cashash_ga_select(scale, set->img_off, n_images, gp->top_pct, sel, stream_)) != CASHASH_OK) return st;
+  if (N > 0) {
+    const uint64_t work = N * 8;
+    const unsigned grid = (unsigned)std::min<uint64_t>((work + 255) / 256, 65535);
+    k_ga_gather<<<grid, 256, 0, s>>>(sel, N, set->desc, reinterpret_cast<const float2*>(set->kpts), desc,
+                                     reinterpret_cast<float2*>(kp));
+    if ((st = err_of(cudaGetLastError())) != CASHASH_OK) return st;
+  }
+  cashash_set S{};
+  S.n_images = n_images;
+  S.n_features = N;
+  S.img_off = sub.data();
+  S.desc = desc;
+  S.codes = codes;
+  S.buckets = buckets;
+  S.sqnorm = sq;
+  S.tables = tables;
+  S.kpts = kp;
+  if ((st = cashash_build_codes(ctx, &S, mean_host, stream_)) != CASHASH_OK) return st;
+  if (P == 0) return err_of(cudaStreamSynchronize(s));
+  cashash_plan* pl = nullptr;
+  if ((st = cashash_plan_create(ctx, &S, pairs_host, P, &pl)) != CASHASH_OK) return st;
+  st = cashash_match_plan(ctx, pl, nullptr, moff, mt, cap, stream_);
+  if (st == CASHASH_OK) st = cashash_sync_status(ctx, stream_);
+  cashash_plan_destroy(pl);
+  if (st != CASHASH_OK) return st;
+  return cashash_estimate_F(kp, sub.data(), n_images, pairs_host, P, moff, mt, gp, words, F_out, info_out, stream_);
+}

@@ -25,7 +25,7 @@ def lib():
 def declared_functions():
     txt = open(HEADER).read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    names = re.findall(r"\b(cashash_[a-z_]+)\s*\(", txt)
+    names = re.findall(r"\b(cashash_\w+)\s*\(", txt)
     return sorted(set(names))
 
 
@@ -141,6 +141,43 @@ def test_chunked_matching_rejects_bad_arguments_on_the_host(lib):
     assert call(0, 0, fn) == ch.CASHASH_EINVAL            # empty chunks
     assert call(0, 1, ch.CHUNK_FN()) == ch.CASHASH_EINVAL  # no callback
     assert call(0, 1, fn, np.array([[0, 2]], np.uint32)) == ch.CASHASH_EINVAL  # image out of range
+
+
+def test_ga_calls_check_arguments_on_the_host(lib):
+    """The Ga-CasHash first-stage calls: defaults, subset sizes (pure host
+    arithmetic) and argument checks that precede any CUDA call."""
+    import ctypes as C
+    import paper_1805_08995_gb300 as ch
+    L = ch._load()
+    g = ch.cashash_ga_default_params()
+    assert (g.top_pct, g.min_matches, g.n_hyp, g.inlier_num, g.inlier_den, g.thresh_px) == (20, 16, 256, 2, 3, 3.0)
+    assert ch.cashash_ga_subset_offsets(np.array([0, 0, 1, 5, 105, 1105], np.uint64), 20).tolist() == \
+        [0, 0, 1, 2, 22, 222]
+    assert ch.cashash_ga_subset_offsets(np.array([0, 7], np.uint64), 100).tolist() == [0, 7]
+    off = np.array([0, 3, 5], np.uint64)
+    sub = np.zeros(3, np.uint64)
+    hp = lambda a: a.ctypes.data_as(C.c_void_p)
+    assert L.cashash_ga_subset_offsets(hp(off), 2, 0, hp(sub)) == ch.CASHASH_EINVAL
+    assert L.cashash_ga_subset_offsets(hp(off), 2, 101, hp(sub)) == ch.CASHASH_EINVAL
+    assert L.cashash_ga_subset_offsets(hp(np.array([0, 3, 2], np.uint64)), 2, 20, hp(sub)) == ch.CASHASH_EINVAL
+    assert L.cashash_ga_select(None, hp(off), 2, 0, None, None) == ch.CASHASH_EINVAL
+    assert L.cashash_ga_select(None, hp(off), 2, 20, None, None) == ch.CASHASH_EINVAL  # no scale / output
+    assert L.cashash_ga_select(None, None, 0, 20, None, None) == ch.CASHASH_OK      # nothing to do
+    pairs = np.array([[0, 1]], np.uint32)
+    dummy = C.c_void_p(16)  # never dereferenced: every case fails its checks first
+    for bad in (dict(n_hyp=0), dict(min_matches=3), dict(inlier_num=5, inlier_den=4), dict(thresh_px=-1.0)):
+        gp = ch.cashash_ga_default_params(**bad)
+        assert L.cashash_estimate_F(dummy, hp(off), 2, hp(pairs), 1, dummy, dummy, C.byref(gp), dummy, dummy,
+                                    dummy, None) == ch.CASHASH_EINVAL
+    gp = ch.cashash_ga_default_params()
+    assert L.cashash_estimate_F(dummy, hp(off), 2, hp(np.array([[0, 2]], np.uint32)), 1, dummy, dummy,
+                                C.byref(gp), dummy, dummy, dummy, None) == ch.CASHASH_EINVAL
+    assert L.cashash_estimate_F(None, None, 0, None, 0, None, None, C.byref(gp), None, None, None, None) == \
+        ch.CASHASH_OK
+    p = ch.cashash_params()
+    assert L.cashash_get_params(None, C.byref(p)) == ch.CASHASH_EINVAL
+    assert L.cashash_ga_stage1(None, None, None, None, None, 0, C.byref(gp), None, None, None, None) == \
+        ch.CASHASH_EINVAL
 
 
 def test_package_fails_loudly_without_library(tmp_path):

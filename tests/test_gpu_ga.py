@@ -1,0 +1,167 @@
+"""GPU parity of the Ga-CasHash first stage (Sec. 5.1) against the oracle.
+
+Selection by scale and every integer decision (stage-1 match counts, inlier
+counts, the winning hypothesis, acceptance) must be identical.  F is compared
+as a unit-norm matrix within 1e-8 (max-abs): both sides solve the same FP64
+problems with different algorithms (GPU: elimination with partial pivoting,
+one-sided / cyclic Jacobi on the normal matrix; oracle: LAPACK SVD), whose
+results differ by a few units of rounding amplified by the conditioning of
+the normalised design matrix.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+F_TOL = 1e-8
+
+
+@pytest.fixture(scope="module")
+def ch():
+    import paper_1805_08995_gb300 as m
+    torch.cuda.set_device(0)
+    return m
+
+
+@pytest.fixture(scope="module")
+def oga():
+    import oracle
+    oracle.build()
+    from oracle import ga
+    return ga
+
+
+def _gp(ch, oga, **kw):
+    return ch.cashash_ga_default_params(**kw), oga.GaParams(**kw)
+
+
+def _check(F_gpu, info_gpu, F_orc, info_orc):
+    info = info_gpu.cpu().numpy().view(np.uint32)
+    assert np.array_equal(info, info_orc)
+    Fg = F_gpu.cpu().numpy()
+    worst = float(np.abs(Fg - F_orc).max()) if len(Fg) else 0.0
+    assert worst <= F_TOL, worst
+    return worst
+
+
+@pytest.mark.parametrize("pct", [1, 20, 100])
+def test_select_parity(ch, oga, pct):
+    rng = np.random.default_rng(pct)
+    sizes = [0, 1, 5, 700, 3000, 20011]
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint64)
+    n = int(off[-1])
+    scale = (np.round(rng.uniform(0, 8, n) * 4) / 4).astype(np.float32)  # many ties
+    scale[::97] = -0.0
+    scale[5::211] = 0.0
+    sel, sub = ch.cashash_ga_select(torch.from_numpy(scale).cuda(), off, pct)
+    esel, esub = oga.top_scale(scale, off, pct)
+    assert np.array_equal(sub, esub)
+    assert np.array_equal(sel.cpu().numpy().view(np.uint32).astype(np.uint64), esel)
+
+
+def _epi_set(n_points=60000, n_views=6, seed=43):
+    return synth.epipolar_set(seed, n_views=n_views, n_points=n_points, arc=2 * math.pi * n_views / 250,
+                              z_max=0.355)
+
+
+def _stage1_both(ch, oga, s, pairs, gp, ogp, seed=5):
+    import oracle as orc
+    po = orc.params()
+    p = ch.cashash_default_params()
+    ctx = ch.cashash_create(p, s.R)
+    ds = ch.DeviceSet(p, s.img_off, s.desc, s.kpts)
+    ch.cashash_build_codes(ctx, ds)
+    mu = ch.cashash_get_mean(ctx)
+    emu = orc.mean(s.desc)
+    assert np.array_equal(mu, emu)
+    words = synth.ransac_words(seed, len(pairs), gp.n_hyp)
+    F, info = ch.cashash_ga_stage1(ctx, ds, torch.from_numpy(s.scale).cuda(), mu, pairs,
+                                   torch.from_numpy(words.view(np.int32)).cuda(), gp)
+    torch.cuda.synchronize()
+    eF, einfo, *_ = oga.stage1(s.desc, s.img_off, s.kpts, s.scale, emu, s.R, pairs, po, ogp, words)
+    ctx.close()
+    return F, info, eF, einfo
+
+
+def test_stage1_parity(ch, oga):
+    s = _epi_set()
+    pairs = np.concatenate([s.pairs, s.pairs[:4, ::-1]]).astype(np.uint32)
+    gp, ogp = _gp(ch, oga)
+    F, info, eF, einfo = _stage1_both(ch, oga, s, pairs, gp, ogp)
+    assert einfo[:, 3].sum() >= len(pairs) - 2  # the workload really exercises the estimate
+    _check(F, info, eF, einfo)
+
+
+def test_stage1_rejections_and_small_pairs(ch, oga):
+    """Small views (few stage-1 matches: no F) and a view whose key-points are
+    scrambled (matches without a common geometry: rejected)."""
+    s = _epi_set(n_points=9000, n_views=4, seed=44)
+    big = _epi_set(n_points=40000, n_views=4, seed=45)
+    # scramble the key-points of view 2 of the big set
+    kp = big.kpts.copy()
+    a, b = int(big.img_off[2]), int(big.img_off[3])
+    kp[a:b] = kp[a:b][np.random.default_rng(1).permutation(b - a)]
+    big.kpts = kp
+    gp, ogp = _gp(ch, oga, n_hyp=64)
+    for st in (s, big):
+        F, info, eF, einfo = _stage1_both(ch, oga, st, st.pairs.astype(np.uint32), gp, ogp, seed=7)
+        _check(F, info, eF, einfo)
+        if st is s:
+            assert (einfo[:, 0] < 16).any() and (einfo[:, 2] == oga.NONE).any()
+        else:
+            rej = [i for i, (u, v) in enumerate(st.pairs) if 2 in (u, v)]
+            assert rej and all(einfo[i, 3] == 0 and einfo[i, 0] >= 16 for i in rej)
+
+
+@pytest.mark.parametrize("case", ["one_hypothesis", "thresholds"])
+def test_estimate_F_parity(ch, oga, case):
+    """cashash_estimate_F on the oracle's own stage-1 match lists."""
+    import oracle as orc
+    s = _epi_set(n_points=30000, n_views=5, seed=46)
+    pairs = s.pairs.astype(np.uint32)
+    kw = dict(n_hyp=1) if case == "one_hypothesis" else dict(thresh_px=0.75, inlier_num=9, inlier_den=10,
+                                                              min_matches=40, n_hyp=100)
+    gp, ogp = _gp(ch, oga, **kw)
+    po = orc.params()
+    mu = orc.mean(s.desc)
+    words = synth.ransac_words(9, len(pairs), gp.n_hyp)
+    eF, einfo, sel, sub, (moff, mt) = oga.stage1(s.desc, s.img_off, s.kpts, s.scale, mu, s.R, pairs, po, ogp,
+                                                words)
+    ksub = torch.from_numpy(np.ascontiguousarray(s.kpts[sel.astype(np.int64)])).cuda()
+    F, info = ch.cashash_estimate_F(ksub, sub, pairs, torch.from_numpy(moff.astype(np.int64)).cuda(),
+                                    torch.from_numpy(np.ascontiguousarray(mt).view(np.int32)).cuda(),
+                                    torch.from_numpy(words.view(np.int32)).cuda(), gp)
+    torch.cuda.synchronize()
+    _check(F, info, eF, einfo)
+    if case == "thresholds":
+        assert (einfo[:, 3] == 0).any() or (einfo[:, 0] < 40).any()
+
+
+def test_stage1_no_pairs_and_bad_args(ch, oga):
+    s = _epi_set(n_points=9000, n_views=3, seed=47)
+    p = ch.cashash_default_params()
+    ctx = ch.cashash_create(p, s.R)
+    ds = ch.DeviceSet(p, s.img_off, s.desc, s.kpts)
+    ch.cashash_build_codes(ctx, ds)
+    mu = ch.cashash_get_mean(ctx)
+    sc = torch.from_numpy(s.scale).cuda()
+    w = torch.zeros((1, 256, 8), dtype=torch.int32, device="cuda")
+    F, info = ch.cashash_ga_stage1(ctx, ds, sc, mu, np.zeros((0, 2), np.uint32), w)
+    assert F.shape == (0, 9) and info.shape == (0, 4)
+    for bad in (dict(n_hyp=0), dict(n_hyp=ch.GA_MAX_HYP + 1), dict(min_matches=7), dict(top_pct=0),
+                dict(inlier_num=4, inlier_den=3), dict(thresh_px=0.0)):
+        with pytest.raises(ch.CashashError) as e:
+            ch.cashash_ga_stage1(ctx, ds, sc, mu, s.pairs[:1], w, ch.cashash_ga_default_params(**bad))
+        assert e.value.status == ch.CASHASH_EINVAL
+    ctx.close()
+    pb = ch.cashash_default_params(epi_px=4.0)  # stage 1 runs without the band
+    ctx = ch.cashash_create(pb, s.R)
+    ds = ch.DeviceSet(pb, s.img_off, s.desc, s.kpts)
+    with pytest.raises(ch.CashashError):
+        ch.cashash_ga_stage1(ctx, ds, sc, mu, s.pairs[:1], w)
+    ctx.close()
