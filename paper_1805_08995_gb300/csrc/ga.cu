@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(GA_T) k_ga_select(const float* __restrict__ sc
     const bool take = gt || (eq && eq_before + eq_rank < need);
     uint32_t tk_tot;
     const uint32_t pos = cta_scan(take, s_w, tk_tot);
-    if (take) out[out_before + pos] = (uint32_t)(a + j);
+    if (take && out_before + pos < k) out[out_before + pos] = (uint32_t)(a + j);
     eq_before += eq_tot;
     out_before += tk_tot;
   }
@@ -168,7 +168,7 @@ __device__ double block_sum(double v, double* s_d) {
 }
 
 // Squared Sampson distance <= t2 (x_B^T F x_A = 0).
-__device__ __forceinline__ bool ga_inlier(const double* F, const GaPt p, double t2) {
+__host__ __device__ __forceinline__ bool ga_inlier(const double* F, const GaPt p, double t2) {
   const double fx0 = F[0] * p.x + F[1] * p.y + F[2];
   const double fx1 = F[3] * p.x + F[4] * p.y + F[5];
   const double fx2 = F[6] * p.x + F[7] * p.y + F[8];
@@ -181,7 +181,7 @@ __device__ __forceinline__ bool ga_inlier(const double* F, const GaPt p, double 
 
 // One-sided Jacobi SVD of a 3 x 3 (columns orthogonalised); returns the right
 // singular vector of the smallest singular value in v.
-__device__ void smallest_right_sv3(const double* Fm, double* v) {
+__host__ __device__ void smallest_right_sv3(const double* Fm, double* v) {
   double U[9], V[9];
   for (int e = 0; e < 9; ++e) {
     U[e] = Fm[e];
@@ -226,7 +226,7 @@ __device__ void smallest_right_sv3(const double* Fm, double* v) {
 }
 
 // F := F - (F v)(v^T) for the smallest right singular vector v (closest rank 2).
-__device__ void rank2(double* Fm) {
+__host__ __device__ void rank2(double* Fm) {
   double v[3];
   smallest_right_sv3(Fm, v);
   for (int r = 0; r < 3; ++r) {
@@ -236,7 +236,7 @@ __device__ void rank2(double* Fm) {
 }
 
 // F = Tb^T Fn Ta for T = [[s, 0, -s cx], [0, s, -s cy], [0, 0, 1]].
-__device__ void denormalise(const double* Fn, const double* Ta, const double* Tb, double* F) {
+__host__ __device__ void denormalise(const double* Fn, const double* Ta, const double* Tb, double* F) {
   double G[9];  // Fn Ta
   for (int r = 0; r < 3; ++r) {
     G[3 * r + 0] = Fn[3 * r] * Ta[0];
@@ -251,7 +251,7 @@ __device__ void denormalise(const double* Fn, const double* Ta, const double* Tb
 }
 
 // The design row of x_B^T F x_A = 0 (f = F row-major) in normalised coordinates.
-__device__ __forceinline__ void design_row(const GaPt p, const double* Ta, const double* Tb, double* row) {
+__host__ __device__ __forceinline__ void design_row(const GaPt p, const double* Ta, const double* Tb, double* row) {
   const double xa = Ta[0] * p.x + Ta[1], ya = Ta[0] * p.y + Ta[2];
   const double xb = Tb[0] * p.z + Tb[1], yb = Tb[0] * p.w + Tb[2];
   row[0] = xb * xa;
@@ -268,7 +268,7 @@ __device__ __forceinline__ void design_row(const GaPt p, const double* Ta, const
 // Hypothesis h of the pair: 8 distinct matches from the words, the null vector
 // of the 8 x 9 system (partial pivoting, f_8 = 1), rank 2, denormalised.
 // false when the sample is degenerate or the result is not finite.
-__device__ bool hypothesis(const GaPt* pts, uint32_t m, const uint32_t* w, const double* Ta, const double* Tb,
+__host__ __device__ bool hypothesis(const GaPt* pts, uint32_t m, const uint32_t* w, const double* Ta, const double* Tb,
                            double* F) {
   uint32_t idx[8];
   for (int k = 0; k < 8; ++k) {
@@ -322,9 +322,10 @@ __device__ bool hypothesis(const GaPt* pts, uint32_t m, const uint32_t* w, const
   return true;
 }
 
-// Eigenvector of the smallest eigenvalue of a symmetric 9 x 9 (cyclic Jacobi).
-__device__ void smallest_eigvec9(double* M, double* v) {
-  double V[81];
+// Eigenvector of the smallest eigenvalue of a symmetric 9 x 9 (cyclic Jacobi);
+// M is overwritten, V [81] is workspace.  Both live in shared memory in the
+// kernel (a local V was placed over the caller's local M in the stack frame).
+__host__ __device__ void smallest_eigvec9(double* M, double* V, double* v) {
   for (int e = 0; e < 81; ++e) V[e] = (e % 10 == 0) ? 1.0 : 0.0;
   for (int sweep = 0; sweep < 30; ++sweep) {
     double off = 0.0, tot = 0.0;
@@ -367,7 +368,7 @@ __device__ void smallest_eigvec9(double* M, double* v) {
 __global__ void __launch_bounds__(GA_T) k_ga_ransac(GaArgs a) {
   __shared__ double s_d[GA_T / 32];
   __shared__ uint32_t s_best[GA_T / 32][2];
-  __shared__ double s_F[9], s_M[45];
+  __shared__ double s_F[9], s_M[45], s_Mf[81], s_V[81];
   __shared__ uint32_t s_bh;
   const uint32_t p = blockIdx.x, tid = threadIdx.x;
   const uint64_t m0 = a.moff[p];
@@ -378,12 +379,17 @@ __global__ void __launch_bounds__(GA_T) k_ga_ransac(GaArgs a) {
     if (tid == 0) a.info[p] = make_uint4(m, 0u, GA_NONE, 0u);
     return;
   }
-  const uint64_t A0 = a.img_off[a.pairs[2 * p]], B0 = a.img_off[a.pairs[2 * p + 1]];
+  const uint32_t ia = a.pairs[2 * p], ib = a.pairs[2 * p + 1];
+  const uint64_t A0 = a.img_off[ia], B0 = a.img_off[ib];
+  const uint32_t nA = (uint32_t)(a.img_off[ia + 1] - A0), nB = (uint32_t)(a.img_off[ib + 1] - B0);
   GaPt* pts = a.pts + m0;
   uint8_t* inl = a.inl + m0;
   double sxa = 0.0, sya = 0.0, sxb = 0.0, syb = 0.0;
   for (uint32_t i = tid; i < m; i += GA_T) {
-    const float2 pa = a.kpts[A0 + a.mt[2 * (m0 + i)]], pb = a.kpts[B0 + a.mt[2 * (m0 + i) + 1]];
+    const uint32_t qa = a.mt[2 * (m0 + i)], jb = a.mt[2 * (m0 + i) + 1];
+    // indices outside the images (never written by the matcher) read as (0, 0)
+    const float2 pa = qa < nA ? a.kpts[A0 + qa] : make_float2(0.f, 0.f);
+    const float2 pb = jb < nB ? a.kpts[B0 + jb] : make_float2(0.f, 0.f);
     const GaPt q = {(double)pa.x, (double)pa.y, (double)pb.x, (double)pb.y};
     pts[i] = q;
     sxa += q.x;
@@ -480,10 +486,10 @@ __global__ void __launch_bounds__(GA_T) k_ga_ransac(GaArgs a) {
     }
     __syncthreads();
     if (tid == 0) {
-      double M[81], f[9];
+      double f[9];
       for (uint32_t r = 0, e = 0; r < 9; ++r)
-        for (uint32_t c = r; c < 9; ++c, ++e) M[9 * r + c] = M[9 * c + r] = s_M[e];
-      smallest_eigvec9(M, f);
+        for (uint32_t c = r; c < 9; ++c, ++e) s_Mf[9 * r + c] = s_Mf[9 * c + r] = s_M[e];
+      smallest_eigvec9(s_Mf, s_V, f);
       rank2(f);
       denormalise(f, Ta, Tb, s_F);
     }

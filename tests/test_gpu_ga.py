@@ -107,12 +107,13 @@ def test_stage1_rejections_and_small_pairs(ch, oga):
     a, b = int(big.img_off[2]), int(big.img_off[3])
     kp[a:b] = kp[a:b][np.random.default_rng(1).permutation(b - a)]
     big.kpts = kp
-    gp, ogp = _gp(ch, oga, n_hyp=64)
     for st in (s, big):
+        # the small views give 17..28 stage-1 matches: min_matches 20 leaves some pairs without F
+        gp, ogp = _gp(ch, oga, n_hyp=64, min_matches=20 if st is s else 16)
         F, info, eF, einfo = _stage1_both(ch, oga, st, st.pairs.astype(np.uint32), gp, ogp, seed=7)
         _check(F, info, eF, einfo)
         if st is s:
-            assert (einfo[:, 0] < 16).any() and (einfo[:, 2] == oga.NONE).any()
+            assert (einfo[:, 0] < 20).any() and (einfo[:, 2] == oga.NONE).any() and (einfo[:, 3] == 1).any()
         else:
             rej = [i for i, (u, v) in enumerate(st.pairs) if 2 in (u, v)]
             assert rej and all(einfo[i, 3] == 0 and einfo[i, 0] >= 16 for i in rej)
