@@ -469,6 +469,200 @@ def run_ours(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# Ga-CasHash: first stage (top-scale subsets, CasHash, RANSAC F) + guided matching
+# ---------------------------------------------------------------------------
+
+def oracle_ga_sample(s, n_pairs: int, gp, words, seed: int = 0):
+    """Times the oracle's two stages on a bounded sample of pairs (all host
+    cores for codes and matching; the RANSAC loop is numpy) and extrapolates:
+    codes by feature count, matching by N_A * N_B, RANSAC by pairs.  Returns
+    (pairs/s, cores, sample text, seconds)."""
+    import oracle as orc
+    from oracle import ga as oga
+    cores = os.cpu_count() or 1
+    rng = np.random.default_rng(seed)
+    P = len(s.pairs)
+    pick = np.sort(rng.choice(P, size=min(n_pairs, P), replace=False))
+    sp = s.pairs[pick]
+    imgs = np.unique(sp)
+    sizes = s.sizes()
+    remap = {int(i): k for k, i in enumerate(imgs)}
+    sp2 = np.array([[remap[int(a)], remap[int(b)]] for a, b in sp], np.uint32)
+    t0 = time.perf_counter()
+    mu = orc.mean(s.desc)
+    t_mean = time.perf_counter() - t0
+    rows = np.concatenate([np.arange(int(s.img_off[i]), int(s.img_off[i + 1])) for i in imgs])
+    off = np.zeros(len(imgs) + 1, np.uint64)
+    off[1:] = np.cumsum(sizes[imgs])
+    desc, kpts, scale = s.desc[rows], s.kpts[rows], s.scale[rows]
+    po1, po2 = orc.params(), orc.params(epi_px=4.0)
+    t0 = time.perf_counter()
+    sel, sub = oga.top_scale(scale, off, gp.top_pct)
+    d1 = np.ascontiguousarray(desc[sel.astype(np.int64)])
+    c1, b1 = oracle_codes_parallel(orc, d1, s.R, po1, mu, cores)
+    t_codes1 = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    moff, mt = orc.match_pairs(d1, sub, c1, b1, sp2, po1, n_threads=cores)
+    t_match1 = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    k1 = kpts[sel.astype(np.int64)]
+    F = np.zeros((len(sp2), 9))
+    acc = np.zeros(len(sp2), bool)
+    for i, (a, b) in enumerate(sp2):
+        lo, hi = int(moff[i]), int(moff[i + 1])
+        q = mt[lo:hi, 0].astype(np.int64) + int(sub[a])
+        j = mt[lo:hi, 1].astype(np.int64) + int(sub[b])
+        Fi, info = oga.estimate_F(k1[q], k1[j], words[pick[i]], gp)
+        F[i], acc[i] = Fi.ravel(), bool(info[3])
+    t_ransac = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    c2, b2 = oracle_codes_parallel(orc, desc, s.R, po2, mu, cores)
+    t_codes2 = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    if acc.any():
+        orc.match_pairs(desc, off, c2, b2, sp2[acc], po2, n_threads=cores, F=F[acc], kpts=kpts)
+    t_match2 = time.perf_counter() - t0
+    n_all, n_smp = float(sizes.sum()), float(len(rows))
+    w_all = float((sizes[s.pairs[:, 0]] * sizes[s.pairs[:, 1]]).sum())
+    w_smp = float((sizes[sp[:, 0]] * sizes[sp[:, 1]]).sum())
+    job = (t_mean + (t_codes1 + t_codes2) * n_all / n_smp + (t_match1 + t_match2) * w_all / w_smp +
+           t_ransac * P / len(sp))
+    text = ("oracle (C codes and matching on %d threads, numpy RANSAC): %d of %d pairs through both stages "
+            "(%d accepted); extrapolated by features, N_A*N_B and pair count" % (cores, len(sp), P, int(acc.sum())))
+    return P / job, cores, text, t_mean + t_codes1 + t_match1 + t_ransac + t_codes2 + t_match2
+
+
+def run_ga(args):
+    """One step = full-set codes (stage-2 context), the first stage on the
+    top-20 % subsets (selection, codes with the full set's centre, CasHash,
+    RANSAC F per pair), then guided matching (band 4 px with the estimated F)
+    of the accepted pairs; host work between the stages (reading which pairs
+    were accepted, the stage-2 plan) is inside the timed step."""
+    import torch
+    import paper_1805_08995_gb300 as ch
+    from paper_1805_08995_gb300 import build as chbuild
+    import synth
+    if int(os.environ.get("WORLD_SIZE", "1")) != 1 or args.gpus != 1:
+        raise SystemExit("--ga runs on one GPU")
+    torch.cuda.set_device(0)
+    chbuild.build()
+    ch._load()
+    s, wdesc = workload("config4", 0)
+    P = len(s.pairs)
+    bf = dict(precision=ch.CASHASH_BF16, schedule=ch.CASHASH_SCHED_PERSISTENT)
+    p1 = ch.cashash_default_params(**bf)
+    p2 = ch.cashash_default_params(epi_px=4.0, **bf)
+    ctx1, ctx2 = ch.cashash_create(p1, s.R), ch.cashash_create(p2, s.R)
+    ds = ch.DeviceSet(p2, s.img_off, s.desc, s.kpts)
+    dev = torch.device("cuda", 0)
+    scale = torch.from_numpy(s.scale).to(dev)
+    gp = ch.cashash_ga_default_params(kernel={"auto": 0, "join": 1, "query": 2}[args.ga_kernel])
+    words_h = synth.ransac_words(4, P, gp.n_hyp)
+    words = torch.from_numpy(words_h.view(np.int32)).to(dev)
+    cap = int(s.sizes()[s.pairs[:, 0]].sum())
+    moff = torch.zeros(P + 1, dtype=torch.int64, device=dev)
+    mt = torch.zeros((max(cap, 1), 2), dtype=torch.int32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    out = {}
+
+    def step(profile=False):
+        t0 = time.perf_counter()
+        ch.cashash_build_codes(ctx2, ds)
+        mu = ch.cashash_get_mean(ctx2)
+        F, info = ch.cashash_ga_stage1(ctx1, ds, scale, mu, s.pairs, words, gp)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        acc = torch.nonzero(info[:, 3]).squeeze(1)
+        acc_h = acc.cpu().numpy()
+        pairs2 = s.pairs[acc_h]
+        F2 = F.index_select(0, acc).contiguous()
+        cap2 = int(s.sizes()[pairs2[:, 0]].sum()) if len(pairs2) else 0
+        plan = ch.cashash_plan_create(ctx2, ds, pairs2)
+        ch.cashash_match_plan(ctx2, plan, moff, mt, max(cap2, 1), F=F2)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        out.update(F=F, info=info, acc=acc_h, pairs2=pairs2, matches=int(moff[len(pairs2)].item()))
+        if profile:
+            out["stats"] = ch.cashash_get_stats(ctx2)
+        plan.close()
+        return t1 - t0, t2 - t1
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    if ch.cashash_sync_status(ctx2) != ch.CASHASH_OK or ch.cashash_sync_status(ctx1) != ch.CASHASH_OK:
+        raise SystemExit("device status not OK after warm-up")
+    ch.cashash_set_profiling(ctx2, True)
+    sampler = ClockSampler(0)
+    sampler.start()
+    time.sleep(0.3)
+    ts1, ts2 = [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        a, b = step(profile=True)
+        ts1.append(a)
+        ts2.append(b)
+    clocks = sampler.stop()
+    t_step = statistics.mean(ts1) + statistics.mean(ts2)
+    info = out["info"].cpu().numpy().view(np.uint32)
+    Fe = out["F"].cpu().numpy()
+    acc = out["acc"]
+    # quality: |<F_est, F_gt>| of unit-norm matrices over the accepted pairs, and the guided matches
+    # with the estimated F against those with the ground-truth F (same pairs, outside the timed steps)
+    cosang = np.abs(np.sum(Fe[acc] * s.F[acc], axis=1)) if len(acc) else np.zeros(0)
+    plan = ch.cashash_plan_create(ctx2, ds, out["pairs2"])
+    mo2 = torch.zeros(len(acc) + 1, dtype=torch.int64, device=dev)
+    mt2 = torch.zeros_like(mt)
+    ch.cashash_match_plan(ctx2, plan, mo2, mt2, mt.shape[0], F=torch.from_numpy(np.ascontiguousarray(s.F[acc])).to(dev))
+    torch.cuda.synchronize()
+    n_gt = int(mo2[-1].item())
+    same = 0
+    if out["matches"] and n_gt:
+        def keys(m_dev, off_dev, n):  # (pair, q, j) as one int64, q and j < 2^24
+            mm = m_dev[:n].cpu().numpy().view(np.uint32).astype(np.int64)
+            pi = np.repeat(np.arange(len(acc), dtype=np.int64), np.diff(off_dev[:len(acc) + 1].cpu().numpy()))
+            return (pi << 48) | (mm[:, 0] << 24) | mm[:, 1]
+        same = int(len(np.intersect1d(keys(mt, moff, out["matches"]), keys(mt2, mo2, n_gt))))
+    plan.close()
+    st = out["stats"]["ms_stage"]
+    cpu = None
+    if not args.no_cpu_baseline:
+        v, cores, text, secs = oracle_ga_sample(s, max(16, args.ref_pairs // 8), oga_params(gp), words_h)
+        cpu = {"value": v, "unit": "pairs/s", "cores": cores, "kind": "oracle", "sample": text, "seconds": secs}
+    line = {"metric": METRIC, "value": P / t_step, "unit": "pairs/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u8/bf16+f64fix, f64 geometry", "data": "synthetic",
+            "config": {"workload": wdesc.replace("ground-truth F", "F estimated by the first stage (Ga-CasHash)"),
+                       "pairs": P, "features": int(s.desc.shape[0]),
+                       "ga": {"stage1_kernel": args.ga_kernel, "top_pct": gp.top_pct, "min_matches": gp.min_matches, "n_hyp": gp.n_hyp,
+                              "accept": "%d/%d inliers" % (gp.inlier_num, gp.inlier_den),
+                              "thresh_px": gp.thresh_px},
+                       "l2": "flushed: 256 MiB write before every step"},
+            "stages_ms": {"stage1": statistics.mean(ts1) * 1e3, "stage2": statistics.mean(ts2) * 1e3,
+                          "stage2_match_kernel": st["match"], "stage2_fallback": st["fallback"]},
+            "ga": {"pairs_with_F": int((info[:, 2] != 0xFFFFFFFF).sum()), "accepted": int(len(acc)),
+                   "stage1_matches_median": float(np.median(info[:, 0])),
+                   "inlier_ratio_median": float(np.median(info[acc, 1] / np.maximum(info[acc, 0], 1)))
+                   if len(acc) else None,
+                   "cos_F_est_gt_median": float(np.median(cosang)) if len(cosang) else None,
+                   "cos_F_est_gt_min": float(cosang.min()) if len(cosang) else None,
+                   "guided_matches": out["matches"], "guided_matches_with_gt_F": n_gt,
+                   "common_with_gt_F": same},
+            "roofline": None, "cpu_baseline": cpu, "e2e": None, "clocks": clocks}
+    print(json.dumps(line))
+    ctx1.close()
+    ctx2.close()
+    return 0
+
+
+def oga_params(gp):
+    from oracle import ga as oga
+    return oga.GaParams(top_pct=gp.top_pct, min_matches=gp.min_matches, n_hyp=gp.n_hyp, inlier_num=gp.inlier_num,
+                        inlier_den=gp.inlier_den, thresh_px=gp.thresh_px)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -489,11 +683,17 @@ def main():
     ap.add_argument("--accept-single", action="store_true", help="a single ranked candidate matches")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ga", action="store_true",
+                    help="Ga-CasHash on config 4: F estimated by the first stage, then guided matching")
+    ap.add_argument("--ga-kernel", default="auto", choices=["auto", "join", "query"],
+                    help="matching kernel of the first stage's subsets")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.ga:
+        return run_ga(args)
     return run_ours(args)
 
 

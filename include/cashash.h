@@ -371,7 +371,9 @@ typedef struct {
   uint32_t n_hyp;        /* 256: RANSAC hypotheses per pair (1..CASHASH_GA_MAX_HYP) */
   uint32_t inlier_num;   /* 2 */
   uint32_t inlier_den;   /* 3: accepted when inlier_den * inliers >= inlier_num * matches */
-  uint32_t reserved;
+  uint32_t kernel;       /* 0: matching kernel of the subsets chosen by their size (the per-query
+                            kernel when the mean subset image has fewer than 4096 features, else
+                            the join); CASHASH_KERNEL_JOIN / CASHASH_KERNEL_QUERY force one */
   double thresh_px;      /* 3.0: inlier when the Sampson distance is <= thresh_px pixels */
 } cashash_ga_params;
 

@@ -63,7 +63,7 @@ class cashash_tuning(C.Structure):
 
 class cashash_ga_params(C.Structure):
     _fields_ = [("top_pct", C.c_uint32), ("min_matches", C.c_uint32), ("n_hyp", C.c_uint32),
-                ("inlier_num", C.c_uint32), ("inlier_den", C.c_uint32), ("reserved", C.c_uint32),
+                ("inlier_num", C.c_uint32), ("inlier_den", C.c_uint32), ("kernel", C.c_uint32),
                 ("thresh_px", C.c_double)]
 
 

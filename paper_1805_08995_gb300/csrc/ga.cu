@@ -21,7 +21,10 @@
 //                 hypothesis per thread (8 x 9 elimination with partial
 //                 pivoting for the null vector, rank 2 by a one-sided Jacobi
 //                 SVD of the 3 x 3, inlier count), block argmax, refit from
-//                 the 9 x 9 normal matrix (cyclic Jacobi), final count.
+//                 the 9 x 9 normal matrix (cyclic Jacobi), final count.  The
+//                 inlier test runs in FP32 with a rounding bound and falls
+//                 back to FP64 only near the threshold, so every decision is
+//                 the FP64 one.
 #include <algorithm>
 #include <vector>
 
@@ -148,11 +151,12 @@ struct GaArgs {
   const uint32_t* mt;      // [.][2] (q, j) local
   const uint32_t* words;   // [P][n_hyp][8]
   GaPt* pts;            // [total matches] scratch: (xa, ya, xb, yb)
+  float4* pts32;        // the same in FP32 (exact: key-points are FP32)
   uint8_t* inl;            // [total matches] scratch
   double* F;               // [P][9] out
   uint4* info;             // [P] out
   uint32_t P, n_hyp, min_matches, num, den;
-  double t2;
+  double t2, thresh;
 };
 
 __device__ double block_sum(double v, double* s_d) {
@@ -177,6 +181,56 @@ __host__ __device__ __forceinline__ bool ga_inlier(const double* F, const GaPt p
   const double r = p.z * fx0 + p.w * fx1 + fx2;
   const double e = (r * r) / (fx0 * fx0 + fx1 * fx1 + ft0 * ft0 + ft1 * ft1);
   return e <= t2;
+}
+
+// The same decision from an FP32 evaluation with a rounding bound; returns 1
+// (inlier) or 0 (outlier) when the bound decides, else the FP64 test.  With
+// u = 2^-24, F' = fl32(F), a = (xa, ya, 1), b = (xb, yb, 1), the FP32 values
+// (nested fmaf) satisfy |r32 - r| <= 6u sum_ij |b_i||F_ij||a_j| for r =
+// b^T F a, and each of F a and F^T b (first two rows) is off by at most
+// 3.1u sum |F||a| (resp. |F^T||b|) per component, so the norm g of the
+// Sampson denominator is off by at most 3.1u (S0 + S1 + T0 + T1) plus 3u g
+// for its own evaluation.  The test |r| <= t g (e = r^2 / g^2 <= t^2) is
+// decided when |r32| +- Er clears t (g32 -+ Eg) with margins 8u / 4u.
+struct GaF32 {
+  float f[9], a[9];     // fl32(F) and |fl32(F)|
+  float t_lo, t_hi;     // thresh rounded down / up
+};
+
+__device__ __forceinline__ void ga_f32(const double* F, double thresh, GaF32& g) {
+  for (int e = 0; e < 9; ++e) {
+    g.f[e] = __double2float_rn(F[e]);
+    g.a[e] = fabsf(g.f[e]);
+  }
+  g.t_lo = __double2float_rd(thresh);
+  g.t_hi = __double2float_ru(thresh);
+}
+
+__device__ __forceinline__ bool ga_inlier_fast(const GaF32& g, const float4 q, const double* F, const GaPt p,
+                                               double t2) {
+  const float u = 5.9604645e-08f;  // 2^-24
+  const float* f = g.f;
+  const float* a = g.a;
+  const float fx0 = fmaf(f[0], q.x, fmaf(f[1], q.y, f[2]));
+  const float fx1 = fmaf(f[3], q.x, fmaf(f[4], q.y, f[5]));
+  const float fx2 = fmaf(f[6], q.x, fmaf(f[7], q.y, f[8]));
+  const float ft0 = fmaf(f[0], q.z, fmaf(f[3], q.w, f[6]));
+  const float ft1 = fmaf(f[1], q.z, fmaf(f[4], q.w, f[7]));
+  const float r = fmaf(q.z, fx0, fmaf(q.w, fx1, fx2));
+  const float ax = fabsf(q.x), ay = fabsf(q.y), bx = fabsf(q.z), by = fabsf(q.w);
+  const float S0 = fmaf(a[0], ax, fmaf(a[1], ay, a[2]));
+  const float S1 = fmaf(a[3], ax, fmaf(a[4], ay, a[5]));
+  const float S2 = fmaf(a[6], ax, fmaf(a[7], ay, a[8]));
+  const float T0 = fmaf(a[0], bx, fmaf(a[3], by, a[6]));
+  const float T1 = fmaf(a[1], bx, fmaf(a[4], by, a[7]));
+  const float Sr = fmaf(bx, S0, fmaf(by, S1, S2));
+  const float gg = sqrtf(fmaf(fx0, fx0, fmaf(fx1, fx1, fmaf(ft0, ft0, ft1 * ft1))));
+  const float Er = 8.f * u * Sr;
+  const float Eg = 4.f * u * (S0 + S1 + T0 + T1 + gg);
+  const float ar = fabsf(r);
+  if (ar + Er < g.t_lo * (gg - Eg) * (1.f - 4.f * u)) return true;
+  if (ar - Er > g.t_hi * (gg + Eg) * (1.f + 4.f * u)) return false;
+  return ga_inlier(F, p, t2);
 }
 
 // One-sided Jacobi SVD of a 3 x 3 (columns orthogonalised); returns the right
@@ -269,7 +323,7 @@ __host__ __device__ __forceinline__ void design_row(const GaPt p, const double* 
 // of the 8 x 9 system (partial pivoting, f_8 = 1), rank 2, denormalised.
 // false when the sample is degenerate or the result is not finite.
 __host__ __device__ bool hypothesis(const GaPt* pts, uint32_t m, const uint32_t* w, const double* Ta, const double* Tb,
-                           double* F) {
+                                    double* F, double* fnull) {
   uint32_t idx[8];
   for (int k = 0; k < 8; ++k) {
     uint32_t v = (uint32_t)(((uint64_t)w[k] * (uint64_t)(m - k)) >> 32);
@@ -315,6 +369,7 @@ __host__ __device__ bool hypothesis(const GaPt* pts, uint32_t m, const uint32_t*
     for (int e = c + 1; e < 9; ++e) s += A[c][e] * f[e];
     f[c] = -s / A[c][c];
   }
+  for (int e = 0; e < 9; ++e) fnull[e] = f[e];
   rank2(f);
   denormalise(f, Ta, Tb, F);
   for (int e = 0; e < 9; ++e)
@@ -322,53 +377,66 @@ __host__ __device__ bool hypothesis(const GaPt* pts, uint32_t m, const uint32_t*
   return true;
 }
 
-// Eigenvector of the smallest eigenvalue of a symmetric 9 x 9 (cyclic Jacobi);
-// M is overwritten, V [81] is workspace.  Both live in shared memory in the
-// kernel (a local V was placed over the caller's local M in the stack frame).
-__host__ __device__ void smallest_eigvec9(double* M, double* V, double* v) {
-  for (int e = 0; e < 81; ++e) V[e] = (e % 10 == 0) ? 1.0 : 0.0;
-  for (int sweep = 0; sweep < 30; ++sweep) {
-    double off = 0.0, tot = 0.0;
-    for (int p = 0; p < 9; ++p)
-      for (int q = 0; q < 9; ++q) {
-        tot += M[9 * p + q] * M[9 * p + q];
-        if (p != q) off += M[9 * p + q] * M[9 * p + q];
-      }
-    if (off <= 1e-32 * tot) break;
-    for (int p = 0; p < 8; ++p)
-      for (int q = p + 1; q < 9; ++q) {
-        const double apq = M[9 * p + q];
-        if (fabs(apq) <= 1e-300) continue;
-        const double theta = (M[9 * q + q] - M[9 * p + p]) / (2.0 * apq);
-        const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-        const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
-        for (int k = 0; k < 9; ++k) {  // columns p, q
-          const double mkp = M[9 * k + p], mkq = M[9 * k + q];
-          M[9 * k + p] = c * mkp - s * mkq;
-          M[9 * k + q] = s * mkp + c * mkq;
-        }
-        for (int k = 0; k < 9; ++k) {  // rows p, q
-          const double mpk = M[9 * p + k], mqk = M[9 * q + k];
-          M[9 * p + k] = c * mpk - s * mqk;
-          M[9 * q + k] = s * mpk + c * mqk;
-        }
-        for (int k = 0; k < 9; ++k) {
-          const double vkp = V[9 * k + p], vkq = V[9 * k + q];
-          V[9 * k + p] = c * vkp - s * vkq;
-          V[9 * k + q] = s * vkp + c * vkq;
-        }
-      }
+// Eigenvector of the smallest eigenvalue of the symmetric positive
+// semi-definite 9 x 9 M (the refit's normal matrix), by inverse iteration
+// (Wilkinson; Golub and Van Loan, Sec. 7.6.1) on the Cholesky factor of
+// M + delta I, delta = 1e-14 trace M (a shift leaves the eigenvectors as they
+// are and keeps the factor finite when the fit is exact), started from x.
+// Stops when an iterate moves by less than 1e-15 (max-norm) or after 100
+// iterations.  x is overwritten with the unit eigenvector.  M (row-major, 81)
+// and L (81) are in shared memory in the kernel.
+__host__ __device__ void smallest_eigvec9(const double* M, double* L, double* x) {
+  double tr = 0.0;
+  for (int i = 0; i < 9; ++i) tr += M[10 * i];
+  const double delta = 1e-14 * tr + 1e-300;
+  for (int j = 0; j < 9; ++j) {  // L L^T = M + delta I, lower triangle of L
+    double d = M[10 * j] + delta;
+    for (int k = 0; k < j; ++k) d -= L[9 * j + k] * L[9 * j + k];
+    d = sqrt(d > 0.0 ? d : 1e-300);
+    L[10 * j] = d;
+    for (int i = j + 1; i < 9; ++i) {
+      double v = M[9 * i + j];
+      for (int k = 0; k < j; ++k) v -= L[9 * i + k] * L[9 * j + k];
+      L[9 * i + j] = v / d;
+    }
   }
-  int best = 0;
-  for (int p = 1; p < 9; ++p)
-    if (M[9 * p + p] < M[9 * best + best]) best = p;
-  for (int k = 0; k < 9; ++k) v[k] = V[9 * k + best];
+  double n0 = 0.0;
+  for (int i = 0; i < 9; ++i) n0 += x[i] * x[i];
+  n0 = 1.0 / sqrt(n0);
+  for (int i = 0; i < 9; ++i) x[i] *= n0;
+  for (int it = 0; it < 100; ++it) {
+    double y[9];
+    for (int i = 0; i < 9; ++i) {  // L y = x
+      double v = x[i];
+      for (int k = 0; k < i; ++k) v -= L[9 * i + k] * y[k];
+      y[i] = v / L[10 * i];
+    }
+    for (int i = 8; i >= 0; --i) {  // L^T z = y
+      double v = y[i];
+      for (int k = i + 1; k < 9; ++k) v -= L[9 * k + i] * y[k];
+      y[i] = v / L[10 * i];
+    }
+    double nn = 0.0, dot = 0.0;
+    for (int i = 0; i < 9; ++i) {
+      nn += y[i] * y[i];
+      dot += y[i] * x[i];
+    }
+    const double sc = (dot >= 0.0 ? 1.0 : -1.0) / sqrt(nn);
+    double mv = 0.0;
+    for (int i = 0; i < 9; ++i) {
+      const double z = y[i] * sc;
+      mv = fmax(mv, fabs(z - x[i]));
+      x[i] = z;
+    }
+    if (mv < 1e-15) break;
+  }
 }
 
-__global__ void __launch_bounds__(GA_T) k_ga_ransac(GaArgs a) {
+__global__ void __launch_bounds__(GA_T, 2) k_ga_ransac(GaArgs a) {
   __shared__ double s_d[GA_T / 32];
   __shared__ uint32_t s_best[GA_T / 32][2];
-  __shared__ double s_F[9], s_M[45], s_Mf[81], s_V[81];
+  __shared__ double s_F[9], s_M[45], s_Mf[81], s_L[81], s_x[9];
+  __shared__ double s_hF[GA_T][9], s_hf[GA_T][9];  // each thread's best hypothesis: F and its null vector
   __shared__ uint32_t s_bh;
   const uint32_t p = blockIdx.x, tid = threadIdx.x;
   const uint64_t m0 = a.moff[p];
@@ -383,6 +451,7 @@ __global__ void __launch_bounds__(GA_T) k_ga_ransac(GaArgs a) {
   const uint64_t A0 = a.img_off[ia], B0 = a.img_off[ib];
   const uint32_t nA = (uint32_t)(a.img_off[ia + 1] - A0), nB = (uint32_t)(a.img_off[ib + 1] - B0);
   GaPt* pts = a.pts + m0;
+  float4* pts32 = a.pts32 + m0;
   uint8_t* inl = a.inl + m0;
   double sxa = 0.0, sya = 0.0, sxb = 0.0, syb = 0.0;
   for (uint32_t i = tid; i < m; i += GA_T) {
@@ -392,6 +461,7 @@ __global__ void __launch_bounds__(GA_T) k_ga_ransac(GaArgs a) {
     const float2 pb = jb < nB ? a.kpts[B0 + jb] : make_float2(0.f, 0.f);
     const GaPt q = {(double)pa.x, (double)pa.y, (double)pb.x, (double)pb.y};
     pts[i] = q;
+    pts32[i] = make_float4(pa.x, pa.y, pb.x, pb.y);
     sxa += q.x;
     sya += q.y;
     sxb += q.z;
@@ -412,13 +482,19 @@ __global__ void __launch_bounds__(GA_T) k_ga_ransac(GaArgs a) {
   // hypotheses: thread h takes h, h + GA_T, ...; the most inliers win, ties to the lower h
   uint32_t best_c = 0, best_h = GA_NONE;
   for (uint32_t h = tid; h < a.n_hyp; h += GA_T) {
-    double F[9];
-    if (!hypothesis(pts, m, a.words + ((size_t)p * a.n_hyp + h) * 8, Ta, Tb, F)) continue;
+    double F[9], fn[9];
+    if (!hypothesis(pts, m, a.words + ((size_t)p * a.n_hyp + h) * 8, Ta, Tb, F, fn)) continue;
+    GaF32 g;
+    ga_f32(F, a.thresh, g);
     uint32_t c = 0;
-    for (uint32_t i = 0; i < m; ++i) c += ga_inlier(F, pts[i], a.t2) ? 1u : 0u;
+    for (uint32_t i = 0; i < m; ++i) c += ga_inlier_fast(g, pts32[i], F, pts[i], a.t2) ? 1u : 0u;
     if (best_h == GA_NONE || c > best_c) {
       best_c = c;
       best_h = h;
+      for (int e = 0; e < 9; ++e) {
+        s_hF[tid][e] = F[e];
+        s_hf[tid][e] = fn[e];
+      }
     }
   }
   {  // CTA argmax: key (count, -h), invalid lowest
@@ -446,7 +522,11 @@ __global__ void __launch_bounds__(GA_T) k_ga_ransac(GaArgs a) {
         }
       }
       s_bh = bh;
-      if (bh != GA_NONE) hypothesis(pts, m, a.words + ((size_t)p * a.n_hyp + bh) * 8, Ta, Tb, s_F);
+      if (bh != GA_NONE)  // hypothesis bh was the best of thread bh % GA_T
+        for (int e = 0; e < 9; ++e) {
+          s_F[e] = s_hF[bh % GA_T][e];
+          s_x[e] = s_hf[bh % GA_T][e];
+        }
     }
     __syncthreads();
   }
@@ -459,37 +539,45 @@ __global__ void __launch_bounds__(GA_T) k_ga_ransac(GaArgs a) {
   double F[9];
   for (int e = 0; e < 9; ++e) F[e] = s_F[e];
   uint32_t cnt_local = 0;
+  GaF32 g;
+  ga_f32(F, a.thresh, g);
   for (uint32_t i = tid; i < m; i += GA_T) {
-    const bool in = ga_inlier(F, pts[i], a.t2);
+    const bool in = ga_inlier_fast(g, pts32[i], F, pts[i], a.t2);
     inl[i] = in ? 1 : 0;
     cnt_local += in ? 1u : 0u;
   }
   const uint32_t n_best = (uint32_t)block_sum((double)cnt_local, s_d);
   __syncthreads();  // inlier flags visible
   if (n_best >= 8) {
-    // normal matrix of the inliers' design rows, entries (r, c), r <= c, each summed in match order
-    if (tid < 45) {
-      uint32_t r = 0, t = tid;
+    // normal matrix of the inliers' design rows, entries (r, c), r <= c: group g of 45 threads
+    // sums the matches i = g, g + 5, ... in order, then the five partial sums are added in group order
+    __shared__ double s_part[5][45];
+    if (tid < 225) {
+      const uint32_t grp5 = tid / 45, ent = tid % 45;
+      uint32_t r = 0, t = ent;
       while (t >= 9 - r) {
         t -= 9 - r;
         ++r;
       }
       const uint32_t c = r + t;
-      double s = 0.0;
-      for (uint32_t i = 0; i < m; ++i) {
+      double sum = 0.0;
+      for (uint32_t i = grp5; i < m; i += 5) {
         if (!inl[i]) continue;
         double row[9];
         design_row(pts[i], Ta, Tb, row);
-        s += row[r] * row[c];
+        sum += row[r] * row[c];
       }
-      s_M[tid] = s;
+      s_part[grp5][ent] = sum;
     }
+    __syncthreads();
+    if (tid < 45) s_M[tid] = (((s_part[0][tid] + s_part[1][tid]) + s_part[2][tid]) + s_part[3][tid]) + s_part[4][tid];
     __syncthreads();
     if (tid == 0) {
       double f[9];
       for (uint32_t r = 0, e = 0; r < 9; ++r)
         for (uint32_t c = r; c < 9; ++c, ++e) s_Mf[9 * r + c] = s_Mf[9 * c + r] = s_M[e];
-      smallest_eigvec9(s_Mf, s_V, f);
+      for (int e = 0; e < 9; ++e) f[e] = s_x[e];  // start: the winning sample's null vector
+      smallest_eigvec9(s_Mf, s_L, f);
       rank2(f);
       denormalise(f, Ta, Tb, s_F);
     }
@@ -509,7 +597,8 @@ __global__ void __launch_bounds__(GA_T) k_ga_ransac(GaArgs a) {
   const double sc = (F[bi] > 0.0 ? 1.0 : -1.0) / sqrt(nn);
   for (int e = 0; e < 9; ++e) F[e] *= sc;
   uint32_t c2 = 0;
-  for (uint32_t i = tid; i < m; i += GA_T) c2 += ga_inlier(F, pts[i], a.t2) ? 1u : 0u;
+  ga_f32(F, a.thresh, g);
+  for (uint32_t i = tid; i < m; i += GA_T) c2 += ga_inlier_fast(g, pts32[i], F, pts[i], a.t2) ? 1u : 0u;
   const uint32_t n_in = (uint32_t)block_sum((double)c2, s_d);
   if (tid < 9) Fout[tid] = F[tid];
   if (tid == 0)
@@ -530,7 +619,7 @@ int err_of(cudaError_t e) {
 bool ga_params_ok(const cashash_ga_params* gp) {
   return gp && gp->top_pct >= 1 && gp->top_pct <= 100 && gp->min_matches >= 8 && gp->n_hyp >= 1 &&
          gp->n_hyp <= CASHASH_GA_MAX_HYP && gp->inlier_den >= 1 && gp->inlier_num <= gp->inlier_den &&
-         gp->thresh_px > 0.0 && gp->thresh_px < 1e150;
+         gp->thresh_px > 0.0 && gp->thresh_px < 1e150 && gp->kernel <= CASHASH_KERNEL_QUERY;
 }
 
 // Device scratch released at the end of a call (stream-ordered).
@@ -561,7 +650,7 @@ extern "C" void cashash_ga_default_params(cashash_ga_params* gp) {
   gp->n_hyp = 256;
   gp->inlier_num = 2;
   gp->inlier_den = 3;
-  gp->reserved = 0;
+  gp->kernel = 0;
   gp->thresh_px = 3.0;
 }
 
@@ -623,8 +712,10 @@ extern "C" int cashash_estimate_F(const float* kpts, const uint64_t* img_off, ui
   uint32_t* d_pairs = nullptr;
   GaPt* d_pts = nullptr;
   uint8_t* d_inl = nullptr;
+  float4* d_pts32 = nullptr;
   if ((st = sc.get(d_off, n_images + 1)) != CASHASH_OK || (st = sc.get(d_pairs, 2ull * P)) != CASHASH_OK ||
-      (st = sc.get(d_pts, total)) != CASHASH_OK || (st = sc.get(d_inl, total)) != CASHASH_OK)
+      (st = sc.get(d_pts, total)) != CASHASH_OK || (st = sc.get(d_inl, total)) != CASHASH_OK ||
+      (st = sc.get(d_pts32, total)) != CASHASH_OK)
     return st;
   if ((st = err_of(cudaMemcpyAsync(d_off, img_off, (n_images + 1) * 8ull, cudaMemcpyHostToDevice, s))) != CASHASH_OK)
     return st;
@@ -638,6 +729,7 @@ extern "C" int cashash_estimate_F(const float* kpts, const uint64_t* img_off, ui
   a.mt = matches;
   a.words = words;
   a.pts = d_pts;
+  a.pts32 = d_pts32;
   a.inl = d_inl;
   a.F = F_out;
   a.info = reinterpret_cast<uint4*>(info_out);
@@ -647,6 +739,7 @@ extern "C" int cashash_estimate_F(const float* kpts, const uint64_t* img_off, ui
   a.num = gp->inlier_num;
   a.den = gp->inlier_den;
   a.t2 = gp->thresh_px * gp->thresh_px;
+  a.thresh = gp->thresh_px;
   k_ga_ransac<<<P, GA_T, 0, s>>>(a);
   return err_of(cudaGetLastError());
 }
@@ -707,7 +800,18 @@ extern "C" int cashash_ga_stage1(cashash_ctx* ctx, const cashash_set* set, const
   if (P == 0) return err_of(cudaStreamSynchronize(s));
   cashash_plan* pl = nullptr;
   if ((st = cashash_plan_create(ctx, &S, pairs_host, P, &pl)) != CASHASH_OK) return st;
-  st = cashash_match_plan(ctx, pl, nullptr, moff, mt, cap, stream_);
+  cashash_tuning tu{};
+  if (cashash_plan_get_tuning(pl, &tu) == CASHASH_OK && tu.kernel != 0) {  // batched plans only
+    uint32_t want = gp->kernel;
+    if (want == 0) want = N < 4096ull * std::max<uint32_t>(n_images, 1) ? CASHASH_KERNEL_QUERY : CASHASH_KERNEL_JOIN;
+    if (want != tu.kernel) {
+      cashash_tuning t2{};
+      t2.kernel = want;
+      st = cashash_plan_set_tuning(pl, &t2);
+      if (st == CASHASH_ENOTSUP) st = CASHASH_OK;  // the join does not apply: keep the plan's kernel
+    }
+  }
+  if (st == CASHASH_OK) st = cashash_match_plan(ctx, pl, nullptr, moff, mt, cap, stream_);
   if (st == CASHASH_OK) st = cashash_sync_status(ctx, stream_);
   cashash_plan_destroy(pl);
   if (st != CASHASH_OK) return st;

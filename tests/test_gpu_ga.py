@@ -155,7 +155,7 @@ def test_stage1_no_pairs_and_bad_args(ch, oga):
     F, info = ch.cashash_ga_stage1(ctx, ds, sc, mu, np.zeros((0, 2), np.uint32), w)
     assert F.shape == (0, 9) and info.shape == (0, 4)
     for bad in (dict(n_hyp=0), dict(n_hyp=ch.GA_MAX_HYP + 1), dict(min_matches=7), dict(top_pct=0),
-                dict(inlier_num=4, inlier_den=3), dict(thresh_px=0.0)):
+                dict(inlier_num=4, inlier_den=3), dict(thresh_px=0.0), dict(kernel=3)):
         with pytest.raises(ch.CashashError) as e:
             ch.cashash_ga_stage1(ctx, ds, sc, mu, s.pairs[:1], w, ch.cashash_ga_default_params(**bad))
         assert e.value.status == ch.CASHASH_EINVAL
