@@ -168,3 +168,48 @@ def test_config4_full_size(ch, orc):
     _sample_check(orc, s, off2, mt2, codes_of, mu, 24, 7, po=po)
     plan.close()
     ctx.close()
+
+
+def test_config4_ga_stage1_full_size(ch):
+    """Ga-CasHash first stage on config 4 as bench.py --ga runs it (all 14,613
+    pairs, BF16 codes, per-query subset matching); 24 sampled pairs are redone
+    by the oracle on the images they touch (selection, subset codes with the
+    full set's centre, CasHash, RANSAC with the same words): selection, counts,
+    the winning hypothesis and acceptance identical, F within 1e-8."""
+    import oracle as orc
+    from oracle import ga as oga
+    orc.build()
+    s = synth.config4()
+    bf = dict(precision=ch.CASHASH_BF16, schedule=ch.CASHASH_SCHED_PERSISTENT)
+    p1, p2 = ch.cashash_default_params(**bf), ch.cashash_default_params(epi_px=4.0, **bf)
+    ctx1, ctx2 = ch.cashash_create(p1, s.R), ch.cashash_create(p2, s.R)
+    ds = ch.DeviceSet(p2, s.img_off, s.desc, s.kpts)
+    ch.cashash_build_codes(ctx2, ds)
+    mu = ch.cashash_get_mean(ctx2)
+    assert np.array_equal(mu, orc.mean(s.desc))
+    gp = ch.cashash_ga_default_params()
+    words = synth.ransac_words(4, len(s.pairs), gp.n_hyp)
+    F, info = ch.cashash_ga_stage1(ctx1, ds, torch.from_numpy(s.scale).cuda(), mu, s.pairs,
+                                   torch.from_numpy(words.view(np.int32)).cuda(), gp)
+    torch.cuda.synchronize()
+    F = F.cpu().numpy()
+    info = info.cpu().numpy().view(np.uint32)
+    assert info[:, 3].sum() > 0.9 * len(s.pairs)
+    sel, sub = ch.cashash_ga_select(torch.from_numpy(s.scale).cuda(), s.img_off, gp.top_pct)
+    esel, esub = oga.top_scale(s.scale, s.img_off, gp.top_pct)
+    assert np.array_equal(sub, esub) and np.array_equal(sel.cpu().numpy().view(np.uint32).astype(np.uint64), esel)
+    pick = np.sort(np.random.default_rng(11).choice(len(s.pairs), 24, replace=False))
+    imgs = np.unique(s.pairs[pick])
+    remap = {int(i): k for k, i in enumerate(imgs)}
+    rows = np.concatenate([np.arange(int(s.img_off[i]), int(s.img_off[i + 1])) for i in imgs])
+    off = np.zeros(len(imgs) + 1, np.uint64)
+    off[1:] = np.cumsum(s.sizes()[imgs])
+    pr = np.array([[remap[int(a)], remap[int(b)]] for a, b in s.pairs[pick]], np.uint32)
+    ogp = oga.GaParams(top_pct=gp.top_pct, min_matches=gp.min_matches, n_hyp=gp.n_hyp,
+                       inlier_num=gp.inlier_num, inlier_den=gp.inlier_den, thresh_px=gp.thresh_px)
+    eF, einfo, *_ = oga.stage1(s.desc[rows], off, s.kpts[rows], s.scale[rows], mu, s.R, pr, orc.params(), ogp,
+                               words[pick])
+    assert np.array_equal(info[pick], einfo)
+    assert np.abs(F[pick] - eF).max() <= 1e-8
+    ctx1.close()
+    ctx2.close()
