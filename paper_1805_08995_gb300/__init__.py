@@ -108,6 +108,7 @@ def _load():
             "cashash_plan_autotune": ([vp, vp, vp, u32, vp], C.c_int),
             "cashash_match_chunked": ([vp, P(cashash_set), vp, u64, vp, u32, P(u64), CHUNK_FN, vp, vp], C.c_int),
             "cashash_get_params": ([vp, P(cashash_params)], C.c_int),
+            "cashash_set_host_tuning": ([vp, P(cashash_tuning)], C.c_int),
             "cashash_ga_default_params": ([P(cashash_ga_params)], None),
             "cashash_ga_subset_offsets": ([vp, u32, u32, vp], C.c_int),
             "cashash_ga_select": ([vp, vp, u32, u32, vp, vp], C.c_int),
@@ -131,7 +132,8 @@ def exported_symbols():
             "cashash_run_host", "cashash_get_stats", "cashash_set_profiling", "cashash_match_pair_noalloc",
             "cashash_plan_set_threshold_hint", "cashash_plan_get_tuning", "cashash_plan_set_tuning",
             "cashash_plan_autotune", "cashash_match_chunked", "cashash_get_params", "cashash_ga_default_params",
-            "cashash_ga_subset_offsets", "cashash_ga_select", "cashash_estimate_F", "cashash_ga_stage1"]
+            "cashash_ga_subset_offsets", "cashash_ga_select", "cashash_estimate_F", "cashash_ga_stage1",
+            "cashash_set_host_tuning"]
 
 
 def _check(st, what):
@@ -302,6 +304,15 @@ def cashash_plan_autotune(ctx: Context, plan: Plan, F=None, max_pairs: int = 0, 
     _check(_load().cashash_plan_autotune(ctx.handle, plan.handle, _dptr(F), int(max_pairs), _stream(stream)),
            "cashash_plan_autotune")
     return cashash_plan_get_tuning(plan)
+
+
+def cashash_set_host_tuning(ctx: Context, kernel: int = 0, tile: int = 0, ctas_per_sm: int = 0):
+    """Kernel configuration of cashash_run_host's plans; kernel 0 restores the default."""
+    if kernel == 0:
+        _check(_load().cashash_set_host_tuning(ctx.handle, None), "cashash_set_host_tuning")
+        return
+    t = cashash_tuning(kernel, tile, ctas_per_sm, 0, -1.0)
+    _check(_load().cashash_set_host_tuning(ctx.handle, C.byref(t)), "cashash_set_host_tuning")
 
 
 def cashash_plan_destroy(plan: Plan):

@@ -34,6 +34,8 @@ struct HostWS {  // device buffers of the end-to-end host path, grown on demand
   std::vector<uint32_t> plan_pairs;  // pair list of the cached plan
   std::vector<uint64_t> plan_off;    // image offsets of the cached plan
   cashash_plan* plan = nullptr;
+  cashash_tuning tune{};             // configuration for the host path's plans, when has_tune
+  bool has_tune = false;
 };
 
 }  // namespace
@@ -1114,6 +1116,21 @@ int cashash_get_stats(cashash_ctx* c, cashash_stats* out) {
   return CASHASH_OK;
 }
 
+int cashash_set_host_tuning(cashash_ctx* c, const cashash_tuning* t) {
+  if (!c) return CASHASH_EINVAL;
+  if (t && t->kernel != CASHASH_KERNEL_JOIN && t->kernel != CASHASH_KERNEL_QUERY) return CASHASH_EINVAL;
+  HostWS& h = c->hw;
+  h.has_tune = t != nullptr;
+  if (t) h.tune = *t;
+  if (h.plan) {  // the next call builds its plan with the new configuration
+    cashash_plan_destroy(h.plan);
+    h.plan = nullptr;
+    h.plan_pairs.clear();
+    h.plan_off.clear();
+  }
+  return CASHASH_OK;
+}
+
 int cashash_run_host(cashash_ctx* c, const uint8_t* desc_host, const uint64_t* img_off, uint32_t n_images,
                      const float* kpts_host, const uint32_t* pairs_host, uint32_t P, const double* F_host,
                      uint64_t* match_off_host, uint32_t* matches_host, uint64_t cap, uint64_t stage_bytes) {
@@ -1213,6 +1230,12 @@ int cashash_run_host(cashash_ctx* c, const uint8_t* desc_host, const uint64_t* i
     h.plan = nullptr;
     st = cashash_plan_create(c, &S, pairs_host, P, &h.plan);
     if (st != CASHASH_OK) return st;
+    cashash_tuning cur{};
+    if (h.has_tune && cashash_plan_get_tuning(h.plan, &cur) == CASHASH_OK && cur.kernel != 0) {
+      st = cashash_plan_set_tuning(h.plan, &h.tune);
+      if (st == CASHASH_ENOTSUP) st = CASHASH_OK;  // the join does not apply here: keep the default
+      if (st != CASHASH_OK) return st;
+    }
     h.plan_pairs.assign(pairs_host, pairs_host + 2 * (size_t)P);
     h.plan_off.assign(img_off, img_off + n_images + 1);
   }

@@ -21,7 +21,8 @@
 //                 hypothesis per thread (8 x 9 elimination with partial
 //                 pivoting for the null vector, rank 2 by a one-sided Jacobi
 //                 SVD of the 3 x 3, inlier count), block argmax, refit from
-//                 the 9 x 9 normal matrix (cyclic Jacobi), final count.  The
+//                 the 9 x 9 normal matrix (inverse iteration on its Cholesky
+//                 factor), final count.  The
 //                 inlier test runs in FP32 with a rounding bound and falls
 //                 back to FP64 only near the threshold, so every decision is
 //                 the FP64 one.

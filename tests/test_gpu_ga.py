@@ -4,7 +4,8 @@ Selection by scale and every integer decision (stage-1 match counts, inlier
 counts, the winning hypothesis, acceptance) must be identical.  F is compared
 as a unit-norm matrix within 1e-8 (max-abs): both sides solve the same FP64
 problems with different algorithms (GPU: elimination with partial pivoting,
-one-sided / cyclic Jacobi on the normal matrix; oracle: LAPACK SVD), whose
+a one-sided Jacobi SVD of the 3 x 3, inverse iteration on the normal matrix;
+oracle: LAPACK SVD), whose
 results differ by a few units of rounding amplified by the conditioning of
 the normalised design matrix.
 """

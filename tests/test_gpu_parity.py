@@ -541,6 +541,17 @@ def test_host_end_to_end_matches_device_path(ch, orc):
     st, off, mt = ch.cashash_run_host(ctx, s.desc, s.img_off, pairs, 10)
     assert st == ch.CASHASH_EOVERFLOW and np.array_equal(off, eoff) and np.array_equal(mt, emt[:10])
     ctx.close()
+    # a batched context with every host-path kernel configuration
+    ctx = ch.cashash_create(ch.cashash_default_params(schedule=ch.CASHASH_SCHED_PERSISTENT), s.R)
+    for kernel, tile in ((ch.CASHASH_KERNEL_QUERY, 512), (ch.CASHASH_KERNEL_JOIN, 2), (ch.CASHASH_KERNEL_QUERY, 256),
+                         (0, 0)):
+        ch.cashash_set_host_tuning(ctx, kernel, tile)
+        st, off, mt = ch.cashash_run_host(ctx, pinned, s.img_off, pairs, cap)
+        assert st == ch.CASHASH_OK
+        assert np.array_equal(off, eoff) and np.array_equal(mt, emt)
+    with pytest.raises(ch.CashashError):
+        ch.cashash_set_host_tuning(ctx, 7)
+    ctx.close()
 
 
 def test_invalid_arguments_are_rejected(ch):
