@@ -686,6 +686,7 @@ extern "C" int cashash_ga_select(const float* scale, const uint64_t* img_off, ui
   if ((st = err_of(cudaMemcpyAsync(d_sub, sub.data(), (n_images + 1) * 8ull, cudaMemcpyHostToDevice, s))) !=
       CASHASH_OK)
     return st;
+  if (n_images > 0x7FFFFFFFu) return CASHASH_EINVAL;  // one CTA per image
   k_ga_select<<<n_images, GA_T, 0, s>>>(scale, d_off, d_sub, sel);
   return err_of(cudaGetLastError());
 }
@@ -698,6 +699,7 @@ extern "C" int cashash_estimate_F(const float* kpts, const uint64_t* img_off, ui
                                                                     !info_out || !words || !kpts)))
     return CASHASH_EINVAL;
   if (P == 0) return CASHASH_OK;
+  if (P > 0x7FFFFFFFu) return CASHASH_EINVAL;  // one CTA per pair
   for (uint64_t i = 0; i < 2ull * P; ++i)
     if (pairs_host[i] >= n_images) return CASHASH_EINVAL;
   for (uint32_t i = 0; i < n_images; ++i)

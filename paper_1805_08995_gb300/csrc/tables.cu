@@ -192,6 +192,7 @@ cudaError_t launch_build_join(const uint8_t* buckets, const uint32_t* codes, con
                               uint32_t n_max, uint8_t* join, cudaStream_t s) {
   const uint64_t tasks = (uint64_t)n_images * n_tables;
   if (tasks == 0) return cudaSuccess;
+  if (tasks > 0x7FFFFFFFull) return cudaErrorInvalidValue;  // one CTA (or warp) per image and table
   if (n_max <= BJ_MAX_N) {
     static int attr_dev = -1;
     int dev = 0;
@@ -216,6 +217,7 @@ cudaError_t launch_build_tables(const uint8_t* buckets, const uint64_t* chunk_fe
                                 uint32_t n_chunks, uint32_t n_tables, uint8_t* tables, cudaStream_t s) {
   const uint64_t tasks = (uint64_t)n_chunks * n_tables;
   if (tasks == 0) return cudaSuccess;
+  if (tasks > 0x7FFFFFFFull) return cudaErrorInvalidValue;  // one CTA per chunk and table
   static_assert(JC <= (int)BJ_MAX_N, "chunk tables sort in shared memory");
   k_sort_tables<true><<<(unsigned)tasks, 256, sort_smem(JC), s>>>(buckets, nullptr, chunk_feat0, chunk_len, nullptr,
                                                                   n_tables, tables);
