@@ -429,7 +429,7 @@ def run_ours(args):
             ts.append(time.perf_counter() - t0)
             assert st == ch.CASHASH_OK
         n_m = int(mo_h[P])
-        e2e = {"value": P / statistics.mean(ts), "unit": "pairs/s",
+        e2e = {"value": P / statistics.mean(ts), "unit": "pairs/s", "ms_each": [round(t * 1e3, 2) for t in ts],
                "h2d_bytes_per_step": int(s.desc.nbytes + 8 * (len(s.img_off)) +
                                          (s.kpts.nbytes + s.F.nbytes if band else 0)),
                "d2h_bytes_per_step": int(8 * (P + 1) + 8 * n_m)}
