@@ -18,11 +18,16 @@ Readings where the paper is silent (each is also a parameter):
     scale, ties to the lower feature index, kept in feature order;
   * stage-1 codes are the full set's codes of those features (the same centre
     and projection), so stage-1 matching is CasHash restricted to the subsets;
-  * RANSAC: n_hyp hypotheses per pair, each from 8 distinct matches drawn by
-    the word-to-index map below; a match is an inlier when its squared Sampson
-    distance is at most thresh_px^2; the hypothesis with the most inliers wins
-    (ties to the lower index) and F is refitted on its inliers (least squares,
-    same normalisation) when it has at least 8;
+  * RANSAC: at most n_hyp hypotheses per pair, each from 8 distinct matches
+    drawn by the word-to-index map below, in batches of 32 with the adaptive
+    stop of Hartley and Zisserman (Algorithm 4.5): after a batch, stop when
+    (1 - w^8)^N <= 1 - confidence, N the hypotheses done and w the best inlier
+    fraction so far (w^8 by three squarings, the power by binary
+    exponentiation, every step one correctly rounded double operation); a
+    match is an inlier when its squared Sampson distance is at most
+    thresh_px^2; the hypothesis with the most inliers wins (ties to the lower
+    index) and F is refitted on its inliers (least squares, same
+    normalisation) when it has at least 8;
   * the accepted pair's F is the refit, scaled to unit Frobenius norm with its
     largest-magnitude entry (first on ties) positive.
 Convention: x_B^T F x_A = 0 for a query point x_A of image A and its match
@@ -47,6 +52,10 @@ class GaParams:
     inlier_num: int = 2       # accepted when den * inliers >= num * matches
     inlier_den: int = 3
     thresh_px: float = 3.0    # Sampson distance threshold, pixels
+    confidence: float = 0.99  # adaptive stop; >= 1 runs all n_hyp hypotheses
+
+
+BATCH = 32  # hypotheses between two checks of the adaptive stop
 
 
 def top_scale(scale: np.ndarray, img_off: np.ndarray, pct: int):
@@ -130,13 +139,31 @@ def sampson2(F: np.ndarray, xa: np.ndarray, xb: np.ndarray) -> np.ndarray:
     return num / den
 
 
+def ransac_stop(best: int, m: int, done: int, confidence: float) -> bool:
+    """Adaptive stop: (1 - w^8)^done <= 1 - confidence with w = best / m."""
+    if not confidence < 1.0:
+        return False
+    w = best / m
+    w2 = w * w
+    w4 = w2 * w2
+    base = 1.0 - w4 * w4
+    r = 1.0
+    e = done
+    while e:
+        if e & 1:
+            r = r * base
+        base = base * base
+        e >>= 1
+    return r <= 1.0 - confidence
+
+
 def estimate_F(pa: np.ndarray, pb: np.ndarray, words: np.ndarray, gp: GaParams):
     """RANSAC + normalised 8-point on the matched key-points pa (image A) and
     pb (image B), [m][2] float.  Returns (F [3][3] or zeros, info) with info =
-    (n_matches, n_inliers, best_hyp, accepted)."""
+    (n_matches, n_inliers, best_hyp, accepted, hypotheses evaluated)."""
     m = len(pa)
     if m < gp.min_matches:
-        return np.zeros((3, 3)), (m, 0, NONE, 0)
+        return np.zeros((3, 3)), (m, 0, NONE, 0, 0)
     pa = pa.astype(np.float64)
     pb = pb.astype(np.float64)
     Ta, Tb = hartley(pa), hartley(pb)
@@ -145,17 +172,23 @@ def estimate_F(pa: np.ndarray, pb: np.ndarray, words: np.ndarray, gp: GaParams):
     rows = design_rows(na, nb)
     t2 = gp.thresh_px * gp.thresh_px
     best, best_h, best_F = -1, NONE, None
-    for h in range(gp.n_hyp):
-        idx = sample_indices(words[h], m)
-        Fn = rank2(null_f(rows[idx]))
-        F = Tb.T @ Fn @ Ta
-        if not np.all(np.isfinite(F)):
-            continue
-        cnt = int(np.count_nonzero(sampson2(F, xa, xb) <= t2))
-        if cnt > best:
-            best, best_h, best_F = cnt, h, F
+    done = 0
+    while done < gp.n_hyp:
+        end = min(done + BATCH, gp.n_hyp)
+        for h in range(done, end):
+            idx = sample_indices(words[h], m)
+            Fn = rank2(null_f(rows[idx]))
+            F = Tb.T @ Fn @ Ta
+            if not np.all(np.isfinite(F)):
+                continue
+            cnt = int(np.count_nonzero(sampson2(F, xa, xb) <= t2))
+            if cnt > best:
+                best, best_h, best_F = cnt, h, F
+        done = end
+        if best_F is not None and ransac_stop(best, m, done, gp.confidence):
+            break
     if best_F is None:
-        return np.zeros((3, 3)), (m, 0, NONE, 0)
+        return np.zeros((3, 3)), (m, 0, NONE, 0, done)
     F = best_F
     inl = sampson2(F, xa, xb) <= t2
     if np.count_nonzero(inl) >= 8:
@@ -163,13 +196,13 @@ def estimate_F(pa: np.ndarray, pb: np.ndarray, words: np.ndarray, gp: GaParams):
     F = normalise_F(F)
     n_in = int(np.count_nonzero(sampson2(F, xa, xb) <= t2))
     acc = int(gp.inlier_den * n_in >= gp.inlier_num * m)
-    return F, (m, n_in, best_h, acc)
+    return F, (m, n_in, best_h, acc, done)
 
 
 def stage1(desc, img_off, kpts, scale, mu, R, pairs, po, gp: GaParams, words):
     """The whole first stage: subset selection, CasHash matching of the
     subsets (codes with the full set's centre mu), F per pair.  Returns
-    (F [P][9], info [P][4] uint32, sel, sub_off, (match offsets, matches))."""
+    (F [P][9], info [P][5] uint32, sel, sub_off, (match offsets, matches))."""
     sel, sub_off = top_scale(scale, img_off, gp.top_pct)
     sel_i = sel.astype(np.int64)
     d_sub = np.ascontiguousarray(desc[sel_i])
@@ -178,7 +211,7 @@ def stage1(desc, img_off, kpts, scale, mu, R, pairs, po, gp: GaParams, words):
     moff, mt = match_pairs(d_sub, sub_off, codes, buckets, pairs, po)
     P = len(pairs)
     F = np.zeros((P, 9))
-    info = np.zeros((P, 4), np.uint32)
+    info = np.zeros((P, 5), np.uint32)
     for p in range(P):
         a, b = int(pairs[p][0]), int(pairs[p][1])
         lo, hi = int(moff[p]), int(moff[p + 1])

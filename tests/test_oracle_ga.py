@@ -197,8 +197,8 @@ def test_ransac_planted_outliers_accepted():
     pa, pb = np.concatenate([xa, oa]), np.concatenate([xb, ob])
     perm = np.random.default_rng(9).permutation(90)
     Fe, info = ga.estimate_F(pa[perm], pb[perm], _words(256, 10), ga.GaParams())
-    m, n_in, best, acc = info
-    assert (m, n_in, acc) == (90, 70, 1) and best != ga.NONE
+    m, n_in, best, acc, done = info
+    assert (m, n_in, acc) == (90, 70, 1) and best != ga.NONE and done % 32 == 0 and done <= 256
     assert _same_F(Fe, F, 1e-8)
     assert abs(np.linalg.norm(Fe) - 1) < 1e-12 and Fe.ravel()[np.argmax(np.abs(Fe))] > 0
 
@@ -212,7 +212,8 @@ def test_ransac_two_thirds_boundary_and_ties():
     for h in (0, 1):
         w[h] = [_word(k + 3 * h, 90 - k) for k in range(8)]
     Fe, info = ga.estimate_F(pa, pb, w, ga.GaParams(n_hyp=64))
-    assert tuple(info) == (90, 60, 0, 1)  # 3 * 60 >= 2 * 90 exactly
+    # 3 * 60 >= 2 * 90 exactly; w = 2/3 never stops early: (1 - w^8)^64 = 0.078 > 0.01
+    assert tuple(info) == (90, 60, 0, 1, 64)
     assert _same_F(Fe, F, 1e-8)
 
 
@@ -222,7 +223,7 @@ def test_ransac_rejects_and_skips():
     Fe, info = ga.estimate_F(np.concatenate([xa, oa]), np.concatenate([xb, ob]), _words(256, 16), ga.GaParams())
     assert info[0] == 90 and info[3] == 0 and info[1] < 60
     Fz, info = ga.estimate_F(xa[:15], xb[:15], _words(8, 17), ga.GaParams())
-    assert tuple(info) == (15, 0, ga.NONE, 0) and not Fz.any()
+    assert tuple(info) == (15, 0, ga.NONE, 0, 0) and not Fz.any()
 
 
 def test_refit_does_not_depend_on_the_winning_sample():
@@ -242,3 +243,33 @@ def test_refit_does_not_depend_on_the_winning_sample():
     assert np.abs(F1 - F2).max() < 1e-10 and _same_F(F1, F, 1e-2)
     # while the winning 8-point hypotheses themselves differ on noisy data
     assert np.abs(H[0] - H[1]).max() > 1e-6
+
+
+def test_ransac_stop_rule_closed_form():
+    """(1 - w^8)^N <= 1 - p against the closed form, at points far from equality."""
+    for best, m, done, conf, want in ((100, 100, 32, 0.99, True), (75, 100, 32, 0.99, False),
+                                      (75, 100, 64, 0.99, True), (50, 100, 256, 0.99, False),
+                                      (50, 100, 1280, 0.99, True), (100, 100, 4096, 1.0, False),
+                                      (9, 10, 8, 0.9999, False), (9, 10, 64, 0.9999, True)):
+        q = (1.0 - (best / m) ** 8) ** done
+        assert (q <= 1.0 - conf if conf < 1.0 else False) == want
+        assert ga.ransac_stop(best, m, done, conf) == want
+
+
+def test_ransac_adaptive_batches():
+    """Hypotheses run in batches of 32 until the stop rule holds."""
+    xa, xb, F = _views(50, seed=21)
+    _, info = ga.estimate_F(xa, xb, _words(256, 22), ga.GaParams())
+    assert info[1] == 50 and info[4] == 32                      # w = 1 after the first batch
+    _, info = ga.estimate_F(xa, xb, _words(256, 22), ga.GaParams(confidence=1.0))
+    assert info[4] == 256                                        # no early stop
+    xa, xb, F = _views(75, seed=23)
+    oa, ob = _outliers(F, 25, np.random.default_rng(24))
+    w = _words(256, 25)
+    w[0] = [_word(k, 100 - k) for k in range(8)]                 # hypothesis 0 draws inliers only
+    _, info = ga.estimate_F(np.concatenate([xa, oa]), np.concatenate([xb, ob]), w, ga.GaParams())
+    assert info[1] == 75 and info[4] == 64                       # 0.0341 after 32, 0.00116 after 64
+    xa, xb, F = _views(50, seed=26)
+    oa, ob = _outliers(F, 50, np.random.default_rng(27))
+    _, info = ga.estimate_F(np.concatenate([xa, oa]), np.concatenate([xb, ob]), _words(256, 28), ga.GaParams())
+    assert info[4] == 256                                        # w <= 1/2 never stops within 256

@@ -76,6 +76,9 @@ GA_MUTANTS = {
     "selection ties to the higher index": ("np.lexsort((np.arange(n), -s.astype(np.float64)))",
                                            "np.lexsort((-np.arange(n), -s.astype(np.float64)))"),
     "subset size rounded down": ("k = (n * pct + 99) // 100", "k = (n * pct) // 100"),
+    "stop rule with w^6": ("base = 1.0 - w4 * w4", "base = 1.0 - w4 * w2"),
+    "stop rule on the hypotheses before the batch": ("ransac_stop(best, m, done, gp.confidence)",
+                                                     "ransac_stop(best, m, done - BATCH, gp.confidence)"),
 }
 
 
