@@ -650,7 +650,7 @@ def run_ga(args):
             "vs_baseline": None, "dtype": "u8/bf16+f64fix, f64 geometry", "data": "synthetic",
             "config": {"workload": wdesc.replace("ground-truth F", "F estimated by the first stage (Ga-CasHash)"),
                        "pairs": P, "features": int(s.desc.shape[0]),
-                       "ga": {"stage1_kernel": args.ga_kernel, "top_pct": gp.top_pct, "min_matches": gp.min_matches, "n_hyp": gp.n_hyp,
+                       "ga": {"stage1_kernel": args.ga_kernel, "confidence": gp.confidence, "top_pct": gp.top_pct, "min_matches": gp.min_matches, "n_hyp": gp.n_hyp,
                               "accept": "%d/%d inliers" % (gp.inlier_num, gp.inlier_den),
                               "thresh_px": gp.thresh_px},
                        "l2": "flushed: 256 MiB write before every step"},
@@ -658,6 +658,7 @@ def run_ga(args):
                           "stage2_match_kernel": st["match"], "stage2_fallback": st["fallback"]},
             "ga": {"pairs_with_F": int((info[:, 2] != 0xFFFFFFFF).sum()), "accepted": int(len(acc)),
                    "stage1_matches_median": float(np.median(info[:, 0])),
+                   "hypotheses_run_mean": float(np.mean(info[:, 4])),
                    "inlier_ratio_median": float(np.median(info[acc, 1] / np.maximum(info[acc, 0], 1)))
                    if len(acc) else None,
                    "cos_F_est_gt_median": float(np.median(cosang)) if len(cosang) else None,
@@ -674,7 +675,7 @@ def run_ga(args):
 def oga_params(gp):
     from oracle import ga as oga
     return oga.GaParams(top_pct=gp.top_pct, min_matches=gp.min_matches, n_hyp=gp.n_hyp, inlier_num=gp.inlier_num,
-                        inlier_den=gp.inlier_den, thresh_px=gp.thresh_px)
+                        inlier_den=gp.inlier_den, thresh_px=gp.thresh_px, confidence=gp.confidence)
 
 
 def main():

@@ -375,13 +375,17 @@ const char* cashash_strerror(int status);
 typedef struct {
   uint32_t top_pct;      /* 20: each image keeps ceil(n * top_pct / 100) features (1..100) */
   uint32_t min_matches;  /* 16: pairs with fewer stage-1 matches get no F (>= 8) */
-  uint32_t n_hyp;        /* 256: RANSAC hypotheses per pair (1..CASHASH_GA_MAX_HYP) */
+  uint32_t n_hyp;        /* 256: at most this many RANSAC hypotheses per pair (1..CASHASH_GA_MAX_HYP) */
   uint32_t inlier_num;   /* 2 */
   uint32_t inlier_den;   /* 3: accepted when inlier_den * inliers >= inlier_num * matches */
   uint32_t kernel;       /* 0: matching kernel of the subsets chosen by their size (the per-query
                             kernel when the mean subset image has fewer than 4096 features, else
                             the join); CASHASH_KERNEL_JOIN / CASHASH_KERNEL_QUERY force one */
   double thresh_px;      /* 3.0: inlier when the Sampson distance is <= thresh_px pixels */
+  double confidence;     /* 0.99: hypotheses run in batches of 32; after a batch RANSAC stops when
+                            (1 - w^8)^N <= 1 - confidence (Hartley and Zisserman, Algorithm 4.5;
+                            N hypotheses done, w the best inlier fraction so far, each step one
+                            correctly rounded double operation); >= 1: all n_hyp run */
 } cashash_ga_params;
 
 typedef struct {
@@ -389,6 +393,8 @@ typedef struct {
   uint32_t n_inliers;    /* inliers of the returned F (0 when there is none) */
   uint32_t best_hyp;     /* winning hypothesis, or 0xFFFFFFFF */
   uint32_t accepted;     /* 1: the pair goes on to guided matching with F */
+  uint32_t n_evaluated;  /* hypotheses run (a multiple of 32, or n_hyp) */
+  uint32_t reserved[3];
 } cashash_ga_info;
 
 /* Fills gp with the defaults listed above. */

@@ -64,7 +64,7 @@ class cashash_tuning(C.Structure):
 class cashash_ga_params(C.Structure):
     _fields_ = [("top_pct", C.c_uint32), ("min_matches", C.c_uint32), ("n_hyp", C.c_uint32),
                 ("inlier_num", C.c_uint32), ("inlier_den", C.c_uint32), ("kernel", C.c_uint32),
-                ("thresh_px", C.c_double)]
+                ("thresh_px", C.c_double), ("confidence", C.c_double)]
 
 
 GA_MAX_HYP = 4096
@@ -452,14 +452,14 @@ def cashash_ga_select(scale, img_off: np.ndarray, top_pct: int, stream=None):
 def _ga_out(P: int, device):
     import torch
     F = torch.empty((max(P, 1), 9), dtype=torch.float64, device=device)
-    info = torch.empty((max(P, 1), 4), dtype=torch.int32, device=device)
+    info = torch.empty((max(P, 1), 8), dtype=torch.int32, device=device)  # cashash_ga_info
     return F, info
 
 
 def cashash_estimate_F(kpts, img_off: np.ndarray, pairs, match_off, matches, words, gp: cashash_ga_params = None,
                        stream=None):
-    """F [P][9] (float64) and info [P][4] (int32: n_matches, n_inliers, best_hyp,
-    accepted) on the device, from the match lists of cashash_match_plan."""
+    """F [P][9] (float64) and info [P][5] (int32: n_matches, n_inliers, best_hyp,
+    accepted, hypotheses run) on the device, from the match lists of cashash_match_plan."""
     gp = gp or cashash_ga_default_params()
     off = np.ascontiguousarray(img_off, np.uint64)
     pr = np.ascontiguousarray(pairs, np.uint32).reshape(-1, 2)
@@ -468,13 +468,13 @@ def cashash_estimate_F(kpts, img_off: np.ndarray, pairs, match_off, matches, wor
     _check(_load().cashash_estimate_F(_dptr(kpts), _hptr(off), len(off) - 1, _hptr(pr), P, _dptr(match_off),
                                       _dptr(matches), C.byref(gp), _dptr(words), _dptr(F), _dptr(info),
                                       _stream(stream)), "cashash_estimate_F")
-    return F[:P], info[:P]
+    return F[:P], info[:P, :5]
 
 
 def cashash_ga_stage1(ctx: Context, dset: DeviceSet, scale, mean: np.ndarray, pairs, words,
                       gp: cashash_ga_params = None, stream=None):
     """Selection, stage-1 CasHash matching of the subsets and F estimation;
-    returns (F [P][9], info [P][4]) on the device."""
+    returns (F [P][9], info [P][5]) on the device."""
     gp = gp or cashash_ga_default_params()
     pr = np.ascontiguousarray(pairs, np.uint32).reshape(-1, 2)
     P = len(pr)
@@ -483,4 +483,4 @@ def cashash_ga_stage1(ctx: Context, dset: DeviceSet, scale, mean: np.ndarray, pa
     _check(_load().cashash_ga_stage1(ctx.handle, C.byref(dset.c), _dptr(scale), _hptr(m), _hptr(pr), P,
                                      C.byref(gp), _dptr(words), _dptr(F), _dptr(info), _stream(stream)),
            "cashash_ga_stage1")
-    return F[:P], info[:P]
+    return F[:P], info[:P, :5]

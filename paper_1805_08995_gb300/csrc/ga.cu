@@ -17,10 +17,11 @@
 //                 key (4 passes of 8 bits), then a stable compaction in
 //                 feature order (ties to the lower index);
 //   k_ga_gather   subset descriptors and key-points;
-//   k_ga_ransac   one CTA per pair: Hartley normalisation (block sums), one
-//                 hypothesis per thread (8 x 9 elimination with partial
-//                 pivoting for the null vector, rank 2 by a one-sided Jacobi
-//                 SVD of the 3 x 3, inlier count), block argmax, refit from
+//   k_ga_ransac   one warp per pair: Hartley normalisation (warp sums),
+//                 hypotheses in batches of 32, one per lane (8 x 9
+//                 elimination with partial pivoting for the null vector, rank
+//                 2 by a one-sided Jacobi SVD of the 3 x 3, inlier count),
+//                 warp argmax, the adaptive stop after each batch, refit from
 //                 the 9 x 9 normal matrix (inverse iteration on its Cholesky
 //                 factor), final count.  The
 //                 inlier test runs in FP32 with a rounding bound and falls
@@ -155,22 +156,11 @@ struct GaArgs {
   float4* pts32;        // the same in FP32 (exact: key-points are FP32)
   uint8_t* inl;            // [total matches] scratch
   double* F;               // [P][9] out
-  uint4* info;             // [P] out
+  uint4* info;             // [P][2] out: (matches, inliers, best, accepted), (evaluated, 0, 0, 0)
   uint32_t P, n_hyp, min_matches, num, den;
-  double t2, thresh;
+  double t2, thresh, conf;
 };
 
-__device__ double block_sum(double v, double* s_d) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-  if (lane == 0) s_d[w] = v;
-  __syncthreads();
-  double t = 0.0;
-  for (int k = 0; k < GA_T / 32; ++k) t += s_d[k];
-  __syncthreads();
-  return t;
-}
 
 // Squared Sampson distance <= t2 (x_B^T F x_A = 0).
 __host__ __device__ __forceinline__ bool ga_inlier(const double* F, const GaPt p, double t2) {
@@ -433,19 +423,49 @@ __host__ __device__ void smallest_eigvec9(const double* M, double* L, double* x)
   }
 }
 
-__global__ void __launch_bounds__(GA_T, 2) k_ga_ransac(GaArgs a) {
-  __shared__ double s_d[GA_T / 32];
-  __shared__ uint32_t s_best[GA_T / 32][2];
-  __shared__ double s_F[9], s_M[45], s_Mf[81], s_L[81], s_x[9];
-  __shared__ double s_hF[GA_T][9], s_hf[GA_T][9];  // each thread's best hypothesis: F and its null vector
-  __shared__ uint32_t s_bh;
-  const uint32_t p = blockIdx.x, tid = threadIdx.x;
+constexpr uint32_t GA_BATCH = 32;  // hypotheses per check of the adaptive stop: one per lane
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+  return v;
+}
+
+// Adaptive stop (Hartley and Zisserman, Algorithm 4.5): (1 - w^8)^done <=
+// 1 - confidence with w = best / m, every step one correctly rounded double
+// operation in a fixed order (three squarings, binary exponentiation), so the
+// decision is the same wherever it is evaluated.  confidence >= 1: never.
+__device__ bool ga_stop(uint32_t best, uint32_t m, uint32_t done, double conf) {
+  if (!(conf < 1.0)) return false;
+  const double w = __ddiv_rn((double)best, (double)m);
+  const double w2 = __dmul_rn(w, w), w4 = __dmul_rn(w2, w2);
+  double base = __dsub_rn(1.0, __dmul_rn(w4, w4)), r = 1.0;
+  for (uint32_t e = done; e; e >>= 1) {
+    if (e & 1u) r = __dmul_rn(r, base);
+    base = __dmul_rn(base, base);
+  }
+  return r <= __dsub_rn(1.0, conf);
+}
+
+__device__ __forceinline__ void ga_write_info(const GaArgs& a, uint32_t p, uint32_t m, uint32_t n_in, uint32_t bh,
+                                              uint32_t acc, uint32_t done) {
+  a.info[2 * (size_t)p] = make_uint4(m, n_in, bh, acc);
+  a.info[2 * (size_t)p + 1] = make_uint4(done, 0u, 0u, 0u);
+}
+
+// One warp per pair: hypotheses in batches of 32 (one per lane) until the
+// adaptive stop holds or n_hyp are done; the most inliers win, ties to the
+// lower hypothesis (a later batch replaces the best only with more inliers).
+__global__ void __launch_bounds__(32, 16) k_ga_ransac(GaArgs a) {
+  __shared__ double s_hF[32][9], s_hf[32][9];  // the batch's hypotheses: F and the null vector
+  __shared__ double s_F[9], s_x[9], s_M[45], s_Mf[81], s_L[81];
+  const uint32_t p = blockIdx.x, lane = threadIdx.x;
   const uint64_t m0 = a.moff[p];
   const uint32_t m = (uint32_t)(a.moff[p + 1] - m0);
   double* Fout = a.F + 9 * (size_t)p;
   if (m < a.min_matches) {
-    if (tid < 9) Fout[tid] = 0.0;
-    if (tid == 0) a.info[p] = make_uint4(m, 0u, GA_NONE, 0u);
+    if (lane < 9) Fout[lane] = 0.0;
+    if (lane == 0) ga_write_info(a, p, m, 0u, GA_NONE, 0u, 0u);
     return;
   }
   const uint32_t ia = a.pairs[2 * p], ib = a.pairs[2 * p + 1];
@@ -455,7 +475,7 @@ __global__ void __launch_bounds__(GA_T, 2) k_ga_ransac(GaArgs a) {
   float4* pts32 = a.pts32 + m0;
   uint8_t* inl = a.inl + m0;
   double sxa = 0.0, sya = 0.0, sxb = 0.0, syb = 0.0;
-  for (uint32_t i = tid; i < m; i += GA_T) {
+  for (uint32_t i = lane; i < m; i += 32) {
     const uint32_t qa = a.mt[2 * (m0 + i)], jb = a.mt[2 * (m0 + i) + 1];
     // indices outside the images (never written by the matcher) read as (0, 0)
     const float2 pa = qa < nA ? a.kpts[A0 + qa] : make_float2(0.f, 0.f);
@@ -468,73 +488,60 @@ __global__ void __launch_bounds__(GA_T, 2) k_ga_ransac(GaArgs a) {
     sxb += q.z;
     syb += q.w;
   }
-  const double cxa = block_sum(sxa, s_d) / m, cya = block_sum(sya, s_d) / m;
-  const double cxb = block_sum(sxb, s_d) / m, cyb = block_sum(syb, s_d) / m;
-  __syncthreads();  // pts visible to the whole CTA
+  const double cxa = warp_sum(sxa) / m, cya = warp_sum(sya) / m;
+  const double cxb = warp_sum(sxb) / m, cyb = warp_sum(syb) / m;
+  __syncwarp();  // pts visible to the whole warp
   double da = 0.0, db = 0.0;
-  for (uint32_t i = tid; i < m; i += GA_T) {
+  for (uint32_t i = lane; i < m; i += 32) {
     const GaPt q = pts[i];
     da += sqrt((q.x - cxa) * (q.x - cxa) + (q.y - cya) * (q.y - cya));
     db += sqrt((q.z - cxb) * (q.z - cxb) + (q.w - cyb) * (q.w - cyb));
   }
-  const double sa = sqrt(2.0) / (block_sum(da, s_d) / m), sb = sqrt(2.0) / (block_sum(db, s_d) / m);
+  const double sa = sqrt(2.0) / (warp_sum(da) / m), sb = sqrt(2.0) / (warp_sum(db) / m);
   const double Ta[3] = {sa, -sa * cxa, -sa * cya}, Tb[3] = {sb, -sb * cxb, -sb * cyb};  // s, -s cx, -s cy
 
-  // hypotheses: thread h takes h, h + GA_T, ...; the most inliers win, ties to the lower h
-  uint32_t best_c = 0, best_h = GA_NONE;
-  for (uint32_t h = tid; h < a.n_hyp; h += GA_T) {
-    double F[9], fn[9];
-    if (!hypothesis(pts, m, a.words + ((size_t)p * a.n_hyp + h) * 8, Ta, Tb, F, fn)) continue;
-    GaF32 g;
-    ga_f32(F, a.thresh, g);
-    uint32_t c = 0;
-    for (uint32_t i = 0; i < m; ++i) c += ga_inlier_fast(g, pts32[i], F, pts[i], a.t2) ? 1u : 0u;
-    if (best_h == GA_NONE || c > best_c) {
-      best_c = c;
-      best_h = h;
-      for (int e = 0; e < 9; ++e) {
-        s_hF[tid][e] = F[e];
-        s_hf[tid][e] = fn[e];
-      }
-    }
-  }
-  {  // CTA argmax: key (count, -h), invalid lowest
-    const int lane = tid & 31, w = tid >> 5;
-    for (int o = 16; o > 0; o >>= 1) {
-      const uint32_t oc = __shfl_xor_sync(0xFFFFFFFFu, best_c, o), oh = __shfl_xor_sync(0xFFFFFFFFu, best_h, o);
-      const bool better = oh != GA_NONE && (best_h == GA_NONE || oc > best_c || (oc == best_c && oh < best_h));
-      if (better) {
-        best_c = oc;
-        best_h = oh;
-      }
-    }
-    if (lane == 0) {
-      s_best[w][0] = best_c;
-      s_best[w][1] = best_h;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      uint32_t bc = 0, bh = GA_NONE;
-      for (int k = 0; k < GA_T / 32; ++k) {
-        const uint32_t oc = s_best[k][0], oh = s_best[k][1];
-        if (oh != GA_NONE && (bh == GA_NONE || oc > bc || (oc == bc && oh < bh))) {
-          bc = oc;
-          bh = oh;
-        }
-      }
-      s_bh = bh;
-      if (bh != GA_NONE)  // hypothesis bh was the best of thread bh % GA_T
+  uint32_t best_c = 0, best_h = GA_NONE, done = 0;  // warp-uniform
+  while (done < a.n_hyp) {
+    const uint32_t h = done + lane;
+    uint32_t c = 0, bh = GA_NONE;
+    if (h < a.n_hyp) {
+      double F[9], fn[9];
+      if (hypothesis(pts, m, a.words + ((size_t)p * a.n_hyp + h) * 8, Ta, Tb, F, fn)) {
+        GaF32 g;
+        ga_f32(F, a.thresh, g);
+        for (uint32_t i = 0; i < m; ++i) c += ga_inlier_fast(g, pts32[i], F, pts[i], a.t2) ? 1u : 0u;
         for (int e = 0; e < 9; ++e) {
-          s_F[e] = s_hF[bh % GA_T][e];
-          s_x[e] = s_hf[bh % GA_T][e];
+          s_hF[lane][e] = F[e];
+          s_hf[lane][e] = fn[e];
         }
+        bh = h;
+      }
     }
-    __syncthreads();
+    // the batch's winner (a total order: valid first, more inliers, lower h), on every lane
+    uint32_t bc = c;
+    for (int o = 16; o > 0; o >>= 1) {
+      const uint32_t oc = __shfl_xor_sync(0xFFFFFFFFu, bc, o), oh = __shfl_xor_sync(0xFFFFFFFFu, bh, o);
+      if (oh != GA_NONE && (bh == GA_NONE || oc > bc || (oc == bc && oh < bh))) {
+        bc = oc;
+        bh = oh;
+      }
+    }
+    __syncwarp();  // the batch's hypotheses are in shared memory
+    if (bh != GA_NONE && (best_h == GA_NONE || bc > best_c)) {
+      best_c = bc;
+      best_h = bh;
+      if (lane < 9) {
+        s_F[lane] = s_hF[bh - done][lane];
+        s_x[lane] = s_hf[bh - done][lane];
+      }
+    }
+    __syncwarp();
+    done = min(done + GA_BATCH, a.n_hyp);
+    if (best_h != GA_NONE && ga_stop(best_c, m, done, a.conf)) break;
   }
-  const uint32_t bh = s_bh;
-  if (bh == GA_NONE) {
-    if (tid < 9) Fout[tid] = 0.0;
-    if (tid == 0) a.info[p] = make_uint4(m, 0u, GA_NONE, 0u);
+  if (best_h == GA_NONE) {
+    if (lane < 9) Fout[lane] = 0.0;
+    if (lane == 0) ga_write_info(a, p, m, 0u, GA_NONE, 0u, done);
     return;
   }
   double F[9];
@@ -542,19 +549,17 @@ __global__ void __launch_bounds__(GA_T, 2) k_ga_ransac(GaArgs a) {
   uint32_t cnt_local = 0;
   GaF32 g;
   ga_f32(F, a.thresh, g);
-  for (uint32_t i = tid; i < m; i += GA_T) {
+  for (uint32_t i = lane; i < m; i += 32) {
     const bool in = ga_inlier_fast(g, pts32[i], F, pts[i], a.t2);
     inl[i] = in ? 1 : 0;
     cnt_local += in ? 1u : 0u;
   }
-  const uint32_t n_best = (uint32_t)block_sum((double)cnt_local, s_d);
-  __syncthreads();  // inlier flags visible
+  const uint32_t n_best = __reduce_add_sync(0xFFFFFFFFu, cnt_local);
+  __syncwarp();  // inlier flags visible
   if (n_best >= 8) {
-    // normal matrix of the inliers' design rows, entries (r, c), r <= c: group g of 45 threads
-    // sums the matches i = g, g + 5, ... in order, then the five partial sums are added in group order
-    __shared__ double s_part[5][45];
-    if (tid < 225) {
-      const uint32_t grp5 = tid / 45, ent = tid % 45;
+    // normal matrix of the inliers' design rows: lane l sums entries l and l + 32 ((r, c), r <= c,
+    // row-major over the upper triangle) over the matches in order
+    for (uint32_t ent = lane; ent < 45; ent += 32) {
       uint32_t r = 0, t = ent;
       while (t >= 9 - r) {
         t -= 9 - r;
@@ -562,18 +567,16 @@ __global__ void __launch_bounds__(GA_T, 2) k_ga_ransac(GaArgs a) {
       }
       const uint32_t c = r + t;
       double sum = 0.0;
-      for (uint32_t i = grp5; i < m; i += 5) {
+      for (uint32_t i = 0; i < m; ++i) {
         if (!inl[i]) continue;
         double row[9];
         design_row(pts[i], Ta, Tb, row);
         sum += row[r] * row[c];
       }
-      s_part[grp5][ent] = sum;
+      s_M[ent] = sum;
     }
-    __syncthreads();
-    if (tid < 45) s_M[tid] = (((s_part[0][tid] + s_part[1][tid]) + s_part[2][tid]) + s_part[3][tid]) + s_part[4][tid];
-    __syncthreads();
-    if (tid == 0) {
+    __syncwarp();
+    if (lane == 0) {
       double f[9];
       for (uint32_t r = 0, e = 0; r < 9; ++r)
         for (uint32_t c = r; c < 9; ++c, ++e) s_Mf[9 * r + c] = s_Mf[9 * c + r] = s_M[e];
@@ -582,7 +585,7 @@ __global__ void __launch_bounds__(GA_T, 2) k_ga_ransac(GaArgs a) {
       rank2(f);
       denormalise(f, Ta, Tb, s_F);
     }
-    __syncthreads();
+    __syncwarp();
     for (int e = 0; e < 9; ++e) F[e] = s_F[e];
   }
   // unit Frobenius norm, largest-magnitude entry (first on ties) positive
@@ -599,11 +602,10 @@ __global__ void __launch_bounds__(GA_T, 2) k_ga_ransac(GaArgs a) {
   for (int e = 0; e < 9; ++e) F[e] *= sc;
   uint32_t c2 = 0;
   ga_f32(F, a.thresh, g);
-  for (uint32_t i = tid; i < m; i += GA_T) c2 += ga_inlier_fast(g, pts32[i], F, pts[i], a.t2) ? 1u : 0u;
-  const uint32_t n_in = (uint32_t)block_sum((double)c2, s_d);
-  if (tid < 9) Fout[tid] = F[tid];
-  if (tid == 0)
-    a.info[p] = make_uint4(m, n_in, bh, (uint64_t)a.den * n_in >= (uint64_t)a.num * m ? 1u : 0u);
+  for (uint32_t i = lane; i < m; i += 32) c2 += ga_inlier_fast(g, pts32[i], F, pts[i], a.t2) ? 1u : 0u;
+  const uint32_t n_in = __reduce_add_sync(0xFFFFFFFFu, c2);
+  if (lane < 9) Fout[lane] = F[lane];
+  if (lane == 0) ga_write_info(a, p, m, n_in, best_h, (uint64_t)a.den * n_in >= (uint64_t)a.num * m ? 1u : 0u, done);
 }
 
 }  // namespace chx
@@ -620,7 +622,8 @@ int err_of(cudaError_t e) {
 bool ga_params_ok(const cashash_ga_params* gp) {
   return gp && gp->top_pct >= 1 && gp->top_pct <= 100 && gp->min_matches >= 8 && gp->n_hyp >= 1 &&
          gp->n_hyp <= CASHASH_GA_MAX_HYP && gp->inlier_den >= 1 && gp->inlier_num <= gp->inlier_den &&
-         gp->thresh_px > 0.0 && gp->thresh_px < 1e150 && gp->kernel <= CASHASH_KERNEL_QUERY;
+         gp->thresh_px > 0.0 && gp->thresh_px < 1e150 && gp->kernel <= CASHASH_KERNEL_QUERY &&
+         gp->confidence >= 0.0;
 }
 
 // Device scratch released at the end of a call (stream-ordered).
@@ -653,6 +656,7 @@ extern "C" void cashash_ga_default_params(cashash_ga_params* gp) {
   gp->inlier_den = 3;
   gp->kernel = 0;
   gp->thresh_px = 3.0;
+  gp->confidence = 0.99;
 }
 
 extern "C" int cashash_ga_subset_offsets(const uint64_t* img_off, uint32_t n_images, uint32_t top_pct,
@@ -743,7 +747,8 @@ extern "C" int cashash_estimate_F(const float* kpts, const uint64_t* img_off, ui
   a.den = gp->inlier_den;
   a.t2 = gp->thresh_px * gp->thresh_px;
   a.thresh = gp->thresh_px;
-  k_ga_ransac<<<P, GA_T, 0, s>>>(a);
+  a.conf = gp->confidence;
+  k_ga_ransac<<<P, 32, 0, s>>>(a);
   return err_of(cudaGetLastError());
 }
 

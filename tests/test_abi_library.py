@@ -150,7 +150,8 @@ def test_ga_calls_check_arguments_on_the_host(lib):
     import paper_1805_08995_gb300 as ch
     L = ch._load()
     g = ch.cashash_ga_default_params()
-    assert (g.top_pct, g.min_matches, g.n_hyp, g.inlier_num, g.inlier_den, g.thresh_px) == (20, 16, 256, 2, 3, 3.0)
+    assert (g.top_pct, g.min_matches, g.n_hyp, g.inlier_num, g.inlier_den, g.thresh_px, g.confidence) == \
+        (20, 16, 256, 2, 3, 3.0, 0.99)
     assert ch.cashash_ga_subset_offsets(np.array([0, 0, 1, 5, 105, 1105], np.uint64), 20).tolist() == \
         [0, 0, 1, 2, 22, 222]
     assert ch.cashash_ga_subset_offsets(np.array([0, 7], np.uint64), 100).tolist() == [0, 7]
@@ -165,7 +166,8 @@ def test_ga_calls_check_arguments_on_the_host(lib):
     assert L.cashash_ga_select(None, None, 0, 20, None, None) == ch.CASHASH_OK      # nothing to do
     pairs = np.array([[0, 1]], np.uint32)
     dummy = C.c_void_p(16)  # never dereferenced: every case fails its checks first
-    for bad in (dict(n_hyp=0), dict(min_matches=3), dict(inlier_num=5, inlier_den=4), dict(thresh_px=-1.0)):
+    for bad in (dict(n_hyp=0), dict(min_matches=3), dict(inlier_num=5, inlier_den=4), dict(thresh_px=-1.0),
+                dict(confidence=-0.5), dict(confidence=float("nan"))):
         gp = ch.cashash_ga_default_params(**bad)
         assert L.cashash_estimate_F(dummy, hp(off), 2, hp(pairs), 1, dummy, dummy, C.byref(gp), dummy, dummy,
                                     dummy, None) == ch.CASHASH_EINVAL

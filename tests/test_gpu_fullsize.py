@@ -206,7 +206,8 @@ def test_config4_ga_stage1_full_size(ch):
     off[1:] = np.cumsum(s.sizes()[imgs])
     pr = np.array([[remap[int(a)], remap[int(b)]] for a, b in s.pairs[pick]], np.uint32)
     ogp = oga.GaParams(top_pct=gp.top_pct, min_matches=gp.min_matches, n_hyp=gp.n_hyp,
-                       inlier_num=gp.inlier_num, inlier_den=gp.inlier_den, thresh_px=gp.thresh_px)
+                       inlier_num=gp.inlier_num, inlier_den=gp.inlier_den, thresh_px=gp.thresh_px,
+                       confidence=gp.confidence)
     eF, einfo, *_ = oga.stage1(s.desc[rows], off, s.kpts[rows], s.scale[rows], mu, s.R, pr, orc.params(), ogp,
                                words[pick])
     assert np.array_equal(info[pick], einfo)

@@ -120,14 +120,15 @@ def test_stage1_rejections_and_small_pairs(ch, oga):
             assert rej and all(einfo[i, 3] == 0 and einfo[i, 0] >= 16 for i in rej)
 
 
-@pytest.mark.parametrize("case", ["one_hypothesis", "thresholds"])
+@pytest.mark.parametrize("case", ["one_hypothesis", "all_hypotheses", "thresholds"])
 def test_estimate_F_parity(ch, oga, case):
     """cashash_estimate_F on the oracle's own stage-1 match lists."""
     import oracle as orc
     s = _epi_set(n_points=30000, n_views=5, seed=46)
     pairs = s.pairs.astype(np.uint32)
-    kw = dict(n_hyp=1) if case == "one_hypothesis" else dict(thresh_px=0.75, inlier_num=9, inlier_den=10,
-                                                              min_matches=40, n_hyp=100)
+    kw = {"one_hypothesis": dict(n_hyp=1), "all_hypotheses": dict(n_hyp=100, confidence=1.0),
+          "thresholds": dict(thresh_px=0.75, inlier_num=9, inlier_den=10, min_matches=40, n_hyp=100,
+                             confidence=0.9999)}[case]
     gp, ogp = _gp(ch, oga, **kw)
     po = orc.params()
     mu = orc.mean(s.desc)
@@ -140,6 +141,8 @@ def test_estimate_F_parity(ch, oga, case):
                                     torch.from_numpy(words.view(np.int32)).cuda(), gp)
     torch.cuda.synchronize()
     _check(F, info, eF, einfo)
+    if case == "all_hypotheses":
+        assert (einfo[einfo[:, 2] != oga.NONE, 4] == 100).all()
     if case == "thresholds":
         assert (einfo[:, 3] == 0).any() or (einfo[:, 0] < 40).any()
 
@@ -154,9 +157,9 @@ def test_stage1_no_pairs_and_bad_args(ch, oga):
     sc = torch.from_numpy(s.scale).cuda()
     w = torch.zeros((1, 256, 8), dtype=torch.int32, device="cuda")
     F, info = ch.cashash_ga_stage1(ctx, ds, sc, mu, np.zeros((0, 2), np.uint32), w)
-    assert F.shape == (0, 9) and info.shape == (0, 4)
+    assert F.shape == (0, 9) and info.shape == (0, 5)
     for bad in (dict(n_hyp=0), dict(n_hyp=ch.GA_MAX_HYP + 1), dict(min_matches=7), dict(top_pct=0),
-                dict(inlier_num=4, inlier_den=3), dict(thresh_px=0.0), dict(kernel=3)):
+                dict(inlier_num=4, inlier_den=3), dict(thresh_px=0.0), dict(kernel=3), dict(confidence=-1.0)):
         with pytest.raises(ch.CashashError) as e:
             ch.cashash_ga_stage1(ctx, ds, sc, mu, s.pairs[:1], w, ch.cashash_ga_default_params(**bad))
         assert e.value.status == ch.CASHASH_EINVAL
