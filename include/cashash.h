@@ -431,8 +431,10 @@ int cashash_estimate_F(const float* kpts, const uint64_t* img_off, uint32_t n_im
  * centre mean_host (HOST [128]: the full set's, e.g. from cashash_get_mean,
  * so stage-1 codes are the full set's codes of the selected features),
  * CasHash matching of the subsets with ctx (which must have epi_px < 0), then
- * cashash_estimate_F.  Work buffers are allocated and released inside; the
- * call synchronises `stream`.  Errors: EINVAL, ENOMEM, ECUDA, EDEVICE. */
+ * cashash_estimate_F.  Work buffers are allocated and released inside
+ * (stream-ordered); the call synchronises `stream` after the subset matching,
+ * and F / info are written asynchronously on it after that.  Errors: EINVAL,
+ * ENOMEM, ECUDA, EDEVICE. */
 int cashash_ga_stage1(cashash_ctx* ctx, const cashash_set* set, const float* scale, const double* mean_host,
                       const uint32_t* pairs, uint32_t P, const cashash_ga_params* gp, const uint32_t* words,
                       double* F, cashash_ga_info* info, cashash_stream_t stream);

@@ -176,21 +176,29 @@ __host__ __device__ __forceinline__ bool ga_inlier(const double* F, const GaPt p
 
 // The same decision from an FP32 evaluation with a rounding bound; returns 1
 // (inlier) or 0 (outlier) when the bound decides, else the FP64 test.  With
-// u = 2^-24, F' = fl32(F), a = (xa, ya, 1), b = (xb, yb, 1), the FP32 values
+// u = 2^-24, F' = fl32(F) (F scaled as above), a = (xa, ya, 1), b = (xb, yb, 1), the FP32 values
 // (nested fmaf) satisfy |r32 - r| <= 6u sum_ij |b_i||F_ij||a_j| for r =
 // b^T F a, and each of F a and F^T b (first two rows) is off by at most
 // 3.1u sum |F||a| (resp. |F^T||b|) per component, so the norm g of the
 // Sampson denominator is off by at most 3.1u (S0 + S1 + T0 + T1) plus 3u g
 // for its own evaluation.  The test |r| <= t g (e = r^2 / g^2 <= t^2) is
 // decided when |r32| +- Er clears t (g32 -+ Eg) with margins 8u / 4u.
+// The Sampson distance does not depend on the scale of F, so F is scaled to
+// max |F_ij| = 1 before rounding (no overflow; entries that round as
+// subnormals lose at most 2^-149 each, covered by the absolute term of the
+// bounds).  A zero or non-finite F gives NaN values, which send every test to
+// FP64.
 struct GaF32 {
-  float f[9], a[9];     // fl32(F) and |fl32(F)|
+  float f[9], a[9];     // fl32(F / max |F|) and its absolute values
   float t_lo, t_hi;     // thresh rounded down / up
 };
 
 __device__ __forceinline__ void ga_f32(const double* F, double thresh, GaF32& g) {
+  double mx = 0.0;
+  for (int e = 0; e < 9; ++e) mx = fmax(mx, fabs(F[e]));
+  const double sc = (mx > 0.0 && mx < 1e308) ? 1.0 / mx : __longlong_as_double(0x7FF8000000000000LL);
   for (int e = 0; e < 9; ++e) {
-    g.f[e] = __double2float_rn(F[e]);
+    g.f[e] = __double2float_rn(F[e] * sc);
     g.a[e] = fabsf(g.f[e]);
   }
   g.t_lo = __double2float_rd(thresh);
@@ -216,8 +224,9 @@ __device__ __forceinline__ bool ga_inlier_fast(const GaF32& g, const float4 q, c
   const float T1 = fmaf(a[1], bx, fmaf(a[4], by, a[7]));
   const float Sr = fmaf(bx, S0, fmaf(by, S1, S2));
   const float gg = sqrtf(fmaf(fx0, fx0, fmaf(fx1, fx1, fmaf(ft0, ft0, ft1 * ft1))));
-  const float Er = 8.f * u * Sr;
-  const float Eg = 4.f * u * (S0 + S1 + T0 + T1 + gg);
+  const float ea = 1.f + ax + ay, eb = 1.f + bx + by;  // subnormal rounding: 1e-36 per unit of |a| |b|
+  const float Er = fmaf(8.f * u, Sr, 1e-36f * ea * eb);
+  const float Eg = fmaf(4.f * u, S0 + S1 + T0 + T1 + gg, 1e-36f * (ea + eb));
   const float ar = fabsf(r);
   if (ar + Er < g.t_lo * (gg - Eg) * (1.f - 4.f * u)) return true;
   if (ar - Er > g.t_hi * (gg + Eg) * (1.f + 4.f * u)) return false;
