@@ -255,12 +255,17 @@ int cashash_run_host(cashash_ctx* ctx, const uint8_t* desc_host, const uint64_t*
                      const float* kpts_host, const uint32_t* pairs_host, uint32_t P, const double* F_host,
                      uint64_t* match_off_host, uint32_t* matches_host, uint64_t cap, uint64_t stage_bytes);
 
-/* Kernel configuration of the plans cashash_run_host builds for batched
- * contexts (t: kernel JOIN or QUERY, tile and ctas_per_sm as for
- * cashash_plan_set_tuning, e.g. the result of cashash_plan_autotune on the
- * same workload), or NULL for the default choice.  Drops the cached plan.
- * Where the join does not apply the default stays.  Errors: EINVAL. */
+/* Kernel configuration of the plans cashash_run_host and
+ * cashash_match_chunked build for batched contexts (t: kernel JOIN or QUERY,
+ * tile and ctas_per_sm as for cashash_plan_set_tuning, e.g. the result of
+ * cashash_plan_autotune on the same workload), or NULL for the default
+ * choice.  Drops run_host's cached plan.  Where the join does not apply the
+ * default stays.  Errors: EINVAL. */
 int cashash_set_host_tuning(cashash_ctx* ctx, const cashash_tuning* t);
+
+/* The configuration set by cashash_set_host_tuning (HOST out; kernel 0 when
+ * none is set).  Errors: EINVAL. */
+int cashash_get_host_tuning(const cashash_ctx* ctx, cashash_tuning* out);
 
 /* Largest query image (features) that cashash_match_pair_noalloc accepts. */
 #define CASHASH_NOALLOC_MAX_QUERIES 65536u

@@ -109,6 +109,7 @@ def _load():
             "cashash_match_chunked": ([vp, P(cashash_set), vp, u64, vp, u32, P(u64), CHUNK_FN, vp, vp], C.c_int),
             "cashash_get_params": ([vp, P(cashash_params)], C.c_int),
             "cashash_set_host_tuning": ([vp, P(cashash_tuning)], C.c_int),
+            "cashash_get_host_tuning": ([vp, P(cashash_tuning)], C.c_int),
             "cashash_ga_default_params": ([P(cashash_ga_params)], None),
             "cashash_ga_subset_offsets": ([vp, u32, u32, vp], C.c_int),
             "cashash_ga_select": ([vp, vp, u32, u32, vp, vp], C.c_int),
@@ -133,7 +134,7 @@ def exported_symbols():
             "cashash_plan_set_threshold_hint", "cashash_plan_get_tuning", "cashash_plan_set_tuning",
             "cashash_plan_autotune", "cashash_match_chunked", "cashash_get_params", "cashash_ga_default_params",
             "cashash_ga_subset_offsets", "cashash_ga_select", "cashash_estimate_F", "cashash_ga_stage1",
-            "cashash_set_host_tuning"]
+            "cashash_set_host_tuning", "cashash_get_host_tuning"]
 
 
 def _check(st, what):
@@ -313,6 +314,12 @@ def cashash_set_host_tuning(ctx: Context, kernel: int = 0, tile: int = 0, ctas_p
         return
     t = cashash_tuning(kernel, tile, ctas_per_sm, 0, -1.0)
     _check(_load().cashash_set_host_tuning(ctx.handle, C.byref(t)), "cashash_set_host_tuning")
+
+
+def cashash_get_host_tuning(ctx: Context) -> dict:
+    t = cashash_tuning()
+    _check(_load().cashash_get_host_tuning(ctx.handle, C.byref(t)), "cashash_get_host_tuning")
+    return {"kernel": t.kernel, "tile": t.tile, "ctas_per_sm": t.ctas_per_sm}
 
 
 def cashash_plan_destroy(plan: Plan):

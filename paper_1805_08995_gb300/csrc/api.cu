@@ -1131,6 +1131,17 @@ int cashash_set_host_tuning(cashash_ctx* c, const cashash_tuning* t) {
   return CASHASH_OK;
 }
 
+int cashash_get_host_tuning(const cashash_ctx* c, cashash_tuning* out) {
+  if (!c || !out) return CASHASH_EINVAL;
+  if (c->hw.has_tune) {
+    *out = c->hw.tune;
+  } else {
+    *out = cashash_tuning{};
+    out->ms_sample = -1.0;
+  }
+  return CASHASH_OK;
+}
+
 int cashash_run_host(cashash_ctx* c, const uint8_t* desc_host, const uint64_t* img_off, uint32_t n_images,
                      const float* kpts_host, const uint32_t* pairs_host, uint32_t P, const double* F_host,
                      uint64_t* match_off_host, uint32_t* matches_host, uint64_t cap, uint64_t stage_bytes) {

@@ -81,7 +81,14 @@ extern "C" int cashash_match_chunked(cashash_ctx* c, const cashash_set* s, const
     cashash_plan* pl = nullptr;
     st = cashash_plan_create(c, s, pr, count, &pl);
     if (st != CASHASH_OK) return st;
-    st = cashash_match_plan(c, pl, F_dev ? F_dev + 9 * first : nullptr, buf.moff_d, buf.mt_d, cap, stream_);
+    cashash_tuning want{}, cur{};
+    if (cashash_get_host_tuning(c, &want) == CASHASH_OK && want.kernel != 0 &&
+        cashash_plan_get_tuning(pl, &cur) == CASHASH_OK && cur.kernel != 0) {  // batched plans only
+      st = cashash_plan_set_tuning(pl, &want);
+      if (st == CASHASH_ENOTSUP) st = CASHASH_OK;  // the join does not apply to this chunk
+    }
+    if (st == CASHASH_OK)
+      st = cashash_match_plan(c, pl, F_dev ? F_dev + 9 * first : nullptr, buf.moff_d, buf.mt_d, cap, stream_);
     if (st == CASHASH_OK) st = cashash_sync_status(c, stream_);
     if (st == CASHASH_OK)
       st = err_of(cudaMemcpyAsync(buf.moff_h, buf.moff_d, ((uint64_t)count + 1) * sizeof(uint64_t),

@@ -179,6 +179,7 @@ def test_ga_calls_check_arguments_on_the_host(lib):
     p = ch.cashash_params()
     assert L.cashash_get_params(None, C.byref(p)) == ch.CASHASH_EINVAL
     assert L.cashash_set_host_tuning(None, None) == ch.CASHASH_EINVAL
+    assert L.cashash_get_host_tuning(None, None) == ch.CASHASH_EINVAL
     assert L.cashash_ga_stage1(None, None, None, None, None, 0, C.byref(gp), None, None, None, None) == \
         ch.CASHASH_EINVAL
 
