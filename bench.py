@@ -315,8 +315,8 @@ def run_ours(args):
     if sched == ch.CASHASH_SCHED_PERSISTENT and not args.no_autotune:
         ch.cashash_build_codes(ctx, ds, stream=stream)  # the tuner matches the set's current codes
         tuning = ch.cashash_plan_autotune(ctx, plan, F=F_dev, max_pairs=0, stream=stream)
-        if args.chunk_pairs:  # the chunks' plans take the tuned configuration
-            ch.cashash_set_host_tuning(ctx, tuning["kernel"], tuning["tile"], tuning["ctas_per_sm"])
+        # (the chunked path keeps its default: each chunk's plan matches once, and the per-query
+        # kernel speculates only from a plan's second launch, while the join calibrates per plan)
     ch.cashash_set_profiling(ctx, True)
     for _ in range(args.warmup):
         flush.zero_()
