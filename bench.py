@@ -315,8 +315,8 @@ def run_ours(args):
     if sched == ch.CASHASH_SCHED_PERSISTENT and not args.no_autotune:
         ch.cashash_build_codes(ctx, ds, stream=stream)  # the tuner matches the set's current codes
         tuning = ch.cashash_plan_autotune(ctx, plan, F=F_dev, max_pairs=0, stream=stream)
-        # (the chunked path keeps its default: each chunk's plan matches once, and the per-query
-        # kernel speculates only from a plan's second launch, while the join calibrates per plan)
+        if args.chunk_pairs:  # the chunks' plans take the tuned configuration
+            ch.cashash_set_host_tuning(ctx, tuning["kernel"], tuning["tile"], tuning["ctas_per_sm"])
     ch.cashash_set_profiling(ctx, True)
     for _ in range(args.warmup):
         flush.zero_()
@@ -378,7 +378,7 @@ def run_ours(args):
     buckets = ds.buckets_np(T)
     entries = lookup_entries(buckets, s.img_off, s.pairs, T, m)
     t_match = statistics.mean(stage_ms["match"]) / 1e3
-    kernel = "k_join" if stage_ms["calibrate"] else "k_match"
+    kernel = "k_join" if tuning.get("kernel") == ch.CASHASH_KERNEL_JOIN else "k_match"
     sm_mhz = pk.get("sm_max_mhz", 2070.0)
     ent_peak = POPC_PER_CLK_SM / 4.0 * N_SM * sm_mhz * 1e6
     ent_rate = entries / t_match

@@ -260,10 +260,7 @@ int cashash_run_host(cashash_ctx* ctx, const uint8_t* desc_host, const uint64_t*
  * tile and ctas_per_sm as for cashash_plan_set_tuning, e.g. the result of
  * cashash_plan_autotune on the same workload), or NULL for the default
  * choice.  Drops run_host's cached plan.  Where the join does not apply the
- * default stays.  The per-query kernel learns its speculation threshold from
- * a plan's earlier launches, so for chunked matching (one launch per chunk
- * plan) the join, which calibrates every new plan, is usually faster.
- * Errors: EINVAL. */
+ * default stays.  Errors: EINVAL. */
 int cashash_set_host_tuning(cashash_ctx* ctx, const cashash_tuning* t);
 
 /* The configuration set by cashash_set_host_tuning (HOST out; kernel 0 when

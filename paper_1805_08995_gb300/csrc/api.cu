@@ -786,7 +786,7 @@ int enqueue_match(cashash_ctx* c, cashash_plan* pl, const double* F_dev, uint64_
     a.items = pl->d_items;
     a.n_items = pl->n_items;
     a.item_ctr = pl->d_item_ctr + P;
-    if (pl->join && c->p.epi_px < 0.0) {
+    if (c->p.epi_px < 0.0) {  // threshold guesses for pairs without one (either kernel)
       StageTimer tm(c, CASHASH_STAGE_CALIBRATE, stream, capturing);
       CK(launch_join_calibrate(a, stream));
     }
@@ -822,8 +822,8 @@ uint64_t match_launches(const cashash_plan* pl) {
   uint64_t n = pl->P ? 2 : 1;  // scan + compaction
   if (pl->P_out != pl->P) n += 1 + (pl->ctx->p.epi_px >= 0.0 ? 1 : 0);  // mutual filter (+ transposed F)
   if (pl->persistent) {
-    // calibration (not with the band) + join, or the speculative kernel; then the fallback
-    const bool cal = pl->join && pl->ctx->p.epi_px < 0.0 && pl->P;
+    // calibration (not with the band), the join or the speculative kernel, then the fallback
+    const bool cal = pl->ctx->p.epi_px < 0.0 && pl->P;
     n += (pl->grid ? (cal ? 2 : 1) : 0) + (pl->n_res ? 1 : 0);
   } else {
     for (uint32_t i = 0; i < pl->P; ++i) n += pl->count[i] ? 1 : 0;
@@ -871,7 +871,7 @@ int cashash_match_plan(cashash_ctx* c, cashash_plan* pl, const double* F_dev, ui
     if (c->profiling)  // the graph holds the stage events as external event-record nodes
       c->ev_used[CASHASH_STAGE_MATCH] = c->ev_used[CASHASH_STAGE_COMPACT] = 1;
       c->ev_used[CASHASH_STAGE_FALLBACK] = 1;
-      if (pl->join && c->p.epi_px < 0.0) c->ev_used[CASHASH_STAGE_CALIBRATE] = 1;
+      if (c->p.epi_px < 0.0) c->ev_used[CASHASH_STAGE_CALIBRATE] = 1;
   } else {
     const int st = enqueue_match(c, pl, F_dev, match_off, matches, cap, stream, false);
     if (st != CASHASH_OK) return st;

@@ -16,9 +16,10 @@
 //    key equal to one already kept;
 //  * speculative (batched): the hot loop only appends keys below a threshold
 //    to the thread's survivor queue in global memory (L2-resident).  The
-//    threshold is learned per pair: the largest k-th Hamming distance any
-//    tile of the pair has produced (kept across launches, so repeated
-//    matching of a pair list speculates from its second launch on); a
+//    threshold is per pair: without the band a plan's first launch starts
+//    from the calibrated guess of k_join_calibrate (sampled queries), and
+//    every launch raises it to the largest k-th Hamming distance any tile of
+//    the pair has produced (kept across launches); a
 //    typical query then keeps about a tenth of its candidates, and the
 //    insertion network runs once per query over the survivors.  Exactness never depends on the guess: a
 //    query whose survivors hold fewer than k distinct keys while some

@@ -176,8 +176,8 @@ def test_batched_kernel_choice(ch, orc, case):
     """The batched schedule runs the tensor-core bucket join by default
     (calibration + join + fallback + scan + compaction = 5 launches; with the
     band no calibration, 4) unless a query image exceeds the join's
-    shared-memory counters; then the speculative per-query kernel (4
-    launches).  Both match the oracle.  A candidate image of more than 65,535
+    shared-memory counters; then the speculative per-query kernel (also
+    calibrated: 5 launches).  Both match the oracle.  A candidate image of more than 65,535
     features takes the join tables' global-scatter builder."""
     import math
     pk = dict(schedule=1)
@@ -204,7 +204,7 @@ def test_batched_kernel_choice(ch, orc, case):
     n0 = ch.cashash_get_stats(ctx)["n_launches"]
     ch.cashash_match_plan(ctx, plan, moff, mt, cap, F=F)
     assert ch.cashash_sync_status(ctx) == ch.CASHASH_OK
-    assert ch.cashash_get_stats(ctx)["n_launches"] - n0 == (4 if case in ("large_image", "band") else 5)
+    assert ch.cashash_get_stats(ctx)["n_launches"] - n0 == (4 if case == "band" else 5)
     kern = ch.cashash_plan_get_tuning(plan)["kernel"]
     assert kern == (ch.CASHASH_KERNEL_QUERY if case == "large_image" else ch.CASHASH_KERNEL_JOIN)
     po = oparams(orc, pk)
