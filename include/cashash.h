@@ -61,7 +61,7 @@ typedef enum {
   CASHASH_EOVERFLOW = 4,  /* match capacity too small; match_off[P] holds the total needed */
   CASHASH_EDEVICE = 5,    /* a kernel recorded an internal error (index out of range) */
   CASHASH_ETIMEOUT = 6,   /* a bounded device or staging wait ran out */
-  CASHASH_ENOTSUP = 7     /* parameter combination not supported by this build */
+  CASHASH_ENOTSUP = 7     /* parameter combination the library does not support */
 } cashash_status;
 
 enum { CASHASH_FP32 = 0, CASHASH_BF16 = 1 };                          /* projection precision form */

@@ -292,7 +292,7 @@ const char* cashash_strerror(int st) {
     case CASHASH_EOVERFLOW: return "match capacity exceeded";
     case CASHASH_EDEVICE: return "device-side error recorded";
     case CASHASH_ETIMEOUT: return "bounded wait timed out";
-    case CASHASH_ENOTSUP: return "not supported by this build";
+    case CASHASH_ENOTSUP: return "not supported by the library";
     default: return "unknown status";
   }
 }
