@@ -606,3 +606,44 @@ def test_stage_profiling_and_graph_replay(ch):
         assert ch.cashash_sync_status(ctx) == ch.CASHASH_OK
         plan.close()
         ctx.close()
+
+
+def test_shards_on_concurrent_streams(ch, orc):
+    """One GPU, two shards of a pair list (the LPT split of shard.py) matched
+    by two contexts on two streams, both queued before either is waited for;
+    the merged lists equal the oracle's for the whole list."""
+    from paper_1805_08995_gb300 import shard
+    sizes = [3000, 2500, 700, 4100, 1800]
+    s = synth.random_set(909, sizes)
+    pairs = _pairs(sizes)
+    p = ch.cashash_default_params(schedule=ch.CASHASH_SCHED_PERSISTENT)
+    ctxs = [ch.cashash_create(p, s.R) for _ in range(2)]
+    ds = ch.DeviceSet(p, s.img_off, s.desc)
+    ch.cashash_build_codes(ctxs[0], ds)
+    torch.cuda.synchronize()
+    streams = [torch.cuda.Stream() for _ in range(2)]
+    runs = []
+    for r in range(2):
+        idx = shard.shard_pairs(pairs, s.img_off, 2, r)
+        plan = ch.cashash_plan_create(ctxs[r], ds, pairs[idx])
+        cap = int(s.sizes()[pairs[idx, 0]].sum())
+        moff = torch.zeros(len(idx) + 1, dtype=torch.int64, device="cuda")
+        mt = torch.zeros((max(cap, 1), 2), dtype=torch.int32, device="cuda")
+        runs.append((idx, plan, moff, mt, cap))
+    for _ in range(2):  # the second round replays both captured graphs concurrently
+        for r, (idx, plan, moff, mt, cap) in enumerate(runs):
+            ch.cashash_match_plan(ctxs[r], plan, moff, mt, cap, stream=streams[r])
+        torch.cuda.synchronize()
+    parts = []
+    for r, (idx, plan, moff, mt, cap) in enumerate(runs):
+        assert ch.cashash_sync_status(ctxs[r], streams[r]) == ch.CASHASH_OK
+        off = moff.cpu().numpy()
+        parts.append((idx, off, mt[:int(off[-1])].cpu().numpy().view(np.uint32)))
+        plan.close()
+    po = orc.params()
+    mu, codes, buckets = oracle_codes(orc, s.desc, s.R, po)
+    eoff, emt = orc.match_pairs(s.desc, s.img_off, codes, buckets, pairs, po)
+    moff, mt = shard.merge_shards(len(pairs), parts)
+    assert np.array_equal(moff, eoff) and np.array_equal(mt, emt)
+    for c in ctxs:
+        c.close()
