@@ -34,7 +34,6 @@ sys.path.insert(0, ROOT)
 
 METRIC = "image pairs matched/sec (8k x 8k SIFT) on 1 GB300 at bit-exact matches; % HBM roofline"
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}
-N_SM = 152
 POPC_PER_CLK_SM = 16          # 32-bit population counts per clock per SM (measured 15.96)
 L2_FLUSH_BYTES = 256 << 20
 # DRAM traffic per lookup entry of the matching kernel, from the ncu capture
@@ -67,11 +66,16 @@ def peaks():
         return d
 
 
-def workload(name: str, rank: int):
+def workload(name: str, rank: int, precision: str = "bf16"):
+    """The synthetic image set of a named workload and its description.  On
+    the 100-image exhaustive set the plain FP32 projection is config 1 and the
+    BF16 tensor-core projection (with exact re-evaluation) is config 2."""
     import synth
     if name == "config1":
         s = synth.config1(seed=1 + 1000 * rank)
-        desc = "config1: 100 images x U{4000..12000} SIFT-like uint8 descriptors (30%% noisy copies of " \
+        tag = ("config2: BF16 tensor-core projection (exact FP64 re-evaluation under its bound) on the config-1 set"
+               if precision == "bf16" else "config1: plain FP32 projection")
+        desc = tag + ": 100 images x U{4000..12000} SIFT-like uint8 descriptors (30%% noisy copies of " \
                "index-neighbours), all 4950 pairs, seed %d" % (1 + 1000 * rank)
     elif name == "config0":
         s = synth.config0(seed=1000 * rank)
@@ -176,16 +180,18 @@ def oracle_codes_parallel(orc, desc, R, po, mu, threads):
     return codes, buckets
 
 
-def oracle_sample(s, n_pairs: int, seed: int = 0, flags: int = 0):
+def oracle_sample(s, n_pairs: int, seed: int = 0, flags: int = 0, threads: int = 0, tau=None):
     """Times the oracle on a bounded sample: the centre over the whole set,
     codes for the features of the images the sampled pairs touch, and the
-    matching of n_pairs random pairs, all host cores.  Extrapolates to the
-    whole job (codes of every feature + every pair, pair cost scaled by
-    N_A * N_B).  Returns (pairs/s, cores, sample text, seconds)."""
+    matching of n_pairs random pairs, on `threads` host threads (0 = all
+    cores).  The whole job's time is scaled from the sample (codes by feature
+    count, matching by N_A * N_B).  Returns a dict: pairs/s of the whole job,
+    cores used, a description, the seconds spent, the sampled pair indices
+    and the oracle's lists for them (for the parity check)."""
     import oracle as orc
-    cores = os.cpu_count() or 1
+    cores = threads if threads > 0 else (os.cpu_count() or 1)
     band = s.F is not None
-    po = orc.params(epi_px=4.0, flags=flags) if band else orc.params(flags=flags)
+    po = orc.params(epi_px=4.0 if band else -1.0, flags=flags, tau=tau)
     rng = np.random.default_rng(seed)
     P = len(s.pairs)
     pick = np.sort(rng.choice(P, size=min(n_pairs, P), replace=False))
@@ -208,15 +214,32 @@ def oracle_sample(s, n_pairs: int, seed: int = 0, flags: int = 0):
     if band:
         kw = dict(F=s.F[pick], kpts=np.concatenate([s.kpts[int(s.img_off[i]):int(s.img_off[i + 1])] for i in imgs]))
     t0 = time.perf_counter()
-    orc.match_pairs(sub_desc, sub_off, codes, buckets, sp2, po, n_threads=cores, **kw)
+    eoff, emt = orc.match_pairs(sub_desc, sub_off, codes, buckets, sp2, po, n_threads=cores, **kw)
     t_match = time.perf_counter() - t0
     work_full = float((sizes[s.pairs[:, 0]] * sizes[s.pairs[:, 1]]).sum())
     work_smp = float((sizes[sp[:, 0]] * sizes[sp[:, 1]]).sum())
     job = t_mean + t_hash * (sizes.sum() / max(1, sub_desc.shape[0])) + t_match * (work_full / max(1.0, work_smp))
-    text = ("oracle (C, %d threads): centre over %d features, codes of %d features (%d images), %d of %d pairs "
-            "matched; extrapolated to codes of all %d features + all pairs by feature count and N_A*N_B"
-            % (cores, s.desc.shape[0], sub_desc.shape[0], len(imgs), len(sp), P, s.desc.shape[0]))
-    return P / job, cores, text, t_mean + t_hash + t_match
+    text = ("oracle (C, %d thread%s): centre over %d features, codes of %d features (%d images), %d of %d pairs "
+            "matched; the whole job's time scaled from it (codes by feature count, matching by N_A*N_B)"
+            % (cores, "" if cores == 1 else "s", s.desc.shape[0], sub_desc.shape[0], len(imgs), len(sp), P))
+    return {"pairs_per_s": P / job, "cores": cores, "sample": text, "seconds": t_mean + t_hash + t_match,
+            "job_s": job, "pick": pick, "off": eoff, "mt": emt}
+
+
+def parity_check(smp, moff_dev, mt_dev):
+    """Compares the oracle's lists of the sampled pairs with the GPU lists of
+    the last timed step, entry for entry."""
+    off = moff_dev.cpu().numpy().view(np.uint64)
+    mt = mt_dev[:int(off[-1])].cpu().numpy().view(np.uint32)
+    bad, n_match = 0, 0
+    for k, i in enumerate(smp["pick"]):
+        g = mt[int(off[i]):int(off[i + 1])]
+        e = smp["mt"][int(smp["off"][k]):int(smp["off"][k + 1])]
+        n_match += len(e)
+        if not np.array_equal(g, e):
+            bad += 1
+    return {"pairs_checked": int(len(smp["pick"])), "matches_checked": int(n_match), "mismatches": int(bad),
+            "against": "oracle lists of the cpu_baseline sample vs the GPU lists of the last timed step"}
 
 
 def run_flags(args) -> int:
@@ -225,25 +248,30 @@ def run_flags(args) -> int:
 
 
 def run_reference(args):
+    """The oracle on the machine's host cores.  One step = a bounded sample of
+    the workload (random pairs with the codes of the images they touch);
+    ms_per_step is the oracle's time for that many pairs of the job, i.e. the
+    sample's measured time scaled to average pairs (codes by feature count,
+    matching by N_A * N_B), and value = pairs per step / that time."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    s, wdesc = workload(args.workload, 0)
-    # each step times the oracle on a bounded sample; the --ref-pairs budget is
-    # split over all steps so that the whole run stays within a few minutes
+    s, wdesc = workload(args.workload, 0, args.precision)
+    # the --ref-pairs budget is split over all steps so that the run stays within a few minutes
     sp = max(16, args.ref_pairs // max(1, args.steps + args.warmup))
     times = []
     for i in range(args.warmup + args.steps):
-        v, cores, text, secs = oracle_sample(s, sp, seed=i, flags=run_flags(args))
+        r = oracle_sample(s, sp, seed=i, flags=run_flags(args), tau=args.tau)
         if i >= args.warmup:
-            times.append(len(s.pairs) / v)
-    job = statistics.mean(times)
-    value = len(s.pairs) / job
+            times.append(r["job_s"] * len(r["pick"]) / len(s.pairs))
+    step_s = statistics.mean(times)
+    value = sp / step_s
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": job * 1e3, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8/f64", "data": "synthetic",
-            "config": {"workload": wdesc},
-            "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle", "sample": text},
+            "config": {"workload": wdesc, "pairs_per_step": sp},
+            "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": r["cores"], "kind": "oracle",
+                             "sample": "per step: " + r["sample"]},
             "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -252,6 +280,54 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+
+def roofline_of(ch, p, s, ds, stage_ms, tuning, n_sm):
+    """Roofline of the matching kernel (stage "match", timed alone by its own
+    CUDA events on its launch stream over the timed steps).
+
+    Unit: the lookup-table entries (q, j) that Step 1 visits, counted exactly
+    (sum over pairs and tables of |A_v| * |B_v| over buckets v).  Headline
+    fraction: the bytes the method touches -- per entry the candidate's index
+    and 128-bit code (20 B), per query its k ranked rows, its own row, code,
+    bucket ids and the 6 bucket offsets (1,480 B) -- over the kernel time,
+    against the measured HBM copy bandwidth.  Most of these bytes are served
+    from shared memory and L2, so the fraction can exceed 1; dram_frac is the
+    same kernel's DRAM traffic (ncu) against that bandwidth, and alu_view /
+    tensor_view give the integer and tensor ceilings of the Hamming step."""
+    pk = peaks()
+    T, m = p.n_tables, p.bits_per_table
+    entries = lookup_entries(ds.buckets_np(T), s.img_off, s.pairs, T, m)
+    queries = float(s.sizes()[s.pairs[:, 0]].sum())
+    t_match = statistics.mean(stage_ms["match"]) / 1e3
+    kernel = "k_join" if tuning.get("kernel") == ch.CASHASH_KERNEL_JOIN else "k_match"
+    touched = 20.0 * entries + queries * (p.top_k * 128 + 128 + 16 + 8 + 48)
+    achieved = touched / t_match / 1e9
+    traffic = None
+    prof = PROFILED_TRAFFIC.get(kernel)
+    if prof and prof["sha256"] == source_sha256(prof["source"]):
+        traffic = prof["bytes_per_entry"] * entries
+    sm_mhz = pk.get("sm_max_mhz", 2070.0)
+    ent_peak = POPC_PER_CLK_SM / 4.0 * n_sm * sm_mhz * 1e6
+    ent_rate = entries / t_match
+    fp8_peak = 2.0 * pk["bf16_tflops"] * 1e12  # nominal FP8 / BF16 dense ratio 4.5 / 2.25
+    return {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / pk["hbm_gbs"], "traffic": traffic, "kernel": kernel,
+            "units_per_launch": entries, "unit_def": "lookup-table entries (one 128-bit Hamming each)",
+            "queries_per_launch": queries, "kernel_ms": t_match * 1e3,
+            "bytes_def": "touched bytes: 20 B per entry (index + code) + %d B per query (k rows, query row, "
+                         "code, bucket ids, offsets)" % (p.top_k * 128 + 128 + 16 + 8 + 48),
+            "peak_def": "HBM copy bandwidth (%s)" % pk["source"],
+            "traffic_def": "dram bytes read + written per launch, per-entry figure of an ncu capture "
+                           "scaled by the entries; null when the kernel source differs from the profiled one",
+            "dram_frac": (traffic / t_match / 1e9 / pk["hbm_gbs"]) if traffic else None,
+            "alu_view": {"achieved_gentries_s": ent_rate / 1e9, "peak_gentries_s": ent_peak / 1e9,
+                         "frac": ent_rate / ent_peak,
+                         "note": "CUDA-core Hamming ceiling: 16 POPC/clk/SM / 4 POPC per entry x %d SMs "
+                                 "(queried) x %.0f MHz" % (n_sm, sm_mhz)},
+            "tensor_view": {"achieved_tflops": 256.0 * entries / t_match / 1e12, "peak_tflops": fp8_peak / 1e12,
+                            "frac": 256.0 * entries / t_match / fp8_peak,
+                            "note": "+-1 FP8 contraction, 2 x 128 flop per entry; peak = 2 x measured BF16"}}
+
 
 def run_ours(args):
     import torch
@@ -274,17 +350,33 @@ def run_ours(args):
         dist.barrier()
     ch._load()
 
-    s, wdesc = workload(args.workload, rank)
+    split_pairs = args.split == "pairs" and world > 1
+    # weak scaling: each rank its own image set; pair split: every rank the same set, its share of the pairs
+    s, wdesc = workload(args.workload, 0 if args.split == "pairs" else rank, args.precision)
     if args.max_pairs and args.max_pairs < len(s.pairs):
         # profiling case: the whole image set stays resident, fewer pairs are matched
         s.pairs = s.pairs[:args.max_pairs]
+        if s.F is not None:
+            s.F = s.F[:args.max_pairs]
         wdesc += " (first %d pairs only)" % args.max_pairs
+    P_job = len(s.pairs)
+    if split_pairs:
+        from paper_1805_08995_gb300 import shard as shd
+        mine = shd.shard_pairs(s.pairs, s.img_off, world, rank)
+        s.pairs = s.pairs[mine]
+        if s.F is not None:
+            s.F = s.F[mine]
+        wdesc += " (pairs split over %d ranks by N_A*N_B, LPT)" % world
+    if args.tau is not None:
+        wdesc += ", Hamming threshold tau = %d" % args.tau
     prec = ch.CASHASH_BF16 if args.precision == "bf16" else ch.CASHASH_FP32
     sched = ch.CASHASH_SCHED_PERSISTENT if args.schedule == "persistent" else ch.CASHASH_SCHED_PER_PAIR
     band = s.F is not None
     flags = run_flags(args)
-    p = ch.cashash_default_params(precision=prec, schedule=sched, flags=flags,
-                                  **(dict(epi_px=4.0) if band else {}))
+    pk = dict(epi_px=4.0) if band else {}
+    if args.tau is not None:
+        pk["tau"] = args.tau
+    p = ch.cashash_default_params(precision=prec, schedule=sched, flags=flags, **pk)
     ctx = ch.cashash_create(p, s.R)
     ds = ch.DeviceSet(p, s.img_off, s.desc, s.kpts if band else None)
     plan = ch.cashash_plan_create(ctx, ds, s.pairs)
@@ -366,47 +458,19 @@ def run_ours(args):
         tt = torch.tensor([t_steps], dtype=torch.float64, device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_max = float(tt.item())
-    value = P * world * args.steps / t_max
+    value = (P_job if split_pairs else P * world) * args.steps / t_max
+    rf = roofline_of(ch, p, s, ds, stage_ms, tuning, torch.cuda.get_device_properties(dev).multi_processor_count)
 
-    # dominant kernel: the matching kernel (stage "match" times it alone); its
-    # work counted by the method's lookup entries (Step 1): one 128-bit Hamming
-    # distance each.  Peak: the CUDA-core ceiling of that step, 4 POPC per entry
-    # at 16 POPC/clk/SM; the bucket join computes the distances on the tensor
-    # cores instead (tensor_view) and is limited by its integer ALU / issue work.
-    pk = peaks()
-    T, m = p.n_tables, p.bits_per_table
-    buckets = ds.buckets_np(T)
-    entries = lookup_entries(buckets, s.img_off, s.pairs, T, m)
-    t_match = statistics.mean(stage_ms["match"]) / 1e3
-    kernel = "k_join" if tuning.get("kernel") == ch.CASHASH_KERNEL_JOIN else "k_match"
-    sm_mhz = pk.get("sm_max_mhz", 2070.0)
-    ent_peak = POPC_PER_CLK_SM / 4.0 * N_SM * sm_mhz * 1e6
-    ent_rate = entries / t_match
-    fp8_peak = 2.0 * pk["bf16_tflops"] * 1e12  # nominal FP8 / BF16 dense ratio 4.5 / 2.25
-    traffic = None
-    prof = PROFILED_TRAFFIC.get(kernel)
-    if prof and prof["sha256"] == source_sha256(prof["source"]):
-        traffic = prof["bytes_per_entry"] * entries
-    # touched-bytes view (per query: candidate codes + indices, k rows, query, offsets)
-    touched = 20.0 * entries + float(s.sizes()[s.pairs[:, 0]].sum()) * (10 * 128 + 128 + 16 + 8 + 48)
-    roofline = {"bound": "alu", "achieved": ent_rate / 1e9, "peak": ent_peak / 1e9, "unit": "Gentries/s",
-                "frac": ent_rate / ent_peak, "traffic": traffic, "kernel": kernel,
-                "units_per_launch": entries, "unit_def": "lookup-table entries (one 128-bit Hamming each)",
-                "kernel_ms": t_match * 1e3,
-                "peak_def": "CUDA-core Hamming ceiling: 16 POPC/clk/SM / 4 POPC per entry x 152 SMs x %.0f MHz "
-                            "(sm_max_mhz, %s)" % (sm_mhz, pk["source"]),
-                "traffic_def": "dram bytes read + written per launch, per-entry figure of an ncu capture "
-                               "scaled by the entries; null when the kernel source differs from the profiled one",
-                "tensor_view": {"achieved_tflops": 256.0 * entries / t_match / 1e12,
-                                "peak_tflops": fp8_peak / 1e12,
-                                "frac": 256.0 * entries / t_match / fp8_peak,
-                                "note": "+-1 FP8 contraction, 2 x 128 flop per entry; peak = 2 x measured BF16"},
-                "hbm_view": {"touched_gbs": touched / t_match / 1e9,
-                             "frac_of_hbm": touched / t_match / 1e9 / pk["hbm_gbs"],
-                             "note": "bytes the method touches per query, mostly served from shared memory / L2"}}
+    # stage timers and counters of the chunked path cover the last chunk only: no kernel roofline
+    roofline = None if args.chunk_pairs else rf
+    # parity: the GPU lists of the last timed step, before anything else writes them
+    smp = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        smp = oracle_sample(s, args.ref_pairs, flags=run_flags(args), tau=args.tau)
+    parity = None
+    if smp is not None and not args.chunk_pairs:
+        parity = parity_check(smp, moff, mt)
 
-    if args.chunk_pairs:  # stage timers and counters cover the last chunk only: no kernel roofline
-        roofline = None
     # end-to-end through the C-ABI with host buffers (pinned descriptors)
     e2e = None
     if not args.no_e2e:
@@ -430,32 +494,53 @@ def run_ours(args):
                                                matches=mt_h, kpts=kp_pin, F=s.F if band else None)
             ts.append(time.perf_counter() - t0)
             assert st == ch.CASHASH_OK
+        t_e2e = statistics.mean(ts)
+        if dist:
+            tt = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t_e2e = float(tt.item())
         n_m = int(mo_h[P])
-        e2e = {"value": P / statistics.mean(ts), "unit": "pairs/s", "ms_each": [round(t * 1e3, 2) for t in ts],
+        e2e = {"value": (P_job if split_pairs else P * world) / t_e2e, "unit": "pairs/s",
+               "ms_each": [round(t * 1e3, 2) for t in ts],
                "h2d_bytes_per_step": int(s.desc.nbytes + 8 * (len(s.img_off)) +
                                          (s.kpts.nbytes + s.F.nbytes if band else 0)),
                "d2h_bytes_per_step": int(8 * (P + 1) + 8 * n_m)}
+        if parity is not None:  # the host path's lists of the sampled pairs too
+            e2e["parity_mismatches"] = parity_check(smp, torch.from_numpy(mo_h.view(np.int64)),
+                                                    torch.from_numpy(mt_h.view(np.int32)))["mismatches"]
         ctx2.close()
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, cores, text, secs = oracle_sample(s, args.ref_pairs, flags=run_flags(args))
-        cpu = {"value": v, "unit": "pairs/s", "cores": cores, "kind": "oracle", "sample": text,
-               "seconds": secs}
+    if smp is not None:
+        # the same oracle on one host thread, on a sample sized for a few seconds
+        one = oracle_sample(s, max(8, args.ref_pairs // 16), seed=1, flags=run_flags(args), threads=1,
+                            tau=args.tau)
+        cpu = {"value": smp["pairs_per_s"], "unit": "pairs/s", "cores": smp["cores"], "kind": "oracle",
+               "sample": smp["sample"], "seconds": smp["seconds"],
+               "single_thread": {"value": one["pairs_per_s"], "unit": "pairs/s", "cores": 1,
+                                 "sample": one["sample"], "seconds": one["seconds"]}}
+
+    extra = None
+    if rank == 0 and world == 1 and args.extra_c3 and args.workload == "config1" and not args.chunk_pairs:
+        extra = {"config3": config3_forms(ch, torch, dev)}
 
     if rank == 0:
         stages = {k: (statistics.mean(v) if v else None) for k, v in stage_ms.items()}
         line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None,
+                "scaling": "strong" if split_pairs else "weak", "vs_baseline": None,
                 "dtype": "u8/" + ("bf16" if prec == ch.CASHASH_BF16 else "fp32") + "+f64fix",
                 "data": "synthetic",
                 "config": {"workload": wdesc, "images": int(s.n_images), "features": int(s.desc.shape[0]),
-                           "pairs": P, "precision": args.precision, "schedule": args.schedule,
+                           "pairs": P_job if split_pairs else P, "precision": args.precision,
+                           "schedule": args.schedule,
+                           "split": "pairs (LPT by N_A*N_B, no collective)" if split_pairs else
+                                    ("independent image set per rank" if world > 1 else None),
                            "chunked": ("%d pairs per chunk, lists flushed to pinned host memory per chunk"
                                        % args.chunk_pairs) if args.chunk_pairs else None,
                            "l2": "flushed: 256 MiB write between timed steps (outside the events)",
                            "params": "n=128, 6 tables x 8 bits, k=10, ratio 0.8" + (", band 4 px" if band else "") +
+                                     (", tau %d" % args.tau if args.tau is not None else "") +
                                      (", mutual check" if args.mutual else "") +
                                      (", single candidates accepted" if args.accept_single else ""),
                            "kernel_tuning": {"kernel": {1: "join", 2: "query"}.get(tuning["kernel"], "per_pair"),
@@ -464,13 +549,152 @@ def run_ours(args):
                            "matches_per_step": int(chunk_matches[0] if args.chunk_pairs else stats["n_matches"]),
                            "reevaluated_projections": int(stats["n_reevaluated"])},
                 "features_per_s": s.desc.shape[0] * world * args.steps / t_max,
-                "stages_ms": stages, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "stages_ms": stages, "roofline": roofline, "parity": parity, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": clocks, "wall_s_timed_region": t_wall}
+        if extra:
+            line["extra"] = extra
         print(json.dumps(line))
     ctx.close()
     if dist:
         dist.destroy_process_group()
+    if parity is not None and (parity["mismatches"] or (e2e or {}).get("parity_mismatches")):
+        sys.stderr.write("parity check failed: GPU lists differ from the oracle's\n")
+        return 1
     return 0
+
+
+def config3_forms(ch, torch, dev):
+    """Config 3 (2,000 images, 59,556 pairs) in the two forms its target
+    compares: the batched BF16 form (one persistent launch per step over the
+    device pair list, CUDA-graph captured, autotuned on a sample of pairs) and
+    the plain FP32 form with one launch per pair.  Device time per step with
+    CUDA events, L2 flushed before each step."""
+    import synth
+    s = synth.config3()
+    P = len(s.pairs)
+    cap = int(s.sizes()[s.pairs[:, 0]].sum())
+    moff = torch.zeros(P + 1, dtype=torch.int64, device=dev)
+    mt = torch.zeros((cap, 2), dtype=torch.int32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    out = {"workload": "config3: 2000 images log-uniform 1000..20000 (%d features), 30 neighbours each, "
+                       "%d pairs" % (s.desc.shape[0], P)}
+    forms = (("batched_bf16", ch.CASHASH_BF16, ch.CASHASH_SCHED_PERSISTENT, 3, 5),
+             ("per_pair_fp32", ch.CASHASH_FP32, ch.CASHASH_SCHED_PER_PAIR, 1, 2))
+    for name, prec, sched, warm, steps in forms:
+        p = ch.cashash_default_params(precision=prec, schedule=sched)
+        ctx = ch.cashash_create(p, s.R)
+        ds = ch.DeviceSet(p, s.img_off, s.desc)
+        plan = ch.cashash_plan_create(ctx, ds, s.pairs)
+        tuning = None
+        if sched == ch.CASHASH_SCHED_PERSISTENT:
+            ch.cashash_build_codes(ctx, ds, stream=stream)
+            tuning = ch.cashash_plan_autotune(ctx, plan, max_pairs=8000, stream=stream)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        ms = []
+        for it in range(warm + steps):
+            flush.zero_()
+            e0.record(stream)
+            ch.cashash_build_codes(ctx, ds, stream=stream)
+            ch.cashash_match_plan(ctx, plan, moff, mt, cap, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            if it >= warm:
+                ms.append(e0.elapsed_time(e1))
+        if ch.cashash_sync_status(ctx) != ch.CASHASH_OK:
+            raise SystemExit("device status not OK in the config-3 forms")
+        out[name] = {"pairs_per_s": P / (statistics.mean(ms) / 1e3), "ms_per_step": statistics.mean(ms),
+                     "steps": steps, "warmup": warm, "matches": int(moff[P].item())}
+        if tuning:
+            out[name]["kernel_tuning"] = {"kernel": {1: "join", 2: "query"}.get(tuning["kernel"]),
+                                          "tile": tuning["tile"], "ctas_per_sm": tuning["ctas_per_sm"]}
+        plan.close()
+        ctx.close()
+    out["ratio_batched_over_per_pair"] = out["batched_bf16"]["pairs_per_s"] / out["per_pair_fp32"]["pairs_per_s"]
+    out["same_matches"] = out["batched_bf16"]["matches"] == out["per_pair_fp32"]["matches"]
+    return out
+
+
+def run_tau_sweep(args):
+    """The Hamming threshold tau of the ranking (Sec. 6) swept on the config-1
+    set (BF16 form, batched, autotuned per tau): per tau the device time per
+    step, the matches, the recall of the planted noisy copies (a planted
+    correspondence (q, j) of pair (A, B): q is a copy of B's row j or j a copy
+    of A's row q) and an oracle parity check on sampled pairs.  Prints one
+    JSON line."""
+    import torch
+    import paper_1805_08995_gb300 as ch
+    from paper_1805_08995_gb300 import build as chbuild
+    import synth
+    if int(os.environ.get("WORLD_SIZE", "1")) != 1 or args.gpus != 1:
+        raise SystemExit("--tau-sweep runs on one GPU")
+    torch.cuda.set_device(0)
+    chbuild.build()
+    ch._load()
+    taus = [int(x) for x in args.tau_sweep.split(",") if x.strip()]
+    s, wdesc = workload("config1", 0, "bf16")
+    P = len(s.pairs)
+    cap = int(s.sizes()[s.pairs[:, 0]].sum())
+    dev = torch.device("cuda", 0)
+    moff = torch.zeros(P + 1, dtype=torch.int64, device=dev)
+    mt = torch.zeros((cap, 2), dtype=torch.int32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    planted = synth.planted_pairs(s.truth["copies"], s.pairs)
+    pk_keys = np.array(sorted((i << 48) | (q << 24) | j for i, st in enumerate(planted) for q, j in st), np.int64)
+    rows = []
+    sampler = ClockSampler(0)
+    sampler.start()
+    for tau in taus:
+        p = ch.cashash_default_params(precision=ch.CASHASH_BF16, schedule=ch.CASHASH_SCHED_PERSISTENT, tau=tau)
+        ctx = ch.cashash_create(p, s.R)
+        ds = ch.DeviceSet(p, s.img_off, s.desc)
+        plan = ch.cashash_plan_create(ctx, ds, s.pairs)
+        ch.cashash_build_codes(ctx, ds, stream=stream)
+        tuning = ch.cashash_plan_autotune(ctx, plan, max_pairs=0, stream=stream)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        ms = []
+        for it in range(args.warmup + args.steps):
+            flush.zero_()
+            e0.record(stream)
+            ch.cashash_build_codes(ctx, ds, stream=stream)
+            ch.cashash_match_plan(ctx, plan, moff, mt, cap, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            if it >= args.warmup:
+                ms.append(e0.elapsed_time(e1))
+        if ch.cashash_sync_status(ctx) != ch.CASHASH_OK:
+            raise SystemExit("device status not OK at tau %d" % tau)
+        off = moff.cpu().numpy().view(np.uint64)
+        n = int(off[-1])
+        m = mt[:n].cpu().numpy().view(np.uint32).astype(np.int64)
+        pi = np.repeat(np.arange(P, dtype=np.int64), np.diff(off.astype(np.int64)))
+        keys = (pi << 48) | (m[:, 0] << 24) | m[:, 1]
+        hit = int(np.isin(keys, pk_keys, assume_unique=True).sum())
+        smp = oracle_sample(s, 48, seed=tau, tau=tau)
+        par = parity_check(smp, moff, mt)
+        rows.append({"tau": tau, "pairs_per_s": P / (statistics.mean(ms) / 1e3), "ms_per_step": statistics.mean(ms),
+                     "matches": n, "planted_found": hit, "planted": int(len(pk_keys)),
+                     "recall": hit / max(1, len(pk_keys)), "precision_vs_planted": hit / max(1, n),
+                     "kernel_tuning": {"kernel": {1: "join", 2: "query"}.get(tuning["kernel"]),
+                                       "tile": tuning["tile"], "ctas_per_sm": tuning["ctas_per_sm"]},
+                     "parity": {"pairs_checked": par["pairs_checked"], "mismatches": par["mismatches"]}})
+        plan.close()
+        ctx.close()
+    clocks = sampler.stop()
+    base = next((r for r in rows if r["tau"] >= 128), None)
+    for r in rows:
+        r["recall_vs_tau128"] = r["recall"] / base["recall"] if base else None
+        r["speed_vs_tau128"] = r["pairs_per_s"] / base["pairs_per_s"] if base else None
+    line = {"metric": METRIC, "unit": "pairs/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "data": "synthetic", "dtype": "u8/bf16+f64fix",
+            "config": {"workload": wdesc, "l2": "flushed: 256 MiB write before every timed step",
+                       "recall_def": "planted noisy-copy correspondences found among the matches"},
+            "tau_sweep": rows, "clocks": clocks}
+    print(json.dumps(line))
+    return 1 if any(r["parity"]["mismatches"] for r in rows) else 0
 
 
 # ---------------------------------------------------------------------------
@@ -631,18 +855,12 @@ def run_ga(args):
         same = int(len(np.intersect1d(keys(mt, moff, out["matches"]), keys(mt2, mo2, n_gt))))
     plan.close()
     st = out["stats"]["ms_stage"]
-    # dominant kernel: the guided stage's band join; work = the lookup entries of the accepted pairs
-    pk = peaks()
-    entries = lookup_entries(ds.buckets_np(p2.n_tables), s.img_off, out["pairs2"], p2.n_tables, p2.bits_per_table)
-    t_match = st["match"] / 1e3
-    sm_mhz = pk.get("sm_max_mhz", 2070.0)
-    ent_peak = POPC_PER_CLK_SM / 4.0 * N_SM * sm_mhz * 1e6
-    roofline = {"bound": "alu", "achieved": entries / t_match / 1e9, "peak": ent_peak / 1e9, "unit": "Gentries/s",
-                "frac": entries / t_match / ent_peak, "traffic": None, "kernel": "k_join (band, guided stage)",
-                "units_per_launch": entries, "unit_def": "lookup-table entries (one 128-bit Hamming each)",
-                "kernel_ms": st["match"],
-                "peak_def": "CUDA-core Hamming ceiling: 16 POPC/clk/SM / 4 POPC per entry x 152 SMs x %.0f MHz "
-                            "(sm_max_mhz, %s)" % (sm_mhz, pk["source"])}
+    # dominant kernel: the guided stage's band join over the accepted pairs
+    import types
+    s2 = types.SimpleNamespace(img_off=s.img_off, pairs=out["pairs2"], sizes=s.sizes)
+    roofline = roofline_of(ch, p2, s2, ds, {"match": [st["match"]]}, {"kernel": ch.CASHASH_KERNEL_JOIN},
+                           torch.cuda.get_device_properties(0).multi_processor_count)
+    roofline["kernel"] = "k_join (band, guided stage)"
     cpu = None
     if not args.no_cpu_baseline:
         v, cores, text, secs = oracle_ga_sample(s, max(16, args.ref_pairs // 8), oga_params(gp), words_h)
@@ -698,6 +916,16 @@ def main():
     ap.add_argument("--chunk-pairs", type=int, default=0,
                     help="time the resumable chunked path (cashash_match_chunked) with this many pairs per chunk")
     ap.add_argument("--accept-single", action="store_true", help="a single ranked candidate matches")
+    ap.add_argument("--tau", type=int, default=None,
+                    help="Hamming threshold of the ranking (Sec. 6): candidates above it are dropped; default off")
+    ap.add_argument("--tau-sweep", default="",
+                    help="comma-separated tau values: one line with pairs/s, matches and planted-copy recall per "
+                         "tau on the config-1 set (e.g. 20,30,40,50,60,128)")
+    ap.add_argument("--split", default="images", choices=["images", "pairs"],
+                    help="under torchrun: each rank its own image set (weak scaling) or a share of one "
+                         "workload's pairs (LPT split, strong scaling)")
+    ap.add_argument("--no-extra-c3", dest="extra_c3", action="store_false",
+                    help="skip the config-3 comparison of the batched BF16 form and the one-pair FP32 form")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ga", action="store_true",
@@ -711,6 +939,8 @@ def main():
         return run_reference(args)
     if args.ga:
         return run_ga(args)
+    if args.tau_sweep:
+        return run_tau_sweep(args)
     return run_ours(args)
 
 

@@ -284,16 +284,22 @@ int cashash_get_host_tuning(const cashash_ctx* ctx, cashash_tuning* out);
  * matches as cashash_match_pairs would for that single pair with the same
  * parameters (p->precision and p->schedule are ignored: the codes and lookup
  * tables of `set` must already have been built, e.g. by cashash_build_codes).
+ * p->code_bits, p->n_tables and p->bits_per_table must be the values the
+ * set's codes and tables were built with: the set does not record them, and
+ * other values make the kernel read the tables with the wrong layout.
  *   match_off: DEVICE [2] uint64 out: 0 and the number of matches;
  *   matches:   DEVICE [cap][2] uint32 out: (query index, candidate index),
  *              ascending query index; entries beyond cap are not written, so
  *              match_off[1] > cap means the list was truncated.
  *   F_dev:     DEVICE [9] fundamental matrix when p->epi_px >= 0, else NULL.
- * Asynchronous on `stream`.  The first call on a device (with that device
- * current) looks up the scratch array's device address; make that first call
- * before any stream capture.  Every call shares the one array: calls that
- * overlap on the GPU (other streams, other host threads) race and must be
- * serialised by the caller.
+ * Asynchronous on `stream`.  Every call looks up the scratch array's device
+ * address in the current device's context (this allocates nothing, and stays
+ * right after cudaDeviceReset); the first call on a device may load the
+ * library's device code, so make it before any stream capture.  Every call
+ * shares the one array: calls that overlap on the GPU (other streams, other
+ * host threads) race and must be serialised by the caller.  Device-side
+ * errors (a truncated list, an index out of range) are ORed into the array's
+ * status word by every call and reported by cashash_noalloc_status.
  * Errors: EINVAL (bad parameters or set, image index out of range, or
  * image_a larger than CASHASH_NOALLOC_MAX_QUERIES features), ENOTSUP
  * (CASHASH_FLAG_MUTUAL: the reverse match would need a second scratch),
@@ -301,6 +307,15 @@ int cashash_get_host_tuning(const cashash_ctx* ctx, cashash_tuning* out);
 int cashash_match_pair_noalloc(const cashash_params* p, const cashash_set* set, uint32_t image_a,
                                uint32_t image_b, const double* F_dev, uint64_t* match_off, uint32_t* matches,
                                uint64_t cap, cashash_stream_t stream);
+
+/* Device-side status of the allocation-free calls on the current device:
+ * synchronises `stream` (which must order after those calls), reads the
+ * status word of the shared scratch array and clears it.  Allocates nothing.
+ * Returns OK, EDEVICE (a kernel recorded an index out of range) or EOVERFLOW
+ * (a list was longer than its cap; match_off[1] holds its length), for every
+ * cashash_match_pair_noalloc call since the last cashash_noalloc_status;
+ * ECUDA when a CUDA call fails. */
+int cashash_noalloc_status(cashash_stream_t stream);
 
 /* Resumable chunked matching of long pair lists (out-of-core outputs; the
  * paper has no counterpart, its loader streams inputs).  The callback of one

@@ -151,8 +151,10 @@ def match_pair(descA, codesA, bucketsA, descB, codesB, bucketsB, p=None, F=None,
     return m
 
 
-def match_pairs(desc, img_off, codes, buckets, pairs, p=None, F=None, kpts=None, n_threads=0):
-    """All pairs; returns (match_off[P+1] uint64, matches[M][2] uint32)."""
+def match_pairs(desc, img_off, codes, buckets, pairs, p=None, F=None, kpts=None, n_threads=0, cap=None):
+    """All pairs; returns (match_off[P+1] uint64, matches[M][2] uint32).
+    cap: capacity hint for the match list; when it suffices the oracle runs
+    once, else (or without a hint) it counts first and then fills."""
     p = p or params()
     desc = _c(desc, np.uint8).reshape(-1, DIM)
     img_off = _c(img_off, np.uint64)
@@ -164,6 +166,11 @@ def match_pairs(desc, img_off, codes, buckets, pairs, p=None, F=None, kpts=None,
     lib = _load()
     args = (_ptr(desc), _ptr(img_off), len(img_off) - 1, _ptr(codes), _ptr(buckets),
             _ptr(pairs), P, C.byref(p), _ptr(F), _ptr(kpts))
+    if cap is not None and cap > 0:
+        out = np.zeros((int(cap), 2), np.uint32)
+        total = lib.oracle_match_pairs(*args, _ptr(off), _ptr(out), out.shape[0], int(n_threads))
+        if total >= 0:
+            return off, out[:total]
     total = lib.oracle_match_pairs(*args, _ptr(off), None, 0, int(n_threads))
     if total < 0:
         raise ValueError("oracle_match_pairs rejected its arguments")

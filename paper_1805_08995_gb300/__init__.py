@@ -103,6 +103,7 @@ def _load():
             "cashash_plan_set_threshold_hint": ([vp, u32, C.c_int], C.c_int),
             "cashash_match_pair_noalloc": ([P(cashash_params), P(cashash_set), u32, u32, vp, vp, vp, u64, vp],
                                            C.c_int),
+            "cashash_noalloc_status": ([vp], C.c_int),
             "cashash_plan_get_tuning": ([vp, P(cashash_tuning)], C.c_int),
             "cashash_plan_set_tuning": ([vp, P(cashash_tuning)], C.c_int),
             "cashash_plan_autotune": ([vp, vp, vp, u32, vp], C.c_int),
@@ -134,7 +135,7 @@ def exported_symbols():
             "cashash_plan_set_threshold_hint", "cashash_plan_get_tuning", "cashash_plan_set_tuning",
             "cashash_plan_autotune", "cashash_match_chunked", "cashash_get_params", "cashash_ga_default_params",
             "cashash_ga_subset_offsets", "cashash_ga_select", "cashash_estimate_F", "cashash_ga_stage1",
-            "cashash_set_host_tuning", "cashash_get_host_tuning"]
+            "cashash_set_host_tuning", "cashash_get_host_tuning", "cashash_noalloc_status"]
 
 
 def _check(st, what):
@@ -361,6 +362,16 @@ def cashash_match_pair_noalloc(params: cashash_params, dset: DeviceSet, image_a:
     _check(_load().cashash_match_pair_noalloc(C.byref(params), C.byref(dset.c), int(image_a), int(image_b),
                                               _dptr(F), _dptr(match_off), _dptr(matches), int(cap),
                                               _stream(stream)), "cashash_match_pair_noalloc")
+
+
+def cashash_noalloc_status(stream=None) -> int:
+    """Reads and clears the device status of the allocation-free calls on the
+    current device (synchronises the stream): CASHASH_OK, CASHASH_EDEVICE or
+    CASHASH_EOVERFLOW, returned rather than raised."""
+    st = _load().cashash_noalloc_status(_stream(stream))
+    if st == CASHASH_ECUDA:
+        _check(st, "cashash_noalloc_status")
+    return st
 
 
 def cashash_match_chunked(ctx: Context, dset: DeviceSet, pairs, chunk_pairs: int, on_chunk, cursor: int = 0,

@@ -127,6 +127,20 @@ struct cashash_plan {
 // ---------------------------------------------------------------------------
 // helpers
 // ---------------------------------------------------------------------------
+// Parameter ranges every entry point accepts (declared in internal.h).
+int chx::params_ok(const cashash_params* p) {
+  if (!p) return 0;
+  if (p->code_bits != 32 && p->code_bits != 64 && p->code_bits != 96 && p->code_bits != 128) return 0;
+  if (p->n_tables < 1 || p->n_tables > CASHASH_MAX_TABLES) return 0;
+  if (p->bits_per_table > 8) return 0;
+  if (p->top_k < 1 || p->top_k > CASHASH_MAX_K) return 0;
+  if (p->ratio_den < 1 || p->ratio_den > 65535 || p->ratio_num > 65535) return 0;
+  if (p->precision > CASHASH_BF16 || p->schedule > CASHASH_SCHED_PERSISTENT) return 0;
+  if (p->flags & ~(CASHASH_FLAG_MUTUAL | CASHASH_FLAG_ACCEPT_SINGLE)) return 0;
+  if (std::isnan(p->epi_px) || std::isinf(p->epi_px)) return 0;
+  return 1;
+}
+
 namespace {
 
 int cuda_err(cudaError_t e) {
@@ -141,18 +155,6 @@ int cuda_err(cudaError_t e) {
     if (_st != CASHASH_OK) return _st;     \
   } while (0)
 
-int params_ok(const cashash_params* p) {
-  if (!p) return 0;
-  if (p->code_bits != 32 && p->code_bits != 64 && p->code_bits != 96 && p->code_bits != 128) return 0;
-  if (p->n_tables < 1 || p->n_tables > CASHASH_MAX_TABLES) return 0;
-  if (p->bits_per_table > 8) return 0;
-  if (p->top_k < 1 || p->top_k > CASHASH_MAX_K) return 0;
-  if (p->ratio_den < 1 || p->ratio_den > 65535 || p->ratio_num > 65535) return 0;
-  if (p->precision > CASHASH_BF16 || p->schedule > CASHASH_SCHED_PERSISTENT) return 0;
-  if (p->flags & ~(CASHASH_FLAG_MUTUAL | CASHASH_FLAG_ACCEPT_SINGLE)) return 0;
-  if (std::isnan(p->epi_px) || std::isinf(p->epi_px)) return 0;
-  return 1;
-}
 
 template <class T>
 int grow(T*& ptr, uint64_t& cap, uint64_t need) {

@@ -192,6 +192,11 @@ __device__ __forceinline__ bool epi_keep_fast(const EpiQ& e, float2 pc) {
 
 #endif
 
+// 1 when every field of p is in the range the entry points accept (code
+// bits, tables, bits per table, k, ratio, precision, schedule, flags, and a
+// finite band width), else 0.
+int params_ok(const cashash_params* p);
+
 // ---- launchers (return cudaError_t of the launch) ----
 cudaError_t launch_colsum(const uint8_t* desc, uint64_t n, unsigned long long* sums, cudaStream_t s);
 cudaError_t launch_row_consts(const unsigned long long* sums, uint64_t n, int have_mean, double* mu,

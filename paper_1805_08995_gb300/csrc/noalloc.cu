@@ -12,12 +12,13 @@
 //
 // The scratch array is a static __device__ object: every GPU that loads this
 // library holds it until the process exits, and every call shares it.  In
-// host code its name is only a host-side stand-in, so its device address is
-// obtained with cudaGetSymbolAddress, once per device, on the first call made
-// with that device current.  Calls that overlap on the GPU (on different
+// host code its name is only a host-side stand-in, so every call looks up its
+// device address with cudaGetSymbolAddress on the current device (a lookup
+// that allocates nothing).  Looking it up per call, rather than caching it
+// per device number, keeps the address right when the device's primary
+// context is torn down and created again (cudaDeviceReset), which can load
+// the array at a new address.  Calls that overlap on the GPU (on different
 // streams, or from different host threads) race on the array.
-#include <mutex>
-
 #include "internal.h"
 
 namespace chx {
@@ -26,8 +27,10 @@ struct NoAllocScratch {
   PairInfo pair;                                   // the one pair of a call
   unsigned long long count;                        // its number of matches (cleared per call)
   unsigned long long total;                        // scan output (= count)
-  unsigned int item_ctr;                           // unused by the per-pair schedule, kept zero
-  uint32_t status;                                 // device status bits (cleared per call)
+  unsigned int item_ctr;                           // tile counter of the per-pair matching kernel (every
+                                                   // tile is claimed through it): cleared before each launch
+  uint32_t status;                                 // device status bits, ORed by every call until
+                                                   // cashash_noalloc_status reads and clears them
   uint32_t pad[4];
   uint2 items[CASHASH_NOALLOC_MAX_QUERIES / 256];  // (pair 0, first query) per 256-query tile
   uint32_t res[CASHASH_NOALLOC_MAX_QUERIES];       // per-query result
@@ -36,7 +39,9 @@ struct NoAllocScratch {
 static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
 
 // Writes the pair record and its work items and clears what must start at
-// zero; everything comes from kernel arguments, so no host copy is needed.
+// zero (the match counter and the tile counter); everything comes from kernel
+// arguments, so no host copy is needed.  The status word is left alone: it
+// collects the errors of every call until the caller reads it.
 __global__ void k_noalloc_setup(NoAllocScratch* sc, PairInfo pi, uint32_t n_items, uint32_t tile) {
   for (uint32_t i = threadIdx.x; i < n_items; i += blockDim.x) sc->items[i] = make_uint2(0u, i * tile);
   if (threadIdx.x == 0) {
@@ -44,14 +49,21 @@ __global__ void k_noalloc_setup(NoAllocScratch* sc, PairInfo pi, uint32_t n_item
     sc->count = 0ull;
     sc->total = 0ull;
     sc->item_ctr = 0u;
-    sc->status = 0u;
   }
 }
 
 namespace {
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-NoAllocScratch* g_ptr[kMaxDevices] = {};
+// The device address of the scratch array in the current device's context.
+int scratch_ptr(NoAllocScratch** out) {
+  void* ptr = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+  if (e != cudaSuccess || !ptr) {
+    cudaGetLastError();
+    return CASHASH_ECUDA;
+  }
+  *out = static_cast<NoAllocScratch*>(ptr);
+  return CASHASH_OK;
+}
 }  // namespace
 
 }  // namespace chx
@@ -63,13 +75,12 @@ extern "C" int cashash_match_pair_noalloc(const cashash_params* p, const cashash
                                           uint32_t* matches, uint64_t cap, cashash_stream_t stream_) {
   cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
   if (!p || !s || !match_off || (cap > 0 && !matches)) return CASHASH_EINVAL;
-  if (p->code_bits != 32 && p->code_bits != 64 && p->code_bits != 96 && p->code_bits != 128) return CASHASH_EINVAL;
-  if (p->n_tables < 1 || p->n_tables > CASHASH_MAX_TABLES || p->bits_per_table > 8) return CASHASH_EINVAL;
-  if (p->top_k < 1 || p->top_k > CASHASH_MAX_K || p->ratio_den < 1 || p->ratio_den > 65535 ||
-      p->ratio_num > 65535)
-    return CASHASH_EINVAL;
-  if (!(p->epi_px == p->epi_px) || p->epi_px > 1e300) return CASHASH_EINVAL;
-  if (p->flags & ~(CASHASH_FLAG_MUTUAL | CASHASH_FLAG_ACCEPT_SINGLE)) return CASHASH_EINVAL;
+  {
+    cashash_params q = *p;  // precision and schedule do not apply here
+    q.precision = CASHASH_FP32;
+    q.schedule = CASHASH_SCHED_PER_PAIR;
+    if (!params_ok(&q)) return CASHASH_EINVAL;
+  }
   if (p->flags & CASHASH_FLAG_MUTUAL) return CASHASH_ENOTSUP;  // would need scratch for the reverse pair
   if (!s->img_off || image_a >= s->n_images || image_b >= s->n_images) return CASHASH_EINVAL;
   if (s->img_off[0] != 0 || s->img_off[s->n_images] != s->n_features) return CASHASH_EINVAL;
@@ -90,19 +101,8 @@ extern "C" int cashash_match_pair_noalloc(const cashash_params* p, const cashash
   if ((nA > 0 || nB > 0) && (!s->desc || !s->codes || !s->buckets || !s->sqnorm || !s->tables))
     return CASHASH_EINVAL;
 
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return CASHASH_ECUDA;
   NoAllocScratch* sc = nullptr;
-  {
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_ptr[dev]) {
-      void* ptr = nullptr;
-      const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-      if (e != cudaSuccess || !ptr) return CASHASH_ECUDA;
-      g_ptr[dev] = static_cast<NoAllocScratch*>(ptr);
-    }
-    sc = g_ptr[dev];
-  }
+  if (scratch_ptr(&sc) != CASHASH_OK) return CASHASH_ECUDA;
 
   KParams kp{};
   kp.code_bits = p->code_bits;
@@ -151,5 +151,21 @@ extern "C" int cashash_match_pair_noalloc(const cashash_params* p, const cashash
   if (launch_scan_counts(&sc->count, 1, match_off, cap, &sc->status, &sc->total, stream) != cudaSuccess)
     return CASHASH_ECUDA;
   if (launch_compact(&sc->pair, 1, sc->res, match_off, matches, cap, stream) != cudaSuccess) return CASHASH_ECUDA;
+  return CASHASH_OK;
+}
+
+extern "C" int cashash_noalloc_status(cashash_stream_t stream_) {
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+  NoAllocScratch* sc = nullptr;
+  if (scratch_ptr(&sc) != CASHASH_OK) return CASHASH_ECUDA;
+  uint32_t st = 0;
+  if (cudaMemcpyAsync(&st, &sc->status, sizeof st, cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+      cudaMemsetAsync(&sc->status, 0, sizeof(uint32_t), stream) != cudaSuccess ||
+      cudaStreamSynchronize(stream) != cudaSuccess) {
+    cudaGetLastError();
+    return CASHASH_ECUDA;
+  }
+  if (st & DST_INDEX) return CASHASH_EDEVICE;
+  if (st & DST_OVERFLOW) return CASHASH_EOVERFLOW;
   return CASHASH_OK;
 }

@@ -106,16 +106,20 @@ def config0(seed: int = 0) -> ImageSet:
                     projection_matrix(seed), "config0", truth=truth)
 
 
-def _copy_mix(rng, sizes, neighbours, copy_frac=0.3):
+def _copy_mix(rng, sizes, neighbours, copy_frac=0.3, truth=None):
     """Fresh descriptors for each image, then copy_frac of each image's rows
-    replaced by noisy copies of fresh rows of its neighbour images."""
+    replaced by noisy copies of fresh rows of its neighbour images.  When
+    `truth` is a list, it receives one int64 array [n_copy][3] per image:
+    (row of the copy in this image, source image, row of the source there);
+    recording it draws no random numbers, so the images are the same."""
     n_img = len(sizes)
     n_copy = [int(round(copy_frac * s)) for s in sizes]
     fresh = [sift_like(rng, s - c) for s, c in zip(sizes, n_copy)]
-    imgs = []
+    imgs, perms, srcs = [], [], []
     for i in range(n_img):
         nb = neighbours[i]
         src_img = nb[rng.integers(0, len(nb), size=n_copy[i])]
+        src_row = np.zeros(n_copy[i], np.int64)
         parts = [fresh[i]]
         if n_copy[i]:
             rows = np.empty((n_copy[i], DIM), np.uint8)
@@ -123,10 +127,42 @@ def _copy_mix(rng, sizes, neighbours, copy_frac=0.3):
                 sel = np.nonzero(src_img == k)[0]
                 pick = rng.integers(0, fresh[k].shape[0], size=sel.size)
                 rows[sel] = fresh[k][pick]
+                src_row[sel] = pick
             parts.append(noisy_copy(rng, rows))
         img = np.concatenate(parts)
-        imgs.append(img[rng.permutation(img.shape[0])])
+        perm = rng.permutation(img.shape[0])
+        imgs.append(img[perm])
+        perms.append(perm)
+        srcs.append((src_img.astype(np.int64), src_row))
+    if truth is not None:
+        where = []  # where[i][r]: position in image i of its r-th pre-permutation row
+        for perm in perms:
+            inv = np.empty(perm.size, np.int64)
+            inv[perm] = np.arange(perm.size)
+            where.append(inv)
+        for i in range(n_img):
+            nf = sizes[i] - n_copy[i]
+            src_img, src_row = srcs[i]
+            pos = where[i][nf + np.arange(n_copy[i])]
+            spos = np.array([where[k][r] for k, r in zip(src_img, src_row)], np.int64)
+            truth.append(np.stack([pos, src_img, spos], axis=1) if n_copy[i] else np.zeros((0, 3), np.int64))
     return imgs
+
+
+def planted_pairs(truth, pairs):
+    """Planted correspondences of each pair (A, B): the set of (q, j) with q a
+    copy of B's row j or j a copy of A's row q.  Returns one set per pair."""
+    by = {}
+    for i, t in enumerate(truth):
+        for pos, k, spos in t:
+            by.setdefault((i, int(k)), []).append((int(pos), int(spos)))
+    out = []
+    for a, b in pairs:
+        a, b = int(a), int(b)
+        s = {(q, j) for q, j in by.get((a, b), [])}
+        s |= {(q, j) for j, q in by.get((b, a), [])}
+        out.append(s)
+    return out
 
 
 def config1(seed: int = 1, n_images: int = 100, lo: int = 4000, hi: int = 12000) -> ImageSet:
@@ -139,11 +175,12 @@ def config1(seed: int = 1, n_images: int = 100, lo: int = 4000, hi: int = 12000)
     for i in range(n_images):
         nb = [k for k in range(i - 5, i + 6) if k != i and 0 <= k < n_images]
         neighbours.append(np.array(nb if nb else [i], np.int64))
-    imgs = _copy_mix(rng, sizes, neighbours)
+    truth = []
+    imgs = _copy_mix(rng, sizes, neighbours, truth=truth)
     iu = np.triu_indices(n_images, 1)
     pairs = np.stack([iu[0], iu[1]], axis=1).astype(np.uint32)
     return ImageSet(np.concatenate(imgs), _offsets(sizes), pairs, projection_matrix(seed),
-                    "config1:%d imgs %d..%d" % (n_images, lo, hi))
+                    "config1:%d imgs %d..%d" % (n_images, lo, hi), truth={"copies": truth})
 
 
 def config3(seed: int = 3, n_images: int = 2000, lo: int = 1000, hi: int = 20000, n_nbr: int = 30) -> ImageSet:

@@ -51,7 +51,9 @@ def oracle_codes(orc, desc, R, po, mu=None, threads=8):
     return mu, codes, buckets
 
 
-def gpu_run(ch, s, pairs, **pk):
+def gpu_run(ch, s, pairs, tuning=None, **pk):
+    """tuning: (kernel, tile, ctas_per_sm) forced on a batched plan, or None
+    for cashash_match_pairs with the default choice."""
     p = ch.cashash_default_params(**pk)
     ctx = ch.cashash_create(p, s.R)
     ds = ch.DeviceSet(p, s.img_off, s.desc, s.kpts)
@@ -62,7 +64,16 @@ def gpu_run(ch, s, pairs, **pk):
     moff = torch.zeros(P + 1, dtype=torch.int64, device="cuda")
     mt = torch.zeros((max(cap, 1), 2), dtype=torch.int32, device="cuda")
     F = None if s.F is None else torch.from_numpy(np.ascontiguousarray(s.F)).cuda()
-    ch.cashash_match_pairs(ctx, ds, pairs, moff, mt, cap, F=F)
+    if tuning is None:
+        ch.cashash_match_pairs(ctx, ds, pairs, moff, mt, cap, F=F)
+    else:
+        plan = ch.cashash_plan_create(ctx, ds, pairs)
+        ch.cashash_plan_set_tuning(plan, *tuning)
+        assert ch.cashash_plan_get_tuning(plan)["kernel"] == tuning[0]
+        for _ in range(2):  # the second run starts from the thresholds the first learned
+            ch.cashash_match_plan(ctx, plan, moff, mt, cap, F=F)
+        torch.cuda.synchronize()
+        plan.close()
     assert ch.cashash_sync_status(ctx) == ch.CASHASH_OK
     off = moff.cpu().numpy().astype(np.uint64)
     got = mt[:int(off[-1])].cpu().numpy().view(np.uint32)
@@ -77,8 +88,8 @@ def oparams(orc, pk):
                       epi_px=pk.get("epi_px", -1.0), flags=pk.get("flags", 0))
 
 
-def check_case(ch, orc, s, pairs, **pk):
-    ctx, ds, off, got, stats = gpu_run(ch, s, pairs, **pk)
+def check_case(ch, orc, s, pairs, tuning=None, **pk):
+    ctx, ds, off, got, stats = gpu_run(ch, s, pairs, tuning=tuning, **pk)
     po = oparams(orc, pk)
     mu, codes, buckets = oracle_codes(orc, s.desc, s.R, po)
     assert np.array_equal(ch.cashash_get_mean(ctx), mu)
@@ -503,6 +514,17 @@ def test_band_edge_decisions(ch, orc, sched):
 def test_many_pairs_medium(ch, orc):
     s = synth.config1(seed=11, n_images=12, lo=1500, hi=4500)
     check_case(ch, orc, s, s.pairs, schedule=1)
+
+
+@pytest.mark.parametrize("kernel", ["join", "query"])
+@pytest.mark.parametrize("tau", [20, 30, 40, 50, 60, 128])
+def test_tau_sweep_values(ch, orc, tau, kernel):
+    """Sec. 6 threshold at every value of the tau sweep (bench.py --tau-sweep),
+    on a 12-image exhaustive set in the BF16 form, with the bucket join and
+    with the per-query kernel."""
+    s = synth.config1(seed=12, n_images=12, lo=3000, hi=9000)
+    tuning = (ch.CASHASH_KERNEL_JOIN, 4, 0) if kernel == "join" else (ch.CASHASH_KERNEL_QUERY, 512, 0)
+    check_case(ch, orc, s, s.pairs, tuning=tuning, schedule=1, precision=1, tau=tau)
 
 
 def test_capacity_overflow_reports_and_truncates(ch, orc):
