@@ -4,13 +4,21 @@
  * The library implements Cascade Hashing (CasHash) SIFT matching between
  * image pairs as described in Xu, Sun and Tao, "GPU Accelerated Cascade
  * Hashing Image Matching for Large Scale 3D Reconstruction":
- *   Sec. 3.1 Step 1  lookup in several tables of m-bit short codes
- *   Sec. 3.1 Step 2  remapping to an n-bit code, Hamming distance
- *   Sec. 3.1 Step 3  ranking: the k candidates of smallest Hamming distance
- *   Sec. 3.1 Step 4  squared Euclidean distance on those k, Lowe's ratio test
- *   Sec. 4.1         hash bit = sign of the inner product with a random vector
- *   Sec. 5           optional Hamming threshold tau before ranking
- *   Sec. 6.2 Eq. 1-2 optional epipolar band before ranking
+ *   Sec. 3.1 ("Review of Cascade Hashing")
+ *            Step 1  lookup in several tables of m-bit short codes
+ *            Step 2  remapping to an n-bit code, Hamming distance
+ *            Step 3  ranking: the k candidates of smallest Hamming distance
+ *            Step 4  squared Euclidean distance on those k, Lowe's ratio test
+ *   Sec. 5.1 ("The Improved Parallel Calculation of Hashing Code")
+ *                    hash bit = sign of the inner product with a random vector
+ *   Sec. 5.2 ("Improved Parallel Euclidean Distance Calculation") Step 4 on the GPU
+ *   Sec. 6   ("Improved Parallel Hashing Ranking") optional Hamming threshold
+ *                    tau before ranking
+ *   Sec. 7.1 ("First Stage of Image Matching") Ga-CasHash: top-scale subsets, F
+ *   Sec. 7.2 ("Second Stage of Guided Matching"), Eq. 1-2: optional epipolar
+ *                    band before ranking
+ *   Sec. 4   ("Three-Level Data Scheduling Strategy") is replaced by resident
+ *                    device sets and pinned, chunked host staging (cashash_run_host)
  *
  * Results are defined exactly (bit-exact, not approximately):
  *   - descriptors are centred by the mean over every descriptor of the set
@@ -67,7 +75,7 @@ typedef enum {
 enum { CASHASH_FP32 = 0, CASHASH_BF16 = 1 };                          /* projection precision form */
 enum { CASHASH_SCHED_PER_PAIR = 0, CASHASH_SCHED_PERSISTENT = 1 };   /* matching schedule */
 
-#define CASHASH_DIM 128          /* SIFT descriptor length d (Sec. 4.1) */
+#define CASHASH_DIM 128          /* SIFT descriptor length d (Sec. 5.1) */
 #define CASHASH_MAX_TABLES 8
 #define CASHASH_MAX_K 32
 #define CASHASH_MAX_IMAGE 16777215u   /* features per image (24-bit candidate index) */
@@ -81,13 +89,13 @@ typedef struct {
   uint32_t top_k;           /* k of Step 3: 1..32 [10] */
   uint32_t ratio_num;       /* Lowe ratio num/den [4/5] */
   uint32_t ratio_den;
-  uint32_t tau;             /* Sec. 5 threshold: candidates with Hamming > tau are dropped;
+  uint32_t tau;             /* Sec. 6 threshold: candidates with Hamming > tau are dropped;
                                tau >= code_bits turns it off [code_bits] */
   uint32_t precision;       /* CASHASH_FP32 (CUDA-core projection) or CASHASH_BF16 (tensor cores) */
   uint32_t schedule;        /* CASHASH_SCHED_PER_PAIR (one launch per pair) or
                                CASHASH_SCHED_PERSISTENT (one launch over the whole pair list) */
   uint32_t flags;           /* CASHASH_FLAG_* below, ORed [0] */
-  double epi_px;            /* Sec. 6.2 threshold d in pixels; < 0 turns the band off [-1] */
+  double epi_px;            /* Sec. 7.2 threshold d in pixels; < 0 turns the band off [-1] */
 } cashash_params;
 
 /* cashash_params.flags (readings beyond the paper, off by default):
@@ -127,7 +135,7 @@ typedef struct {
 uint64_t cashash_tables_bytes(const cashash_params* p, const uint64_t* img_off, uint32_t n_images);
 
 /* Creates a context on the current CUDA device.  R_host is the matrix of
- * random vectors r_k of Sec. 4.1: [code_bits + n_tables * bits_per_table]
+ * random vectors r_k of Sec. 5.1: [code_bits + n_tables * bits_per_table]
  * rows of 128 doubles, row-major; rows 0..code_bits-1 give the remapping
  * code, row code_bits + t*m + i gives bit i of table t.  The context copies
  * R and owns its device workspace.  Errors: EINVAL, ENOTSUP, ENOMEM, ECUDA. */
@@ -136,7 +144,7 @@ int cashash_create(cashash_ctx** out, const cashash_params* p, const double* R_h
 /* Releases the context and its workspace (after synchronising its work). */
 void cashash_destroy(cashash_ctx* ctx);
 
-/* Sec. 4.1 + Steps 1-2: hash codes and lookup tables for every feature of
+/* Sec. 5.1 + Steps 1-2: hash codes and lookup tables for every feature of
  * the set.  mean_host: HOST [128] caller-given centre, or NULL to use the
  * mean over every descriptor of the set (computed exactly from integer
  * column sums, one correctly rounded division).  Writes set->codes,
@@ -160,7 +168,7 @@ int cashash_plan_create(cashash_ctx* ctx, const cashash_set* set, const uint32_t
                         cashash_plan** out);
 void cashash_plan_destroy(cashash_plan* plan);
 
-/* Steps 1-4 (+ Sec. 5 tau, + Sec. 6.2 epipolar band when epi_px >= 0) for
+/* Steps 1-4 (+ Sec. 6 tau, + Sec. 7.2 epipolar band when epi_px >= 0) for
  * every pair of the plan.  Outputs (DEVICE, caller-allocated):
  *   match_off [P + 1] uint64: matches of pair i are entries
  *                             match_off[i] .. match_off[i+1]-1;
@@ -376,10 +384,10 @@ int cashash_get_stats(cashash_ctx* ctx, cashash_stats* out);
 const char* cashash_strerror(int status);
 
 /* ------------------------------------------------------------------------
- * Ga-CasHash, first stage (Sec. 5.1).  The top 20 % of each image's features
+ * Ga-CasHash, first stage (Sec. 7.1).  The top 20 % of each image's features
  * by SIFT scale are matched exhaustively with CasHash; a pair with at least
  * 16 matches gets a fundamental matrix from the GPU, and goes on to the
- * guided matching of Sec. 5.2 (the band, epi_px >= 0, with that F) when at
+ * guided matching of Sec. 7.2 (the band, epi_px >= 0, with that F) when at
  * least 2/3 of its matches are inliers.  The paper names no estimator: this
  * is the normalised 8-point algorithm (Hartley 1997) inside RANSAC (Fischler
  * and Bolles 1981) with the squared Sampson distance as the inlier test and a

@@ -20,7 +20,7 @@
 /* ------------------------------------------------------------------------ */
 /* Centring (the paper is silent; reading: one mean over the whole set of    */
 /* descriptors passed to one code-building call, so that the hyperplanes of  */
-/* Sec. 4.1 are the same for every image).                                   */
+/* Sec. 5.1 are the same for every image).                                   */
 /* ------------------------------------------------------------------------ */
 void oracle_mean(const uint8_t* desc, uint64_t n, double* mu) {
   uint64_t s[ORACLE_DIM];
@@ -32,7 +32,7 @@ void oracle_mean(const uint8_t* desc, uint64_t n, double* mu) {
 }
 
 /* ------------------------------------------------------------------------ */
-/* Sec. 4.1: a hash bit is the sign of the inner product of the (centred)    */
+/* Sec. 5.1: a hash bit is the sign of the inner product of the (centred)    */
 /* descriptor with a random vector r_k.  Reading: double precision, terms    */
 /* taken in index order j = 0..127, each term (x_j - mu_j) * r_kj rounded,   */
 /* accumulated left to right; no fused multiply-add.                        */
@@ -53,7 +53,7 @@ static int params_ok(const oracle_params* p) {
          p->top_k <= ORACLE_MAX_K && p->ratio_den > 0;
 }
 
-/* Steps 1 and 2 of Sec. 3.1 with the hash functions of Sec. 4.1.  Rows
+/* Steps 1 and 2 of Sec. 3.1 with the hash functions of Sec. 5.1.  Rows
  * 0..n-1 of R give the n-bit remapping code (Step 2); rows n + t*m + i give
  * bit i of the m-bit short code of lookup table t (Step 1).  Sign at exactly
  * zero is bit 0 (reading: the strict test v > 0). */
@@ -79,7 +79,7 @@ void oracle_hash(const uint8_t* desc, uint64_t n, const double* mu, const double
   }
 }
 
-/* Sec. 6.2, Eq. 1-2: the epipolar line of the query is l_q = F p_q with
+/* Sec. 7.2, Eq. 1-2: the epipolar line of the query is l_q = F p_q with
  * p_q = (x, y, 1); a candidate p' = (x', y', 1) is kept when its distance to
  * l_q is at most d.  Eq. 2 as printed has no absolute value; the distance of
  * a point to a line is meant, so the test is |a x' + b y' + c| <= d sqrt(a^2+b^2),
@@ -134,7 +134,7 @@ static int32_t sqdist(const uint8_t* a, const uint8_t* b) {
   return s;
 }
 
-/* One image pair, Sec. 3.1 Steps 1-4 (and Sec. 6.2 steps 1-5 when the
+/* One image pair, Sec. 3.1 Steps 1-4 (and Sec. 7.2 steps 1-5 when the
  * epipolar band is on). */
 int64_t oracle_match_pair(const uint8_t* descA, const uint32_t* codesA, const uint8_t* bucketsA, uint32_t nA,
                           const uint8_t* descB, const uint32_t* codesB, const uint8_t* bucketsB, uint32_t nB,
@@ -184,7 +184,7 @@ int64_t oracle_match_pair(const uint8_t* descA, const uint32_t* codesA, const ui
         nc++;
       }
     }
-    /* Sec. 6.2 step 3: the epipolar band removes candidates before ranking. */
+    /* Sec. 7.2 step 3: the epipolar band removes candidates before ranking. */
     if (epi) {
       uint32_t w = 0;
       for (uint32_t e = 0; e < nc; ++e) {
@@ -197,7 +197,7 @@ int64_t oracle_match_pair(const uint8_t* descA, const uint32_t* codesA, const ui
     }
     /* Step 2: Hamming distance between the n-bit remapping codes. */
     for (uint32_t e = 0; e < nc; ++e) cand[e].h = hamming(codesA + (size_t)q * 4, codesB + (size_t)cand[e].j * 4);
-    /* Sec. 5: candidates farther than tau are discarded (off when tau >= n). */
+    /* Sec. 6: candidates farther than tau are discarded (off when tau >= n). */
     if (p->tau < p->code_bits) {
       uint32_t w = 0;
       for (uint32_t e = 0; e < nc; ++e)

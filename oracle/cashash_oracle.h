@@ -13,10 +13,10 @@
  *   Sec. 3.1 Step 2  hashing remapping to n-bit codes, Hamming distance
  *   Sec. 3.1 Step 3  hashing ranking: keep the k smallest Hamming distances
  *   Sec. 3.1 Step 4  Euclidean distance on those k, Lowe's ratio test
- *   Sec. 4.1         hash bits are signs of inner products with random
+ *   Sec. 5.1         hash bits are signs of inner products with random
  *                    vectors r_k (Charikar's sign LSH)
- *   Sec. 5           optional Hamming threshold tau before ranking
- *   Sec. 6.2 Eq. 1-2 optional epipolar band |dist(p', l_q)| <= d
+ *   Sec. 6           optional Hamming threshold tau before ranking
+ *   Sec. 7.2 Eq. 1-2 optional epipolar band |dist(p', l_q)| <= d
  *
  * Readings where the paper is silent (documented beside each function):
  * descriptors are centred by their mean over the whole set given to one
@@ -43,7 +43,7 @@
 extern "C" {
 #endif
 
-#define ORACLE_DIM 128        /* SIFT descriptor length d (Sec. 4.1: d = 128) */
+#define ORACLE_DIM 128        /* SIFT descriptor length d (Sec. 5.1: d = 128) */
 #define ORACLE_MAX_TABLES 8
 #define ORACLE_MAX_K 64
 
@@ -58,9 +58,9 @@ typedef struct {
   uint32_t top_k;           /* k of Step 3, 1..64 */
   uint32_t ratio_num;       /* Lowe ratio as a fraction num/den (0.8 = 4/5) */
   uint32_t ratio_den;
-  uint32_t tau;             /* Sec. 5 threshold; >= code_bits means off */
+  uint32_t tau;             /* Sec. 6 threshold; >= code_bits means off */
   uint32_t flags;           /* ORACLE_MUTUAL | ORACLE_ACCEPT_SINGLE */
-  double epi_px;            /* Sec. 6.2 threshold d in pixels; < 0 means off */
+  double epi_px;            /* Sec. 7.2 threshold d in pixels; < 0 means off */
 } oracle_params;
 
 /* Per-query detail for invariant tests. */
@@ -80,7 +80,7 @@ void oracle_mean(const uint8_t* desc, uint64_t n, double* mu /* [128] */);
 /* One projection value v = sum_j R[b][j] * (x_j - mu_j), ordered double. */
 double oracle_projection(const uint8_t* x /* [128] */, const double* mu, const double* Rrow);
 
-/* Hash codes (Sec. 4.1 + Steps 1-2).  R has code_bits + n_tables*bits_per_table
+/* Hash codes (Sec. 5.1 + Steps 1-2).  R has code_bits + n_tables*bits_per_table
  * rows of 128 doubles.  codes: [n][4] uint32, bit b of the remapping code in
  * word b/32 at bit b%32, unused bits zero.  buckets: [n][n_tables], bucket of
  * table t = sum_i bit(code_bits + t*m + i) << i. */

@@ -3,10 +3,10 @@
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this module.  The product library never does.
 
-Sec. 5.1 (first stage of Ga-CasHash): the top 20 % of each image's features
+Sec. 7.1 (first stage of Ga-CasHash): the top 20 % of each image's features
 by SIFT scale are matched exhaustively with CasHash; for a pair with at least
 16 matches the fundamental matrix is estimated, and the pair goes on to the
-guided matching of Sec. 5.2 when at least 2/3 of its matches are inliers.
+guided matching of Sec. 7.2 when at least 2/3 of its matches are inliers.
 The paper names no estimator; this follows the published normalised 8-point
 algorithm (Hartley, "In defense of the eight-point algorithm", 1997) inside
 RANSAC (Fischler and Bolles, 1981), with the Sampson distance (Hartley and

@@ -430,7 +430,7 @@ def cashash_run_host(ctx: Context, desc: np.ndarray, img_off: np.ndarray, pairs:
 
 
 # ---------------------------------------------------------------------------
-# Ga-CasHash first stage (Sec. 5.1)
+# Ga-CasHash first stage (Sec. 7.1)
 # ---------------------------------------------------------------------------
 
 def cashash_get_params(ctx: Context) -> cashash_params:

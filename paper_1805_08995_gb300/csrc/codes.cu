@@ -1,4 +1,4 @@
-// Hash codes of Sec. 4.1 / Steps 1-2 (Sec. 3.1): centring, projection, signs.
+// Hash codes of Sec. 5.1 / Steps 1-2 (Sec. 3.1): centring, projection, signs.
 //
 // A feature's bit b is the sign of v_b = sum_j R_bj (x_j - mu_j) evaluated in
 // IEEE double, j ascending, every difference, product and sum rounded to

@@ -1,7 +1,7 @@
-// First stage of Ga-CasHash (Sec. 5.1): the top 20 % of each image's
+// First stage of Ga-CasHash (Sec. 7.1): the top 20 % of each image's
 // features by SIFT scale are matched exhaustively with CasHash; a pair with
 // at least 16 matches gets a fundamental matrix estimated on the GPU, and it
-// goes on to the guided matching of Sec. 5.2 when at least 2/3 of its matches
+// goes on to the guided matching of Sec. 7.2 when at least 2/3 of its matches
 // are inliers of that F.
 //
 // The paper names no estimator.  Here: the normalised 8-point algorithm

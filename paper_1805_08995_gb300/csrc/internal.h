@@ -55,7 +55,7 @@ __host__ __device__ inline uint64_t join_block(uint64_t n) {
   return 1040u + 4u * ((n + 3) / 4 * 4) + 16u * n;
 }
 
-// Per-row constants of the projection (Sec. 4.1) derived from R and the centre.
+// Per-row constants of the projection (Sec. 5.1) derived from R and the centre.
 struct RowConst {
   float c32;     // fl32(c_b), c_b = sum_j R_bj mu_j
   float alpha;   // bound factor on ||x||_2 (FP32 form) or on ||x||_2 (BF16 form)
@@ -117,7 +117,7 @@ __device__ __forceinline__ bool ratio_ok(const KParams& kp, uint32_t nv, uint32_
 }
 
 // ---------------------------------------------------------------------------
-// Sec. 6.2 band test, shared by the matching kernels.
+// Sec. 7.2 band test, shared by the matching kernels.
 // ---------------------------------------------------------------------------
 // The epipolar line of the query, l = F p_q, and d^2 (a^2 + b^2), in FP64.
 __device__ __forceinline__ void epi_line(const double* F, float2 pq, double dd, double& la, double& lb, double& lc,

@@ -1,5 +1,5 @@
 // Batched matching as a bucket join on the tensor cores: Steps 1-4 of
-// Sec. 3.1 (+ the Sec. 5 threshold tau) organised around the lookup tables.
+// Sec. 3.1 (+ the Sec. 6 threshold tau) organised around the lookup tables.
 //
 // Step 1 pairs a query with exactly the candidates that share its bucket in
 // some table, so for table t and short code v the work is the dense block
@@ -18,17 +18,17 @@
 // map.
 //
 // Keys H <= theta (theta: the pair's threshold guess, learned per pair from the
-// k-th distances of earlier launches, capped by the Sec. 5 tau) are appended to
+// k-th distances of earlier launches, capped by the Sec. 6 tau) are appended to
 // the query's survivor list: a counter per query in shared memory, a list of
 // JSEG entries per query in global memory.  After the scan the CTA finalises
 // the pair's queries, one thread per query: the k smallest distinct survivors
 // (Step 3; a point met through several tables appears once), exact squared
-// distances with 8 lanes per 128-byte row (Step 4) and Lowe's ratio test.  A
+// distances with 8 lanes per 128-byte row (Step 4, Sec. 5.2) and Lowe's ratio test.  A
 // query whose list overflowed, or that holds fewer than k distinct survivors
 // while the guess turned some candidate away, is left PENDING for the exact
 // fallback kernel, so results never depend on the guess.
 //
-// With the Sec. 6.2 band (EPI) a candidate outside the band is no candidate at
+// With the Sec. 7.2 band (EPI) a candidate outside the band is no candidate at
 // all, so there is no Hamming guess: each entry is tested against the query's
 // epipolar line (FP32 roundings of the FP64 line, computed once per query and
 // pair; undecided entries in FP64) and only entries inside the band survive.
@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(JT, 2) k_join(MatchArgs a) {
   uint32_t* key_s = cnt_s + (a.na_max + 3) / 4 * 4;
   uint32_t* dist_s = key_s + KC * JT;
   uint32_t* seg = a.jqueue + (size_t)blockIdx.x * a.na_max * JSEG;
-  const uint32_t h_user = TAU ? kp.tau : 128u;  // Sec. 5: keys with H > tau are no candidates
+  const uint32_t h_user = TAU ? kp.tau : 128u;  // Sec. 6: keys with H > tau are no candidates
   float4* lines = EPI ? a.jline + (size_t)blockIdx.x * a.na_max : nullptr;  // per query: FP32 a, b, c, r
   const double dd = kp.epi_px * kp.epi_px;
   const float2* kpts = reinterpret_cast<const float2*>(a.kpts);
@@ -310,7 +310,7 @@ __global__ void __launch_bounds__(JT, 2) k_join(MatchArgs a) {
           uint32_t ka = (acc_a | (acc_a >> 16)) & 0xFFu, kb = (acc_b | (acc_b >> 16)) & 0xFFu;
           ka &= va ? jok : 0u;
           kb &= vb ? jok : 0u;
-          if constexpr (EPI) {  // Sec. 6.2: only candidates inside the band
+          if constexpr (EPI) {  // Sec. 7.2: only candidates inside the band
             const float4 La = va ? lines[qa_c] : make_float4(0.f, 0.f, 0.f, 0.f);
             const float4 Lb = vb ? lines[qb_c] : make_float4(0.f, 0.f, 0.f, 0.f);
             uint32_t ba = 0, bb = 0;

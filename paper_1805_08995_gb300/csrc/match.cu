@@ -1,5 +1,5 @@
-// Matching of image pairs: Steps 1-4 of Sec. 3.1, the tau threshold of Sec. 5
-// and the epipolar band of Sec. 6.2 (Eq. 1-2), fused in one kernel.
+// Matching of image pairs: Steps 1-4 of Sec. 3.1, the tau threshold of Sec. 6
+// and the epipolar band of Sec. 7.2 (Eq. 1-2), fused in one kernel.
 //
 // Work item = (pair, tile of TPB queries of the query image); thread = query.
 // The candidate image is streamed through shared memory in chunks of JC
@@ -29,7 +29,7 @@
 // Then each warp computes the exact squared distances of its 32 queries' k
 // candidates with 8 lanes per 128-byte row (d = |a|^2 + |b|^2 - 2 a.b, dp4a
 // on uint8, exact in int32), and each thread applies Lowe's ratio test
-// den^2 d1 < num^2 d2 (Step 4).
+// den^2 d1 < num^2 d2 (Step 4, Sec. 5.2).
 #include "internal.h"
 
 namespace chx {
@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(TPB, (TPB <= 512 ? 2 : 1)) k_match(MatchArgs a
   uint16_t* tab_s = reinterpret_cast<uint16_t*>(smem + (size_t)JC * 16);
   float2* kp_s = reinterpret_cast<float2*>(smem + (size_t)JC * 16 + (size_t)T * (OFF_STRIDE + JC) * 2);
   const double dd = kp.epi_px * kp.epi_px;
-  // Sec. 5: candidates farther than tau are not candidates at all
+  // Sec. 6: candidates farther than tau are not candidates at all
   const uint32_t thr_user = kp.tau < kp.code_bits ? ((kp.tau + 1u) << 24) : KEY_INF;
   const bool filtered = EPI || thr_user != KEY_INF;
   uint32_t* qreg = nullptr;
@@ -157,8 +157,8 @@ __global__ void __launch_bounds__(TPB, (TPB <= 512 ? 2 : 1)) k_match(MatchArgs a
             // Step 2: Hamming distance of the n-bit remapping codes
             const uint32_t h = hamming128(codes_s[jl], qc);
             uint32_t key = (h << 24) | (cb + jl);
-            if (key >= thr_user) key = KEY_INF;                                 // Sec. 5
-            if (EPI && key != KEY_INF && !epi_keep_fast(eq, kp_s[jl])) key = KEY_INF;  // Sec. 6.2
+            if (key >= thr_user) key = KEY_INF;                                 // Sec. 6
+            if (EPI && key != KEY_INF && !epi_keep_fast(eq, kp_s[jl])) key = KEY_INF;  // Sec. 7.2
             if (SPEC) {
               if (filtered && key == KEY_INF) --nlook;
               if (key < thr) {
@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(TPB, (TPB <= 512 ? 2 : 1)) k_match(MatchArgs a
       if (kth != KEY_INF) atomicMax(&s_tau_next, (kth >> 24) + 1u);
     }
 
-    // Step 4: exact squared distances of the k ranked candidates
+    // Step 4 (Sec. 5.2): exact squared distances of the k ranked candidates
     __syncthreads();
     uint32_t* key_s = reinterpret_cast<uint32_t*>(smem);
     uint32_t* dist_s = key_s + KC * TPB;

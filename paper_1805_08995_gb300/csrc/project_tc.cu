@@ -1,4 +1,4 @@
-// BF16 tensor-core form of the projection of Sec. 4.1 (tcgen05 + TMEM, sm_103a).
+// BF16 tensor-core form of the projection of Sec. 5.1 (tcgen05 + TMEM, sm_103a).
 //
 // v_fb = sum_j R_bj x_fj - c_b is computed as a GEMM D[128 features x N rows]
 // = X (uint8 -> bf16, exact) times [Rhi | Rlo]^T, where Rhi = bf16(R) and

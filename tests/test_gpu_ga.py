@@ -1,4 +1,4 @@
-"""GPU parity of the Ga-CasHash first stage (Sec. 5.1) against the oracle.
+"""GPU parity of the Ga-CasHash first stage (Sec. 7.1) against the oracle.
 
 Selection by scale and every integer decision (stage-1 match counts, inlier
 counts, the winning hypothesis, acceptance) must be identical.  F is compared

@@ -463,7 +463,7 @@ def test_identical_and_degenerate_descriptors(ch, orc):
 @pytest.mark.parametrize("flags", [0, 1, 3])
 @pytest.mark.parametrize("sched", [0, 1])
 def test_epipolar_band(ch, orc, sched, flags):
-    """Sec. 6.2: candidates outside the 4 px band around the query's
+    """Sec. 7.2: candidates outside the 4 px band around the query's
     epipolar line are removed before ranking (small config-4 style set)."""
     import math
     s = synth.epipolar_set(41, n_views=7, n_points=24000, arc=2 * math.pi * 7 / 250, z_max=0.355)
@@ -475,7 +475,7 @@ def test_epipolar_band(ch, orc, sched, flags):
 
 @pytest.mark.parametrize("sched", [0, 1])
 def test_band_edge_decisions(ch, orc, sched):
-    """Sec. 6.2 at the edge of the band: candidate j is a copy of query j (so it
+    """Sec. 7.2 at the edge of the band: candidate j is a copy of query j (so it
     shares every bucket) placed on one of the two lines at 4 px from the
     query's epipolar line, moved by a few ulps or not at all.  The kernels'
     FP32 pre-test must defer these to the FP64 predicate and agree with the

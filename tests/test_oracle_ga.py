@@ -1,4 +1,4 @@
-"""Pins of the Ga-CasHash first-stage oracle (Sec. 5.1) against facts fixed
+"""Pins of the Ga-CasHash first-stage oracle (Sec. 7.1) against facts fixed
 outside it: brute-force ranks, the bijection of the sampling map, the
 normalisation's defining properties, exact recovery of a known F from
 noise-free views, the closest rank-2 matrix (Eckart-Young), the Sampson

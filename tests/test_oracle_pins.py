@@ -28,7 +28,7 @@ def _popcount_rows(codes_q, codes_c):
 
 
 # --------------------------------------------------------------------------
-# centring and projection (Sec. 4.1 hash functions)
+# centring and projection (Sec. 5.1 hash functions)
 # --------------------------------------------------------------------------
 
 def test_mean_is_correctly_rounded_rational_mean(orc):
@@ -314,7 +314,7 @@ def test_degenerate_images(orc):
 
 
 def test_tau_threshold_drops_far_candidates(orc):
-    """Sec. 5: candidates with Hamming distance above tau are not ranked."""
+    """Sec. 6: candidates with Hamming distance above tau are not ranked."""
     p0 = orc.params(top_k=10)
     dA, cA, bA, dB, cB, bB = _pair(orc, 60, 200, 220, p0)
     _, d0 = orc.match_pair(dA, cA, bA, dB, cB, bB, p0, detail=True)
@@ -345,7 +345,7 @@ def test_multi_pair_driver_equals_single_pairs(orc):
 
 
 # --------------------------------------------------------------------------
-# Sec. 6.2 epipolar band
+# Sec. 7.2 epipolar band
 # --------------------------------------------------------------------------
 
 def _two_views(rng):
@@ -405,7 +405,7 @@ def test_epipolar_predicate_against_geometry(orc):
 
 
 def test_epipolar_band_filters_before_ranking(orc):
-    """Sec. 6.2 step order: the band is applied to the lookup candidates
+    """Sec. 7.2 step order: the band is applied to the lookup candidates
     before the ranking, so every ranked candidate is inside the band, and
     with an infinite band the result equals the unguided one."""
     rng = np.random.default_rng(81)
