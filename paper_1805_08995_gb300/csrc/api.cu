@@ -578,9 +578,15 @@ int plan_configure(cashash_plan* pl, cashash_tuning t) {
     }
     pl->occ_grid = match_grid(c->p.top_k, 0, epi, c->p.n_tables, 0xFFFFFFFFu);
     t = cashash_tuning{};
-  } else if (t.kernel == CASHASH_KERNEL_JOIN) {
-    t.tile = (t.tile <= 2 && !epi) ? 2u : 4u;  // the band form has 4 candidate tiles only
-    grid = join_grid(c->kp, pl->na_max, P, t.tile, t.ctas_per_sm);
+  } else if (t.kernel == CASHASH_KERNEL_JOIN || t.kernel == CASHASH_KERNEL_JOIN_TC) {
+    if (t.kernel == CASHASH_KERNEL_JOIN) {
+      t.tile = (t.tile <= 2 && !epi) ? 2u : 4u;  // the band form has 4 candidate tiles only
+      grid = join_grid(c->kp, pl->na_max, P, t.tile, t.ctas_per_sm);
+    } else {
+      t.tile = 0;
+      t.ctas_per_sm = t.ctas_per_sm > 2 ? 0u : t.ctas_per_sm;
+      grid = join_tc_grid(c->kp, pl->na_max, P, t.ctas_per_sm);
+    }
     if (P && !grid) return CASHASH_ENOTSUP;
     join = true;
     // One item per pair.  The resident CTAs take consecutive items, so the
@@ -794,7 +800,8 @@ int enqueue_match(cashash_ctx* c, cashash_plan* pl, const double* F_dev, uint64_
     }
     {
       StageTimer tm(c, CASHASH_STAGE_MATCH, stream, capturing);
-      if (pl->join) CK(launch_join(a, pl->grid, pl->tune.tile, stream));
+      if (pl->join && pl->tune.kernel == CASHASH_KERNEL_JOIN_TC) CK(launch_join_tc(a, pl->grid, stream));
+      else if (pl->join) CK(launch_join(a, pl->grid, pl->tune.tile, stream));
       else CK(launch_match(a, 1, pl->grid, stream, pl->tune.tile));
     }
     {
@@ -981,6 +988,12 @@ int cashash_plan_autotune(cashash_ctx* c, cashash_plan* pl, const double* F_dev,
       t.ctas_per_sm = ctas;
       cand.push_back(t);
     }
+  for (uint32_t ctas : {0u, 1u}) {
+    cashash_tuning t{};
+    t.kernel = CASHASH_KERNEL_JOIN_TC;
+    t.ctas_per_sm = ctas;
+    cand.push_back(t);
+  }
   for (uint32_t tile : {512u, 256u}) {
     cashash_tuning t{};
     t.kernel = CASHASH_KERNEL_QUERY;
@@ -1120,7 +1133,9 @@ int cashash_get_stats(cashash_ctx* c, cashash_stats* out) {
 
 int cashash_set_host_tuning(cashash_ctx* c, const cashash_tuning* t) {
   if (!c) return CASHASH_EINVAL;
-  if (t && t->kernel != CASHASH_KERNEL_JOIN && t->kernel != CASHASH_KERNEL_QUERY) return CASHASH_EINVAL;
+  if (t && t->kernel != CASHASH_KERNEL_JOIN && t->kernel != CASHASH_KERNEL_JOIN_TC &&
+      t->kernel != CASHASH_KERNEL_QUERY)
+    return CASHASH_EINVAL;
   HostWS& h = c->hw;
   h.has_tune = t != nullptr;
   if (t) h.tune = *t;

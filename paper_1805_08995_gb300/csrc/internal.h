@@ -257,6 +257,12 @@ cudaError_t launch_join(const MatchArgs& a, uint32_t grid, uint32_t ntc, cudaStr
 // non-zero); 0 when the join does not apply (the largest query image exceeds
 // its shared memory).  The band form runs with 4 candidate tiles.
 uint32_t join_grid(const KParams& kp, uint32_t na_max, uint32_t n_items, uint32_t ntc, uint32_t ctas_per_sm);
+// The bucket join on tcgen05 tensor cores (same results as launch_join):
+// resident CTAs for n_items pairs (at most 2 per SM, ctas_per_sm when
+// non-zero and smaller), 0 when the largest query image exceeds its shared
+// memory; and the launch.
+uint32_t join_tc_grid(const KParams& kp, uint32_t na_max, uint32_t n_items, uint32_t ctas_per_sm);
+cudaError_t launch_join_tc(const MatchArgs& a, uint32_t grid, cudaStream_t s);
 // Matching kernel launch.  spec = 0: direct register top-k (one pair per
 // launch); spec = 1: survivor queues with a speculative threshold (batched).
 // tile: queries per CTA of the speculative form (256, or 512 when k <= 16; 0 = default).

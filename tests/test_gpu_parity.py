@@ -148,9 +148,10 @@ def test_parameter_variants(ch, orc, pk, sched):
     check_case(ch, orc, s, _pairs(sizes), schedule=sched, **pk)
 
 
+@pytest.mark.parametrize("kernel", ["join", "join_tc"])
 @pytest.mark.parametrize("hint,fixed", [(0, True), (30, True), (50, True), (53, True), (56, False), (0, False),
                                         (64, True), (100, True)])
-def test_speculative_threshold_never_changes_results(ch, orc, hint, fixed):
+def test_speculative_threshold_never_changes_results(ch, orc, hint, fixed, kernel):
     """The batched kernel's Hamming threshold is a guess; queries it starves
     are re-matched exactly.  Forcing bad guesses (0: every query falls back;
     near the median k-th distance: about half do; 64 and above: padding rows
@@ -164,6 +165,9 @@ def test_speculative_threshold_never_changes_results(ch, orc, hint, fixed):
     ds = ch.DeviceSet(p, s.img_off, s.desc)
     ch.cashash_build_codes(ctx, ds)
     plan = ch.cashash_plan_create(ctx, ds, pairs)
+    if kernel == "join_tc":
+        ch.cashash_plan_set_tuning(plan, ch.CASHASH_KERNEL_JOIN_TC)
+        assert ch.cashash_plan_get_tuning(plan)["kernel"] == ch.CASHASH_KERNEL_JOIN_TC
     ch.cashash_plan_set_threshold_hint(plan, hint, fixed)
     P = len(pairs)
     cap = int(s.sizes()[pairs[:, 0]].sum())
@@ -461,7 +465,7 @@ def test_identical_and_degenerate_descriptors(ch, orc):
 
 
 @pytest.mark.parametrize("flags", [0, 1, 3])
-@pytest.mark.parametrize("sched", [0, 1])
+@pytest.mark.parametrize("sched", [0, 1, "join_tc"])
 def test_epipolar_band(ch, orc, sched, flags):
     """Sec. 7.2: candidates outside the 4 px band around the query's
     epipolar line are removed before ranking (small config-4 style set)."""
@@ -470,10 +474,11 @@ def test_epipolar_band(ch, orc, sched, flags):
     assert len(s.pairs) >= 10 and s.kpts is not None
     both = np.concatenate([s.pairs, s.pairs[:, ::-1]])
     s.F = np.concatenate([s.F, s.F.reshape(-1, 3, 3).transpose(0, 2, 1).reshape(-1, 9)])
-    check_case(ch, orc, s, both, schedule=sched, epi_px=4.0, flags=flags)
+    tuning = (ch.CASHASH_KERNEL_JOIN_TC, 0, 0) if sched == "join_tc" else None
+    check_case(ch, orc, s, both, tuning=tuning, schedule=1 if tuning else sched, epi_px=4.0, flags=flags)
 
 
-@pytest.mark.parametrize("sched", [0, 1])
+@pytest.mark.parametrize("sched", [0, 1, "join_tc"])
 def test_band_edge_decisions(ch, orc, sched):
     """Sec. 7.2 at the edge of the band: candidate j is a copy of query j (so it
     shares every bucket) placed on one of the two lines at 4 px from the
@@ -508,7 +513,8 @@ def test_band_edge_decisions(ch, orc, sched):
     pairs = np.array([[0, 1]], np.uint32)
     s = synth.ImageSet(desc, img_off, pairs, synth.projection_matrix(515), "band edge", F=F.reshape(1, 9),
                        kpts=kpts)
-    check_case(ch, orc, s, pairs, schedule=sched, epi_px=d)
+    tuning = (ch.CASHASH_KERNEL_JOIN_TC, 0, 0) if sched == "join_tc" else None
+    check_case(ch, orc, s, pairs, tuning=tuning, schedule=1 if tuning else sched, epi_px=d)
 
 
 def test_many_pairs_medium(ch, orc):
@@ -516,15 +522,57 @@ def test_many_pairs_medium(ch, orc):
     check_case(ch, orc, s, s.pairs, schedule=1)
 
 
-@pytest.mark.parametrize("kernel", ["join", "query"])
+@pytest.mark.parametrize("kernel", ["join", "query", "join_tc"])
 @pytest.mark.parametrize("tau", [20, 30, 40, 50, 60, 128])
 def test_tau_sweep_values(ch, orc, tau, kernel):
     """Sec. 6 threshold at every value of the tau sweep (bench.py --tau-sweep),
     on a 12-image exhaustive set in the BF16 form, with the bucket join and
     with the per-query kernel."""
     s = synth.config1(seed=12, n_images=12, lo=3000, hi=9000)
-    tuning = (ch.CASHASH_KERNEL_JOIN, 4, 0) if kernel == "join" else (ch.CASHASH_KERNEL_QUERY, 512, 0)
+    tuning = {"join": (ch.CASHASH_KERNEL_JOIN, 4, 0), "query": (ch.CASHASH_KERNEL_QUERY, 512, 0),
+              "join_tc": (ch.CASHASH_KERNEL_JOIN_TC, 0, 0)}[kernel]
     check_case(ch, orc, s, s.pairs, tuning=tuning, schedule=1, precision=1, tau=tau)
+
+
+PARAM_VARIANTS = [
+    dict(top_k=4), dict(top_k=16), dict(top_k=32), dict(top_k=1), dict(top_k=2),
+    dict(bits_per_table=4, n_tables=3), dict(bits_per_table=0, n_tables=1, top_k=8),
+    dict(n_tables=8, bits_per_table=8), dict(n_tables=1, bits_per_table=5),
+    dict(code_bits=64), dict(code_bits=32, n_tables=2), dict(code_bits=96, n_tables=4, bits_per_table=6),
+    dict(tau=40), dict(tau=0), dict(ratio_num=9, ratio_den=10),
+    dict(flags=1), dict(flags=2), dict(flags=3), dict(flags=3, tau=50, top_k=4),
+]
+
+
+@pytest.mark.parametrize("pk", [dict(), dict(precision=1)] + PARAM_VARIANTS)
+def test_join_tc_parameter_variants(ch, orc, pk):
+    """The tcgen05 bucket join (FP8 +-1 rows in shared memory, 128-row tiles,
+    TMEM accumulators) with every parameter variant: k from 1 to 32, one
+    bucket per table (the whole candidate image in 256-column chunks), 32-,
+    64- and 96-bit codes, tau, the ratio, the mutual check and single
+    candidates; ragged image sizes including empty ones."""
+    sizes = [700, 1300, 0, 260, 4500]
+    s = synth.random_set(202, sizes)
+    check_case(ch, orc, s, _pairs(sizes), tuning=(ch.CASHASH_KERNEL_JOIN_TC, 0, 0), schedule=1, **pk)
+
+
+@pytest.mark.parametrize("case", ["ragged", "one_cta_per_sm", "huge_candidate", "medium"])
+def test_join_tc_workloads(ch, orc, case):
+    """The tcgen05 join on ragged image sizes (several tiles, ragged tails,
+    the chunk and table boundaries of the other kernels), with one CTA per
+    SM, with a candidate image of 70,000 features (tables by the global
+    scatter builder, long candidate runs), and on a 12-image exhaustive set."""
+    T = ch.CASHASH_KERNEL_JOIN_TC
+    if case == "ragged":
+        check_case(ch, orc, synth.random_set(101, SIZES), _pairs(SIZES), tuning=(T, 0, 0), schedule=1)
+    elif case == "one_cta_per_sm":
+        check_case(ch, orc, synth.random_set(101, SIZES), _pairs(SIZES), tuning=(T, 0, 1), schedule=1, precision=1)
+    elif case == "huge_candidate":
+        s = synth.random_set(808, [70000, 1500])
+        check_case(ch, orc, s, np.array([[1, 0]], np.uint32), tuning=(T, 0, 0), schedule=1)
+    else:
+        s = synth.config1(seed=11, n_images=12, lo=1500, hi=4500)
+        check_case(ch, orc, s, s.pairs, tuning=(T, 0, 0), schedule=1, precision=1)
 
 
 def test_capacity_overflow_reports_and_truncates(ch, orc):
