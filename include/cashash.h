@@ -153,6 +153,23 @@ void cashash_destroy(cashash_ctx* ctx);
 int cashash_build_codes(cashash_ctx* ctx, const cashash_set* set, const double* mean_host,
                         cashash_stream_t stream);
 
+/* Diagnostic of the rounding bound of the projection (Sec. 5.1; not needed
+ * for matching).  For features [first, first + count) of `set`, runs the
+ * context's projection form (precision FP32 or BF16) with the centre and row
+ * constants of the last cashash_build_codes on this context, and writes, row-
+ * major [count][rows] with rows = code_bits + n_tables * bits_per_table:
+ *   approx: the FP32 approximation v~_b - c_b of each projection
+ *           v_b = sum_j R_bj (x_j - mu_j), as the kernel computed it;
+ *   bound:  the bound E_b the kernel compares |approx| with (a projection with
+ *           |approx| <= E_b is re-evaluated exactly in double, any other takes
+ *           the sign of approx), valid when |approx - v_b| <= E_b.
+ * approx, bound: DEVICE, caller-allocated, 4-byte aligned.  The set's codes
+ * and tables are not written (the kernels' other outputs go to scratch that
+ * the call allocates and frees).  Synchronous on `stream`.
+ * Errors: EINVAL (no cashash_build_codes yet, bad range), ENOMEM, ECUDA. */
+int cashash_projection_bounds(cashash_ctx* ctx, const cashash_set* set, uint64_t first, uint64_t count,
+                              float* approx, float* bound, cashash_stream_t stream);
+
 /* The centre used by the last cashash_build_codes (HOST [128] out).
  * Synchronises the context's stream.  Errors: EINVAL, ECUDA. */
 int cashash_get_mean(cashash_ctx* ctx, double* mean_out);

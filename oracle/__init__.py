@@ -73,6 +73,8 @@ def _load():
             lib.oracle_mean.argtypes = [C.c_void_p, C.c_uint64, C.c_void_p]
             lib.oracle_projection.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
             lib.oracle_projection.restype = C.c_double
+            lib.oracle_projections.argtypes = [C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p, C.c_uint32,
+                                               C.c_void_p]
             lib.oracle_hash.argtypes = [C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p, P(Params), C.c_void_p,
                                         C.c_void_p]
             lib.oracle_match_pair.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p,
@@ -110,6 +112,31 @@ def projection(x, mu, rrow):
     mu = _c(mu, np.float64)
     rrow = _c(rrow, np.float64)
     return _load().oracle_projection(_ptr(x), _ptr(mu), _ptr(rrow))
+
+
+def projections(desc, mu, R, rows, threads=1):
+    """All ordered-double projections [n][rows] (row b of R against each
+    feature), in `threads` row blocks of features (ctypes releases the GIL)."""
+    desc = _c(desc, np.uint8).reshape(-1, DIM)
+    R = np.ascontiguousarray(_c(R, np.float64)[:rows])
+    mu = _c(mu, np.float64)
+    n = desc.shape[0]
+    v = np.zeros((n, rows), np.float64)
+    lib = _load()
+    step = max(1, (n + threads - 1) // threads)
+
+    def work(s0):
+        blk = np.ascontiguousarray(desc[s0:s0 + step])
+        out = np.zeros((blk.shape[0], rows), np.float64)
+        lib.oracle_projections(_ptr(blk), blk.shape[0], _ptr(mu), _ptr(R), rows, _ptr(out))
+        v[s0:s0 + step] = out
+
+    ts = [threading.Thread(target=work, args=(s0,)) for s0 in range(0, n, step)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    return v
 
 
 def hash_codes(desc, mu, R, p=None):

@@ -79,6 +79,16 @@ void oracle_hash(const uint8_t* desc, uint64_t n, const double* mu, const double
   }
 }
 
+/* Every projection of a block of features, v[f][b] = oracle_projection of
+ * feature f with row b of R, b < rows (the values whose signs oracle_hash
+ * takes); used to measure the GPU's rounding bounds. */
+void oracle_projections(const uint8_t* desc, uint64_t n, const double* mu, const double* R, uint32_t rows,
+                        double* v) {
+  for (uint64_t f = 0; f < n; ++f)
+    for (uint32_t b = 0; b < rows; ++b)
+      v[f * rows + b] = oracle_projection(desc + f * ORACLE_DIM, mu, R + (uint64_t)b * ORACLE_DIM);
+}
+
 /* Sec. 7.2, Eq. 1-2: the epipolar line of the query is l_q = F p_q with
  * p_q = (x, y, 1); a candidate p' = (x', y', 1) is kept when its distance to
  * l_q is at most d.  Eq. 2 as printed has no absolute value; the distance of

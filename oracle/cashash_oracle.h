@@ -87,6 +87,11 @@ double oracle_projection(const uint8_t* x /* [128] */, const double* mu, const d
 void oracle_hash(const uint8_t* desc, uint64_t n, const double* mu, const double* R,
                  const oracle_params* p, uint32_t* codes, uint8_t* buckets);
 
+/* All projections of n features against rows 0..rows-1 of R: v is [n][rows],
+ * each value the ordered double sum of oracle_projection. */
+void oracle_projections(const uint8_t* desc, uint64_t n, const double* mu, const double* R, uint32_t rows,
+                        double* v);
+
 /* Match one image pair (I = A queries, J = B candidates).  match[q] is the
  * matched index in B or -1.  F (row-major 3x3, x_B^T F x_A = 0) and the
  * key-points ([n][2] float x,y) are used only when p->epi_px >= 0.

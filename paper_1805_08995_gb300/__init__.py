@@ -104,6 +104,7 @@ def _load():
             "cashash_match_pair_noalloc": ([P(cashash_params), P(cashash_set), u32, u32, vp, vp, vp, u64, vp],
                                            C.c_int),
             "cashash_noalloc_status": ([vp], C.c_int),
+            "cashash_projection_bounds": ([vp, P(cashash_set), u64, u64, vp, vp, vp], C.c_int),
             "cashash_plan_get_tuning": ([vp, P(cashash_tuning)], C.c_int),
             "cashash_plan_set_tuning": ([vp, P(cashash_tuning)], C.c_int),
             "cashash_plan_autotune": ([vp, vp, vp, u32, vp], C.c_int),
@@ -135,7 +136,8 @@ def exported_symbols():
             "cashash_plan_set_threshold_hint", "cashash_plan_get_tuning", "cashash_plan_set_tuning",
             "cashash_plan_autotune", "cashash_match_chunked", "cashash_get_params", "cashash_ga_default_params",
             "cashash_ga_subset_offsets", "cashash_ga_select", "cashash_estimate_F", "cashash_ga_stage1",
-            "cashash_set_host_tuning", "cashash_get_host_tuning", "cashash_noalloc_status"]
+            "cashash_set_host_tuning", "cashash_get_host_tuning", "cashash_noalloc_status",
+            "cashash_projection_bounds"]
 
 
 def _check(st, what):
@@ -362,6 +364,18 @@ def cashash_match_pair_noalloc(params: cashash_params, dset: DeviceSet, image_a:
     _check(_load().cashash_match_pair_noalloc(C.byref(params), C.byref(dset.c), int(image_a), int(image_b),
                                               _dptr(F), _dptr(match_off), _dptr(matches), int(cap),
                                               _stream(stream)), "cashash_match_pair_noalloc")
+
+
+def cashash_projection_bounds(ctx: Context, dset: DeviceSet, first: int, count: int, stream=None):
+    """Diagnostic of the projection's rounding bound (see include/cashash.h):
+    returns device tensors (approx, bound), each [count][rows] float32."""
+    import torch
+    rows = ctx.params.code_bits + ctx.params.n_tables * ctx.params.bits_per_table
+    approx = torch.empty((max(count, 1), rows), dtype=torch.float32, device="cuda")
+    bound = torch.empty_like(approx)
+    _check(_load().cashash_projection_bounds(ctx.handle, C.byref(dset.c), int(first), int(count), _dptr(approx),
+                                             _dptr(bound), _stream(stream)), "cashash_projection_bounds")
+    return approx[:count], bound[:count]
 
 
 def cashash_noalloc_status(stream=None) -> int:

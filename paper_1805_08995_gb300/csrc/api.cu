@@ -68,6 +68,7 @@ struct cashash_ctx {
   uint64_t cap_if0 = 0, cap_in = 0, cap_ij = 0;
   cudaStream_t last_stream = nullptr;
   uint64_t last_n_features = 0;
+  int built = 0;                       // cashash_build_codes has run (centre and row constants set)
   uint64_t last_pairs = 0;
   uint64_t last_items = 0;
   uint64_t n_launches = 0;
@@ -524,7 +525,48 @@ int cashash_build_codes(cashash_ctx* c, const cashash_set* s, const double* mean
   }
   c->last_stream = stream;
   c->last_n_features = n;
+  c->built = 1;
   return CASHASH_OK;
+}
+
+int cashash_projection_bounds(cashash_ctx* c, const cashash_set* s, uint64_t first, uint64_t count,
+                              float* approx, float* bound, cashash_stream_t stream_) {
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+  uint64_t n_chunks = 0;
+  if (!c || !set_ok(s, &n_chunks) || !approx || !bound || !c->built) return CASHASH_EINVAL;
+  if (first > s->n_features || count > s->n_features - first) return CASHASH_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(approx) & 3) || (reinterpret_cast<uintptr_t>(bound) & 3)) return CASHASH_EINVAL;
+  if (count == 0) return CASHASH_OK;
+  CK(cudaSetDevice(c->device));
+  // the projection kernels' other outputs go to scratch, so the set is not touched
+  uint32_t *codes = nullptr, *sqn = nullptr, *fm = nullptr, *fl = nullptr;
+  uint8_t* bk = nullptr;
+  unsigned long long* cnt = nullptr;
+  uint64_t c1 = 0, c2 = 0, c3 = 0, c4 = 0, c5 = 0, c6 = 0;
+  int st = grow(codes, c1, 4 * count);
+  if (st == CASHASH_OK) st = grow(bk, c2, 8 * count);
+  if (st == CASHASH_OK) st = grow(sqn, c3, count);
+  if (st == CASHASH_OK) st = grow(fm, c4, 6 * count);
+  if (st == CASHASH_OK) st = grow(fl, c5, count);
+  if (st == CASHASH_OK) st = grow(cnt, c6, 2);
+  if (st == CASHASH_OK) st = cuda_err(cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), stream));
+  const uint8_t* d = s->desc + first * DIM;
+  if (st == CASHASH_OK) {
+    if (c->p.precision == CASHASH_BF16)
+      st = cuda_err(launch_project_bf16(d, count, c->d_Rbf, c->np_tc, c->d_rc, c->kp, codes, bk, sqn, fm, fl, cnt,
+                                        c->d_status, stream, approx, bound));
+    else
+      st = cuda_err(launch_project_fp32(d, count, c->d_R32T, c->d_rc, c->kp, codes, bk, sqn, fm, fl, cnt, stream,
+                                        approx, bound));
+  }
+  if (st == CASHASH_OK) st = cuda_err(cudaStreamSynchronize(stream));
+  dfree(codes);
+  dfree(bk);
+  dfree(sqn);
+  dfree(fm);
+  dfree(fl);
+  dfree(cnt);
+  return st;
 }
 
 int cashash_get_mean(cashash_ctx* c, double* mean_out) {

@@ -121,7 +121,8 @@ __global__ void __launch_bounds__(256, 1) k_project_fp32(const uint8_t* __restri
                                                          uint32_t* __restrict__ sqnorm,
                                                          uint32_t* __restrict__ flagmask,
                                                          uint32_t* __restrict__ flaglist,
-                                                         unsigned long long* __restrict__ nflag_feat) {
+                                                         unsigned long long* __restrict__ nflag_feat,
+                                                         float* __restrict__ dbg_x, float* __restrict__ dbg_e) {
   extern __shared__ __align__(16) float psm[];
   float* Rs = psm;                       // [128][192]  R32 transposed (j-major)
   float* xs = Rs + DIM * PT_R;           // [128][64]   x as float (j-major)
@@ -207,6 +208,10 @@ __global__ void __launch_bounds__(256, 1) k_project_fp32(const uint8_t* __restri
           const RowConst r = rc[row];
           const float v = acc[a][b] - r.c32;
           const float E = __fmaf_ru(r.alpha, nx, r.beta);
+          if (dbg_x && f0 + fl < n) {  // diagnostic of the bound (cashash_projection_bounds)
+            dbg_x[(f0 + fl) * kp.rows + row] = v;
+            dbg_e[(f0 + fl) * kp.rows + row] = E;
+          }
           if (fabsf(v) <= E) atomicOr(&sflag[fl][row >> 5], 1u << (row & 31));
           else if (v > 0.f) atomicOr(&sbits[fl][row >> 5], 1u << (row & 31));
         }
@@ -222,7 +227,7 @@ __global__ void __launch_bounds__(256, 1) k_project_fp32(const uint8_t* __restri
 cudaError_t launch_project_fp32(const uint8_t* desc, uint64_t n, const float* R32T, const RowConst* rc,
                                 const KParams& kp, uint32_t* codes, uint8_t* buckets, uint32_t* sqnorm,
                                 uint32_t* flagmask, uint32_t* flaglist, unsigned long long* nflag_feat,
-                                cudaStream_t s) {
+                                cudaStream_t s, float* dbg_x, float* dbg_e) {
   if (n == 0) return cudaSuccess;
   const size_t smem = (size_t)DIM * PT_R * 4 + (size_t)DIM * PT_F * 4;
   cudaError_t e = cudaFuncSetAttribute(k_project_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -233,7 +238,7 @@ cudaError_t launch_project_fp32(const uint8_t* desc, uint64_t n, const float* R3
   const uint64_t ntiles = (n + PT_F - 1) / PT_F;
   const int grid = (int)(ntiles < (uint64_t)nsm ? ntiles : (uint64_t)nsm);
   k_project_fp32<<<grid, 256, smem, s>>>(desc, n, R32T, rc, kp, codes, buckets, sqnorm, flagmask, flaglist,
-                                         nflag_feat);
+                                         nflag_feat, dbg_x, dbg_e);
   return cudaGetLastError();
 }
 

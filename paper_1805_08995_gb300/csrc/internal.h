@@ -205,11 +205,13 @@ cudaError_t launch_row_consts(const unsigned long long* sums, uint64_t n, int ha
 cudaError_t launch_project_fp32(const uint8_t* desc, uint64_t n, const float* R32T, const RowConst* rc,
                                 const KParams& kp, uint32_t* codes, uint8_t* buckets, uint32_t* sqnorm,
                                 uint32_t* flagmask, uint32_t* flaglist, unsigned long long* nflag_feat,
-                                cudaStream_t s);
+                                cudaStream_t s, float* dbg_x = nullptr, float* dbg_e = nullptr);
 cudaError_t launch_project_bf16(const uint8_t* desc, uint64_t n, const void* Rbf, uint32_t NP, const RowConst* rc,
                                 const KParams& kp, uint32_t* codes, uint8_t* buckets, uint32_t* sqnorm,
                                 uint32_t* flagmask, uint32_t* flaglist, unsigned long long* nflag_feat,
-                                uint32_t* status, cudaStream_t s);
+                                uint32_t* status, cudaStream_t s, float* dbg_x = nullptr, float* dbg_e = nullptr);
+// (dbg_x, dbg_e: when non-null, [n][rows] FP32 approximation v~ - c and bound E of
+// every projection, for cashash_projection_bounds; null in the matching path.)
 cudaError_t launch_fix_fp64(const uint8_t* desc, const double* mu, const double* R, const KParams& kp,
                             const uint32_t* flagmask, const uint32_t* flaglist,
                             const unsigned long long* nflag_feat, uint64_t max_feat, uint32_t* codes,

@@ -78,7 +78,9 @@ __global__ void __launch_bounds__(PT_THREADS, 1) k_project_bf16(const uint8_t* _
                                                                 uint32_t* __restrict__ flagmask,
                                                                 uint32_t* __restrict__ flaglist,
                                                                 unsigned long long* __restrict__ nflag_feat,
-                                                                uint32_t* __restrict__ status) {
+                                                                uint32_t* __restrict__ status,
+                                                                float* __restrict__ dbg_x,
+                                                                float* __restrict__ dbg_e) {
   extern __shared__ __align__(1024) uint8_t tsm[];
   __shared__ __align__(8) uint64_t s_mbar[2];
   __shared__ uint32_t s_tmem;
@@ -211,6 +213,10 @@ __global__ void __launch_bounds__(PT_THREADS, 1) k_project_bf16(const uint8_t* _
             const RowConst rw = rc[row];
             const float x = __uint_as_float(r3[u][i]) - rw.c32;
             const float E = __fmaf_ru(rw.alpha, nx, rw.beta);
+            if (dbg_x && f < n) {  // diagnostic of the bound (cashash_projection_bounds)
+              dbg_x[f * kp.rows + row] = x;
+              dbg_e[f * kp.rows + row] = E;
+            }
             if (fabsf(x) <= E) flags[lr >> 5] |= 1u << (lr & 31);
             else if (x > 0.f) bits[lr >> 5] |= 1u << (lr & 31);
           }
@@ -242,7 +248,7 @@ __global__ void __launch_bounds__(PT_THREADS, 1) k_project_bf16(const uint8_t* _
 cudaError_t launch_project_bf16(const uint8_t* desc, uint64_t n, const void* Rbf, uint32_t NP, const RowConst* rc,
                                 const KParams& kp, uint32_t* codes, uint8_t* buckets, uint32_t* sqnorm,
                                 uint32_t* flagmask, uint32_t* flaglist, unsigned long long* nflag_feat,
-                                uint32_t* status, cudaStream_t s) {
+                                uint32_t* status, cudaStream_t s, float* dbg_x, float* dbg_e) {
   if (n == 0) return cudaSuccess;
   if (NP % 16 || NP < 16 || NP > PT_ROWS_TC) return cudaErrorInvalidValue;
   const size_t smem = 2 * (size_t)TC_M * TC_K * 2 + 2 * (size_t)NP * TC_K * 2;
@@ -260,7 +266,8 @@ cudaError_t launch_project_bf16(const uint8_t* desc, uint64_t n, const void* Rbf
   const uint64_t ntiles = (n + TC_M - 1) / TC_M, pairs = (ntiles + 1) / 2;  // two tiles in flight per CTA
   const int grid = (int)(pairs < (uint64_t)nsm ? pairs : (uint64_t)nsm);
   k_project_bf16<<<grid, PT_THREADS, smem, s>>>(desc, n, reinterpret_cast<const uint4*>(Rbf), NP, rc, kp, codes,
-                                                buckets, sqnorm, flagmask, flaglist, nflag_feat, status);
+                                                buckets, sqnorm, flagmask, flaglist, nflag_feat, status, dbg_x,
+                                                dbg_e);
   return cudaGetLastError();
 }
 

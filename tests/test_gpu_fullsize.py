@@ -236,3 +236,70 @@ def test_config4_ga_stage1_full_size(ch):
     assert np.abs(F[pick] - eF).max() <= 1e-8
     ctx1.close()
     ctx2.close()
+
+
+def _bound_margins(ch, orc, s, ctx, ds, mu, rows, feats, chunk=100_000):
+    """Over the features `feats` (ascending ranges): the largest |v~ - v| / E
+    over all projections and over the unflagged ones (|v~| > E, which take the
+    sign of v~), and the number flagged; asserts the bound holds everywhere."""
+    worst_all, worst_unflagged, flagged = 0.0, 0.0, 0
+    for lo, hi in feats:
+        for f0 in range(lo, hi, chunk):
+            n = min(chunk, hi - f0)
+            approx, bound = ch.cashash_projection_bounds(ctx, ds, f0, n)
+            a = approx.cpu().numpy().astype(np.float64)
+            e = bound.cpu().numpy().astype(np.float64)
+            v = orc.projections(s.desc[f0:f0 + n], mu, s.R, rows, threads=16)
+            err = np.abs(a - v)
+            assert (err <= e).all(), "bound violated at %s" % (np.argwhere(err > e)[:4] + [f0, 0]).tolist()
+            r = err / e
+            fl = np.abs(a) <= e
+            flagged += int(fl.sum())
+            worst_all = max(worst_all, float(r.max()))
+            if (~fl).any():
+                worst_unflagged = max(worst_unflagged, float(r[~fl].max()))
+    return worst_all, worst_unflagged, flagged
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_projection_bound_margins_config1(ch, orc, precision):
+    """The rounding bound E of the projection (FP32 form: 2^-16 ||R_b|| ||x||
+    + beta_b; BF16 form: 2^-15 ||R_b|| ||x|| + beta_b, which assumes a
+    pessimistic adder model for the tensor cores' FP32 accumulation) against
+    the oracle's exact ordered-double values on every feature of config 1:
+    |v~ - v| <= E everywhere, the flagged count is the library's re-evaluation
+    count, and the largest |v~ - v| / E over the unflagged projections is
+    below 0.5 (the bound holds with a factor of two to spare)."""
+    s = synth.config1()
+    p = ch.cashash_default_params(precision=precision)
+    ctx = ch.cashash_create(p, s.R)
+    ds = ch.DeviceSet(p, s.img_off, s.desc)
+    ch.cashash_build_codes(ctx, ds)
+    mu = ch.cashash_get_mean(ctx)
+    n_reeval = ch.cashash_get_stats(ctx)["n_reevaluated"]
+    rows = 128 + 6 * 8
+    worst_all, worst_unflagged, flagged = _bound_margins(ch, orc, s, ctx, ds, mu, rows, [(0, s.desc.shape[0])])
+    print("config1 precision %d: max |v~-v|/E all %.4g, unflagged %.4g, flagged %d"
+          % (precision, worst_all, worst_unflagged, flagged))
+    assert flagged == n_reeval
+    assert worst_unflagged < 0.5
+    ctx.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_projection_bound_margins_config3_sample(ch, orc, precision):
+    """The same on 30 sampled config-3 images (1,000 to 20,000 features)."""
+    s = synth.config3()
+    p = ch.cashash_default_params(precision=precision)
+    ctx = ch.cashash_create(p, s.R)
+    ds = ch.DeviceSet(p, s.img_off, s.desc)
+    ch.cashash_build_codes(ctx, ds)
+    mu = ch.cashash_get_mean(ctx)
+    rows = 128 + 6 * 8
+    pick = np.sort(np.random.default_rng(33).choice(s.n_images, 30, replace=False))
+    feats = [(int(s.img_off[i]), int(s.img_off[i + 1])) for i in pick]
+    worst_all, worst_unflagged, flagged = _bound_margins(ch, orc, s, ctx, ds, mu, rows, feats)
+    print("config3 sample precision %d: max |v~-v|/E all %.4g, unflagged %.4g, flagged %d over %d features"
+          % (precision, worst_all, worst_unflagged, flagged, sum(b - a for a, b in feats)))
+    assert worst_unflagged < 0.5
+    ctx.close()

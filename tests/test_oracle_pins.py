@@ -71,6 +71,33 @@ def test_projection_sign_matches_exact_rational_sign(orc):
     assert checked == 512
 
 
+def test_block_projections_are_the_pinned_projection_and_give_the_codes(orc):
+    """oracle.projections (the values the GPU's rounding bounds are measured
+    against) equals the pinned per-element projection bit for bit, and its
+    signs reproduce oracle_hash's code bits and bucket ids."""
+    rng = np.random.default_rng(21)
+    desc = synth.sift_like(rng, 300)
+    mu = orc.mean(desc)
+    R = synth.projection_matrix(21)
+    po = orc.params()
+    rows = 128 + 6 * 8
+    v = orc.projections(desc, mu, R, rows, threads=3)
+    for f in (0, 7, 150, 299):
+        for b in (0, 31, 127, 128, 175):
+            assert v[f, b] == orc.projection(desc[f], mu, R[b])
+    codes, buckets = orc.hash_codes(desc, mu, R, po)
+    bits = (v > 0.0)
+    words = np.zeros((300, 4), np.uint32)
+    for b in range(128):
+        words[:, b // 32] |= bits[:, b].astype(np.uint32) << np.uint32(b % 32)
+    assert np.array_equal(words, codes)
+    ids = np.zeros((300, 6), np.uint8)
+    for t in range(6):
+        for i in range(8):
+            ids[:, t] |= (bits[:, 128 + 8 * t + i].astype(np.uint8) << np.uint8(i))
+    assert np.array_equal(ids, buckets)
+
+
 def test_projection_near_zero_cases(orc):
     """Rows built so that the projection nearly cancels: the double result
     stays within the bound of the exact rational value and keeps its sign
