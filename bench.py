@@ -39,19 +39,23 @@ L2_FLUSH_BYTES = 256 << 20
 # DRAM traffic per lookup entry of the matching kernel, from the ncu capture
 # summarised in profiles/ (valid only for the kernel source it was taken on).
 PROFILED_TRAFFIC = {
-    "k_join": {"source": "paper_1805_08995_gb300/csrc/join.cu",
-               "sha256": "ca98528b4ced70add782bcc2c8dc1c42508a4395b14f6b0133e66656becaf0ef",
-               "bytes_per_entry": (2.494724e9 + 1.099983e9) / 861951265},
+    "k_join": {"sources": ["paper_1805_08995_gb300/csrc/join.cu", "paper_1805_08995_gb300/csrc/join_common.cuh"],
+               "sha256": "a1dab5f155c92f817855de3c9e61a8b14c143b1e81d27147a209148ec7af7658",
+               "bytes_per_entry": (2.386088e9 + 1.099653e9) / 861951265},
 }
 
 
-def source_sha256(rel: str):
+def source_sha256(rels):
+    """SHA-256 of the concatenated kernel sources (None if one is missing)."""
     import hashlib
+    h = hashlib.sha256()
     try:
-        with open(os.path.join(ROOT, rel), "rb") as f:
-            return hashlib.sha256(f.read()).hexdigest()
+        for rel in rels:
+            with open(os.path.join(ROOT, rel), "rb") as f:
+                h.update(f.read())
     except OSError:
         return None
+    return h.hexdigest()
 
 
 def peaks():
@@ -305,7 +309,7 @@ def roofline_of(ch, p, s, ds, stage_ms, tuning, n_sm):
     achieved = touched / t_match / 1e9
     traffic = None
     prof = PROFILED_TRAFFIC.get(kernel)
-    if prof and prof["sha256"] == source_sha256(prof["source"]):
+    if prof and prof["sha256"] == source_sha256(prof["sources"]):
         traffic = prof["bytes_per_entry"] * entries
     sm_mhz = pk.get("sm_max_mhz", 2070.0)
     ent_peak = POPC_PER_CLK_SM / 4.0 * n_sm * sm_mhz * 1e6
