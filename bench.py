@@ -488,12 +488,14 @@ def run_ours(args):
         mo_h = torch.zeros(P + 1, dtype=torch.int64).pin_memory().numpy().view(np.uint64)
         mt_h = torch.zeros((cap, 2), dtype=torch.int32).pin_memory().numpy().view(np.uint32)
         ctx2 = ch.cashash_create(p, s.R)
+        ch.cashash_set_profiling(ctx2, True)  # per-call copy and device stage times (events)
         if tuning.get("kernel"):  # the host path matches with the same configuration as the timed plan
             ch.cashash_set_host_tuning(ctx2, tuning["kernel"], tuning["tile"], tuning["ctas_per_sm"])
         for _ in range(max(1, args.warmup)):
             ch.cashash_run_host(ctx2, pinned, s.img_off, s.pairs, cap, match_off=mo_h, matches=mt_h,
                                 kpts=kp_pin, F=s.F if band else None)
-        ts = []
+        ts, parts = [], []
+        dev_stages = ("centre", "project", "reeval", "tables", "calibrate", "match", "fallback", "compact")
         for _ in range(args.steps):
             flush.zero_()
             torch.cuda.synchronize()
@@ -502,6 +504,9 @@ def run_ours(args):
                                                matches=mt_h, kpts=kp_pin, F=s.F if band else None)
             ts.append(time.perf_counter() - t0)
             assert st == ch.CASHASH_OK
+            ms = ch.cashash_get_stats(ctx2)["ms_stage"]
+            dev_ms = sum(max(ms[k], 0.0) for k in dev_stages)
+            parts.append((ms["h2d"], dev_ms, ms["d2h"], ts[-1] * 1e3 - ms["h2d"] - dev_ms - ms["d2h"]))
         t_e2e = statistics.mean(ts)
         if dist:
             tt = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
@@ -512,7 +517,12 @@ def run_ours(args):
                "ms_each": [round(t * 1e3, 2) for t in ts],
                "h2d_bytes_per_step": int(s.desc.nbytes + 8 * (len(s.img_off)) +
                                          (s.kpts.nbytes + s.F.nbytes if band else 0)),
-               "d2h_bytes_per_step": int(8 * (P + 1) + 8 * n_m)}
+               "d2h_bytes_per_step": int(8 * (P + 1) + 8 * n_m),
+               "breakdown_ms_each": {"h2d": [round(x[0], 3) for x in parts], "device": [round(x[1], 3) for x in parts],
+                                     "d2h": [round(x[2], 3) for x in parts],
+                                     "host_other": [round(x[3], 3) for x in parts]},
+               "breakdown_note": "device = the stages on the compute stream after the last copy (the column "
+                                 "sums overlap the copy); host_other = wall - h2d - device - d2h"}
         if parity is not None:  # the host path's lists of the sampled pairs too
             e2e["parity_mismatches"] = parity_check(smp, torch.from_numpy(mo_h.view(np.int64)),
                                                     torch.from_numpy(mt_h.view(np.int32)))["mismatches"]

@@ -276,7 +276,10 @@ int cashash_sync_status(cashash_ctx* ctx, cashash_stream_t stream);
 /* End-to-end from HOST buffers: stages descriptors host -> device through
  * pinned buffers on a side stream (chunks of at most stage_bytes, 0 = 4 GiB),
  * builds codes and tables, matches every pair, and copies match_off and the
- * matches back.  desc_host: HOST [img_off[n_images]][128]; kpts_host /
+ * matches back.  The column sums of the centre are taken block by block (at
+ * most 256 MiB) as each block lands, overlapping the rest of the copy; the
+ * projections wait for the whole set (their centre is its mean).  With
+ * profiling on, the copies are timed as stages H2D and D2H.  desc_host: HOST [img_off[n_images]][128]; kpts_host /
  * F_host may be NULL unless epi_px >= 0.  match_off_host: HOST [P + 1];
  * matches_host: HOST [cap][2].  Synchronous.  Errors: EINVAL, ENOMEM, ECUDA,
  * EOVERFLOW (match_off_host complete, matches truncated to cap), EDEVICE. */
@@ -379,7 +382,9 @@ enum {
   CASHASH_STAGE_COMPACT = 5,    /* per-pair offsets and compaction of the match lists */
   CASHASH_STAGE_CALIBRATE = 6,  /* batched schedule: per-pair Hamming threshold guesses */
   CASHASH_STAGE_FALLBACK = 7,   /* batched schedule: exact re-matching of the queries left pending */
-  CASHASH_N_STAGES = 8
+  CASHASH_STAGE_H2D = 8,        /* cashash_run_host: host -> device copies of the inputs (copy stream) */
+  CASHASH_STAGE_D2H = 9,        /* cashash_run_host: device -> host copies of the match lists */
+  CASHASH_N_STAGES = 10
 };
 
 /* Counters of the last build/match calls (host copies after the call's stream sync). */

@@ -46,8 +46,8 @@ class cashash_set(C.Structure):
                 ("sqnorm", C.c_void_p), ("tables", C.c_void_p), ("kpts", C.c_void_p)]
 
 
-N_STAGES = 8
-STAGES = ("centre", "project", "reeval", "tables", "match", "compact", "calibrate", "fallback")
+N_STAGES = 10
+STAGES = ("centre", "project", "reeval", "tables", "match", "compact", "calibrate", "fallback", "h2d", "d2h")
 
 
 class cashash_stats(C.Structure):

@@ -69,6 +69,10 @@ struct cashash_ctx {
   cudaStream_t last_stream = nullptr;
   uint64_t last_n_features = 0;
   int built = 0;                       // cashash_build_codes has run (centre and row constants set)
+  std::vector<uint64_t> layout_off;    // image offsets of the uploaded layout arrays
+  const void* layout_bufs[5] = {};     // the buffers they were uploaded to
+  bool layout_ok = false;
+  cudaEvent_t layout_ev = nullptr;     // recorded after the last upload
   uint64_t last_pairs = 0;
   uint64_t last_items = 0;
   uint64_t n_launches = 0;
@@ -284,6 +288,108 @@ void join_layout(const uint64_t* img_off, uint32_t n_images, uint32_t T, std::ve
 // ---------------------------------------------------------------------------
 // C-ABI
 // ---------------------------------------------------------------------------
+namespace {
+// cashash_build_codes; sums_ready: the column sums of the set are already in
+// c->d_colsum (taken block by block while the host path stages the set).
+int build_codes_impl(cashash_ctx* c, const cashash_set* s, const double* mean_host, cudaStream_t stream,
+                     bool sums_ready) {
+  uint64_t n_chunks = 0;
+  if (!c || !set_ok(s, &n_chunks)) return CASHASH_EINVAL;
+  if (mean_host)
+    for (int j = 0; j < DIM; ++j)
+      if (!std::isfinite(mean_host[j])) return CASHASH_EINVAL;
+  const uint64_t n = s->n_features;
+  CK(cudaSetDevice(c->device));
+  int st = grow(c->d_flagmask, c->cap_flagmask, std::max<uint64_t>(n, 1) * 6);
+  if (st == CASHASH_OK) st = grow(c->d_flaglist, c->cap_flaglist, std::max<uint64_t>(n, 1));
+  if (st == CASHASH_OK) st = grow(c->d_chunk_feat0, c->cap_cf0, std::max<uint64_t>(n_chunks, 1));
+  if (st == CASHASH_OK) st = grow(c->d_chunk_len, c->cap_clen, std::max<uint64_t>(n_chunks, 1));
+  const uint64_t ni = std::max<uint32_t>(s->n_images, 1);
+  if (st == CASHASH_OK) st = grow(c->d_img_f0, c->cap_if0, ni);
+  if (st == CASHASH_OK) st = grow(c->d_img_n, c->cap_in, ni);
+  if (st == CASHASH_OK) st = grow(c->d_img_join, c->cap_ij, ni);
+  if (st != CASHASH_OK) return st;
+  std::vector<uint32_t> inn(s->n_images);
+  for (uint32_t i = 0; i < s->n_images; ++i) inn[i] = (uint32_t)(s->img_off[i + 1] - s->img_off[i]);
+  // Layout arrays of the set (image and chunk offsets, table bases): uploaded
+  // again only when the image offsets (or the buffers holding them) changed.
+  const void* bufs[5] = {c->d_img_f0, c->d_img_n, c->d_img_join, c->d_chunk_feat0, c->d_chunk_len};
+  const bool same_layout = c->layout_ok && c->layout_off.size() == (size_t)s->n_images + 1 &&
+                           std::memcmp(c->layout_off.data(), s->img_off, 8 * ((size_t)s->n_images + 1)) == 0 &&
+                           std::memcmp(c->layout_bufs, bufs, sizeof bufs) == 0;
+  if (same_layout) {
+    CK(cudaStreamWaitEvent(stream, c->layout_ev, 0));  // the uploads, if another stream made them
+  } else {
+    c->layout_ok = false;
+    std::vector<uint64_t> jbase, if0(s->img_off, s->img_off + s->n_images);
+    join_layout(s->img_off, s->n_images, c->p.n_tables, jbase);
+    if (s->n_images) {
+      CK(cudaMemcpyAsync(c->d_img_f0, if0.data(), s->n_images * sizeof(uint64_t), cudaMemcpyHostToDevice, stream));
+      CK(cudaMemcpyAsync(c->d_img_n, inn.data(), s->n_images * sizeof(uint32_t), cudaMemcpyHostToDevice, stream));
+      CK(cudaMemcpyAsync(c->d_img_join, jbase.data(), s->n_images * sizeof(uint64_t), cudaMemcpyHostToDevice,
+                         stream));
+    }
+    std::vector<uint64_t> f0;
+    std::vector<uint32_t> len;
+    chunk_layout(s->img_off, s->n_images, f0, len, nullptr);
+    if (n_chunks) {
+      CK(cudaMemcpyAsync(c->d_chunk_feat0, f0.data(), n_chunks * sizeof(uint64_t), cudaMemcpyHostToDevice, stream));
+      CK(cudaMemcpyAsync(c->d_chunk_len, len.data(), n_chunks * sizeof(uint32_t), cudaMemcpyHostToDevice, stream));
+    }
+    if (!c->layout_ev) CK(cudaEventCreateWithFlags(&c->layout_ev, cudaEventDisableTiming));
+    CK(cudaEventRecord(c->layout_ev, stream));
+    c->layout_off.assign(s->img_off, s->img_off + s->n_images + 1);
+    std::memcpy(c->layout_bufs, bufs, sizeof bufs);
+    c->layout_ok = true;
+  }
+  for (int i = 0; i < 4; ++i) c->ev_used[i] = 0;
+  {  // centre (reading: mean over the whole set) and per-row constants
+    StageTimer tm(c, CASHASH_STAGE_CENTRE, stream);
+    if (mean_host) {
+      CK(cudaMemcpyAsync(c->d_mu, mean_host, DIM * sizeof(double), cudaMemcpyHostToDevice, stream));
+    } else if (!sums_ready) {
+      CK(launch_colsum(s->desc, n, c->d_colsum, stream));
+      c->n_launches += n ? 1 : 0;
+    }
+    // bound factor on ||R_b|| ||x||: FP32 FMA chains (2^-16), BF16 tensor cores (2^-15)
+    const float alpha_scale = c->p.precision == CASHASH_BF16 ? 0x1p-15f : 0x1p-16f;
+    CK(launch_row_consts(c->d_colsum, n, mean_host ? 1 : 0, c->d_mu, c->d_R, c->d_nrmR, c->rows, alpha_scale,
+                         c->d_rc, stream));
+    c->n_launches += 1;
+    CK(cudaMemsetAsync(c->d_cnt, 0, 2 * sizeof(unsigned long long), stream));
+  }
+  if (n) {
+    {
+      StageTimer tm(c, CASHASH_STAGE_PROJECT, stream);
+      if (c->p.precision == CASHASH_BF16)
+        CK(launch_project_bf16(s->desc, n, c->d_Rbf, c->np_tc, c->d_rc, c->kp, s->codes, s->buckets, s->sqnorm,
+                               c->d_flagmask, c->d_flaglist, c->d_cnt + 0, c->d_status, stream));
+      else
+        CK(launch_project_fp32(s->desc, n, c->d_R32T, c->d_rc, c->kp, s->codes, s->buckets, s->sqnorm, c->d_flagmask,
+                               c->d_flaglist, c->d_cnt + 0, stream));
+    }
+    {
+      StageTimer tm(c, CASHASH_STAGE_REEVAL, stream);
+      CK(launch_fix_fp64(s->desc, c->d_mu, c->d_R, c->kp, c->d_flagmask, c->d_flaglist, c->d_cnt + 0, n, s->codes,
+                         s->buckets, c->d_cnt + 1, stream));
+    }
+    {
+      StageTimer tm(c, CASHASH_STAGE_TABLES, stream);
+      CK(launch_build_tables(s->buckets, c->d_chunk_feat0, c->d_chunk_len, (uint32_t)n_chunks, c->p.n_tables,
+                             s->tables, stream));
+      const uint32_t n_max = inn.empty() ? 0u : *std::max_element(inn.begin(), inn.end());
+      CK(launch_build_join(s->buckets, s->codes, c->d_img_f0, c->d_img_n, c->d_img_join, s->n_images, c->p.n_tables,
+                           n_max, s->tables, stream));
+    }
+    c->n_launches += 4;
+  }
+  c->last_stream = stream;
+  c->last_n_features = n;
+  c->built = 1;
+  return CASHASH_OK;
+}
+}  // namespace
+
 extern "C" {
 
 const char* cashash_strerror(int st) {
@@ -346,6 +452,7 @@ void cashash_destroy(cashash_ctx* c) {
     if (h.ev[i]) cudaEventDestroy(h.ev[i]);
   }
   if (h.staged) cudaEventDestroy(h.staged);
+  if (c->layout_ev) cudaEventDestroy(c->layout_ev);
   if (h.copy) cudaStreamDestroy(h.copy);
   if (h.comp) cudaStreamDestroy(h.comp);
   dfree(c->d_R); dfree(c->d_nrmR); dfree(c->d_R32T); dfree(c->d_Rbf); dfree(c->d_mu); dfree(c->d_rc);
@@ -446,88 +553,9 @@ int cashash_create(cashash_ctx** out, const cashash_params* p, const double* R_h
 }
 
 int cashash_build_codes(cashash_ctx* c, const cashash_set* s, const double* mean_host, cashash_stream_t stream_) {
-  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
-  uint64_t n_chunks = 0;
-  if (!c || !set_ok(s, &n_chunks)) return CASHASH_EINVAL;
-  if (mean_host)
-    for (int j = 0; j < DIM; ++j)
-      if (!std::isfinite(mean_host[j])) return CASHASH_EINVAL;
-  const uint64_t n = s->n_features;
-  CK(cudaSetDevice(c->device));
-  int st = grow(c->d_flagmask, c->cap_flagmask, std::max<uint64_t>(n, 1) * 6);
-  if (st == CASHASH_OK) st = grow(c->d_flaglist, c->cap_flaglist, std::max<uint64_t>(n, 1));
-  if (st == CASHASH_OK) st = grow(c->d_chunk_feat0, c->cap_cf0, std::max<uint64_t>(n_chunks, 1));
-  if (st == CASHASH_OK) st = grow(c->d_chunk_len, c->cap_clen, std::max<uint64_t>(n_chunks, 1));
-  const uint64_t ni = std::max<uint32_t>(s->n_images, 1);
-  if (st == CASHASH_OK) st = grow(c->d_img_f0, c->cap_if0, ni);
-  if (st == CASHASH_OK) st = grow(c->d_img_n, c->cap_in, ni);
-  if (st == CASHASH_OK) st = grow(c->d_img_join, c->cap_ij, ni);
-  if (st != CASHASH_OK) return st;
-  std::vector<uint64_t> jbase, if0(s->n_images);
-  std::vector<uint32_t> inn(s->n_images);
-  join_layout(s->img_off, s->n_images, c->p.n_tables, jbase);
-  for (uint32_t i = 0; i < s->n_images; ++i) {
-    if0[i] = s->img_off[i];
-    inn[i] = (uint32_t)(s->img_off[i + 1] - s->img_off[i]);
-  }
-  if (s->n_images) {
-    CK(cudaMemcpyAsync(c->d_img_f0, if0.data(), s->n_images * sizeof(uint64_t), cudaMemcpyHostToDevice, stream));
-    CK(cudaMemcpyAsync(c->d_img_n, inn.data(), s->n_images * sizeof(uint32_t), cudaMemcpyHostToDevice, stream));
-    CK(cudaMemcpyAsync(c->d_img_join, jbase.data(), s->n_images * sizeof(uint64_t), cudaMemcpyHostToDevice, stream));
-  }
-  std::vector<uint64_t> f0;
-  std::vector<uint32_t> len;
-  chunk_layout(s->img_off, s->n_images, f0, len, nullptr);
-  if (n_chunks) {
-    CK(cudaMemcpyAsync(c->d_chunk_feat0, f0.data(), n_chunks * sizeof(uint64_t), cudaMemcpyHostToDevice, stream));
-    CK(cudaMemcpyAsync(c->d_chunk_len, len.data(), n_chunks * sizeof(uint32_t), cudaMemcpyHostToDevice, stream));
-  }
-  for (int i = 0; i < 4; ++i) c->ev_used[i] = 0;
-  {  // centre (reading: mean over the whole set) and per-row constants
-    StageTimer tm(c, CASHASH_STAGE_CENTRE, stream);
-    if (mean_host) {
-      CK(cudaMemcpyAsync(c->d_mu, mean_host, DIM * sizeof(double), cudaMemcpyHostToDevice, stream));
-    } else {
-      CK(launch_colsum(s->desc, n, c->d_colsum, stream));
-      c->n_launches += n ? 1 : 0;
-    }
-    // bound factor on ||R_b|| ||x||: FP32 FMA chains (2^-16), BF16 tensor cores (2^-15)
-    const float alpha_scale = c->p.precision == CASHASH_BF16 ? 0x1p-15f : 0x1p-16f;
-    CK(launch_row_consts(c->d_colsum, n, mean_host ? 1 : 0, c->d_mu, c->d_R, c->d_nrmR, c->rows, alpha_scale,
-                         c->d_rc, stream));
-    c->n_launches += 1;
-    CK(cudaMemsetAsync(c->d_cnt, 0, 2 * sizeof(unsigned long long), stream));
-  }
-  if (n) {
-    {
-      StageTimer tm(c, CASHASH_STAGE_PROJECT, stream);
-      if (c->p.precision == CASHASH_BF16)
-        CK(launch_project_bf16(s->desc, n, c->d_Rbf, c->np_tc, c->d_rc, c->kp, s->codes, s->buckets, s->sqnorm,
-                               c->d_flagmask, c->d_flaglist, c->d_cnt + 0, c->d_status, stream));
-      else
-        CK(launch_project_fp32(s->desc, n, c->d_R32T, c->d_rc, c->kp, s->codes, s->buckets, s->sqnorm, c->d_flagmask,
-                               c->d_flaglist, c->d_cnt + 0, stream));
-    }
-    {
-      StageTimer tm(c, CASHASH_STAGE_REEVAL, stream);
-      CK(launch_fix_fp64(s->desc, c->d_mu, c->d_R, c->kp, c->d_flagmask, c->d_flaglist, c->d_cnt + 0, n, s->codes,
-                         s->buckets, c->d_cnt + 1, stream));
-    }
-    {
-      StageTimer tm(c, CASHASH_STAGE_TABLES, stream);
-      CK(launch_build_tables(s->buckets, c->d_chunk_feat0, c->d_chunk_len, (uint32_t)n_chunks, c->p.n_tables,
-                             s->tables, stream));
-      const uint32_t n_max = inn.empty() ? 0u : *std::max_element(inn.begin(), inn.end());
-      CK(launch_build_join(s->buckets, s->codes, c->d_img_f0, c->d_img_n, c->d_img_join, s->n_images, c->p.n_tables,
-                           n_max, s->tables, stream));
-    }
-    c->n_launches += 4;
-  }
-  c->last_stream = stream;
-  c->last_n_features = n;
-  c->built = 1;
-  return CASHASH_OK;
+  return build_codes_impl(c, s, mean_host, reinterpret_cast<cudaStream_t>(stream_), false);
 }
+
 
 int cashash_projection_bounds(cashash_ctx* c, const cashash_set* s, uint64_t first, uint64_t count,
                               float* approx, float* bound, cashash_stream_t stream_) {
@@ -1233,51 +1261,75 @@ int cashash_run_host(cashash_ctx* c, const uint8_t* desc_host, const uint64_t* i
     if ((st = grow(h.kpts, h.cap_kpts, std::max<uint64_t>(N, 1) * 2)) != CASHASH_OK) return st;
     if ((st = grow(h.F, h.cap_F, std::max<uint64_t>(P, 1) * 9)) != CASHASH_OK) return st;
   }
-  // descriptors: host -> device on the copy stream; pinned sources are copied
-  // directly, pageable ones through two pinned bounce buffers
+  // Inputs host -> device on the copy stream: key-points and F first, then the
+  // descriptors in blocks of at most 256 MiB (pinned sources directly,
+  // pageable ones through two pinned bounce buffers of at most stage_bytes).
+  // The compute stream takes each block's column sums as soon as it lands;
+  // the projections wait for the whole set, whose mean is their centre.
+  for (int i = 0; i < CASHASH_STAGE_H2D; ++i) c->ev_used[i] = 0;
+  c->ev_used[CASHASH_STAGE_H2D] = c->ev_used[CASHASH_STAGE_D2H] = 0;
   const uint64_t bytes = N * DIM;
-  if (bytes) {
-    cudaPointerAttributes attr{};
-    bool pinned = false;
-    if (cudaPointerGetAttributes(&attr, desc_host) == cudaSuccess)
-      pinned = attr.type == cudaMemoryTypeHost;
-    else
-      cudaGetLastError();
-    if (pinned) {
-      for (uint64_t o = 0; o < bytes; o += stage_bytes)
-        CK(cudaMemcpyAsync(h.desc + o, desc_host + o, std::min(stage_bytes, bytes - o), cudaMemcpyHostToDevice, h.copy));
-    } else {
-      const uint64_t chunk = std::min(stage_bytes, bytes);
-      if (h.pin_cap < chunk) {
-        for (int i = 0; i < 2; ++i) {
-          if (h.pin[i]) cudaFreeHost(h.pin[i]);
-          h.pin[i] = nullptr;
+  const uint64_t blk = std::min<uint64_t>(stage_bytes, 256ull << 20) & ~(uint64_t)(DIM * 16 - 1);
+  CK(cudaMemsetAsync(c->d_colsum, 0, DIM * sizeof(unsigned long long), h.comp));
+  CK(cudaEventRecord(h.staged, h.comp));      // the colsum buffer is cleared before any block adds to it
+  CK(cudaStreamWaitEvent(h.copy, h.staged, 0));
+  {
+    StageTimer tm(c, CASHASH_STAGE_H2D, h.copy);
+    if (epi) {
+      if (N) CK(cudaMemcpyAsync(h.kpts, kpts_host, N * 2 * sizeof(float), cudaMemcpyHostToDevice, h.copy));
+      if (P) CK(cudaMemcpyAsync(h.F, F_host, (uint64_t)P * 9 * sizeof(double), cudaMemcpyHostToDevice, h.copy));
+    }
+    // one block landed: its column sums on the compute stream
+    auto landed = [&](uint64_t o, uint64_t l) -> int {
+      CK(cudaEventRecord(h.staged, h.copy));
+      CK(cudaStreamWaitEvent(h.comp, h.staged, 0));
+      CK(launch_colsum(h.desc + o, l / DIM, c->d_colsum, h.comp, true));
+      c->n_launches += 1;
+      return CASHASH_OK;
+    };
+    if (bytes) {
+      cudaPointerAttributes attr{};
+      bool pinned = false;
+      if (cudaPointerGetAttributes(&attr, desc_host) == cudaSuccess)
+        pinned = attr.type == cudaMemoryTypeHost;
+      else
+        cudaGetLastError();
+      if (pinned) {
+        for (uint64_t o = 0; o < bytes; o += blk) {
+          const uint64_t l = std::min(blk, bytes - o);
+          CK(cudaMemcpyAsync(h.desc + o, desc_host + o, l, cudaMemcpyHostToDevice, h.copy));
+          if ((st = landed(o, l)) != CASHASH_OK) return st;
         }
-        h.pin_cap = 0;
-        for (int i = 0; i < 2; ++i)
-          if (cudaHostAlloc(reinterpret_cast<void**>(&h.pin[i]), chunk, cudaHostAllocDefault) != cudaSuccess) {
-            cudaGetLastError();
-            return CASHASH_ENOMEM;
+      } else {
+        const uint64_t chunk = std::min(blk, bytes);
+        if (h.pin_cap < chunk) {
+          for (int i = 0; i < 2; ++i) {
+            if (h.pin[i]) cudaFreeHost(h.pin[i]);
+            h.pin[i] = nullptr;
           }
-        h.pin_cap = chunk;
-      }
-      uint64_t k = 0;
-      for (uint64_t o = 0; o < bytes; o += chunk, ++k) {
-        const int b = (int)(k & 1);
-        if (k >= 2) CK(cudaEventSynchronize(h.ev[b]));
-        const uint64_t l = std::min(chunk, bytes - o);
-        std::memcpy(h.pin[b], desc_host + o, l);
-        CK(cudaMemcpyAsync(h.desc + o, h.pin[b], l, cudaMemcpyHostToDevice, h.copy));
-        CK(cudaEventRecord(h.ev[b], h.copy));
+          h.pin_cap = 0;
+          for (int i = 0; i < 2; ++i)
+            if (cudaHostAlloc(reinterpret_cast<void**>(&h.pin[i]), chunk, cudaHostAllocDefault) != cudaSuccess) {
+              cudaGetLastError();
+              return CASHASH_ENOMEM;
+            }
+          h.pin_cap = chunk;
+        }
+        uint64_t k = 0;
+        for (uint64_t o = 0; o < bytes; o += chunk, ++k) {
+          const int b = (int)(k & 1);
+          if (k >= 2) CK(cudaEventSynchronize(h.ev[b]));
+          const uint64_t l = std::min(chunk, bytes - o);
+          std::memcpy(h.pin[b], desc_host + o, l);
+          CK(cudaMemcpyAsync(h.desc + o, h.pin[b], l, cudaMemcpyHostToDevice, h.copy));
+          CK(cudaEventRecord(h.ev[b], h.copy));
+          if ((st = landed(o, l)) != CASHASH_OK) return st;
+        }
       }
     }
   }
-  CK(cudaEventRecord(h.staged, h.copy));
+  CK(cudaEventRecord(h.staged, h.copy));  // key-points, F and every block
   CK(cudaStreamWaitEvent(h.comp, h.staged, 0));
-  if (epi) {
-    if (N) CK(cudaMemcpyAsync(h.kpts, kpts_host, N * 2 * sizeof(float), cudaMemcpyHostToDevice, h.comp));
-    if (P) CK(cudaMemcpyAsync(h.F, F_host, (uint64_t)P * 9 * sizeof(double), cudaMemcpyHostToDevice, h.comp));
-  }
   cashash_set S{};
   S.n_images = n_images;
   S.n_features = N;
@@ -1288,7 +1340,7 @@ int cashash_run_host(cashash_ctx* c, const uint8_t* desc_host, const uint64_t* i
   S.sqnorm = h.sqnorm;
   S.tables = h.tables;
   S.kpts = epi ? h.kpts : nullptr;
-  st = cashash_build_codes(c, &S, nullptr, reinterpret_cast<cashash_stream_t>(h.comp));
+  st = build_codes_impl(c, &S, nullptr, h.comp, true);
   if (st != CASHASH_OK) return st;
   // plan: reused while the pair list and image sizes are unchanged
   const bool same = h.plan && h.plan_pairs.size() == 2 * (size_t)P && h.plan_off.size() == (size_t)n_images + 1 &&
@@ -1314,11 +1366,17 @@ int cashash_run_host(cashash_ctx* c, const uint8_t* desc_host, const uint64_t* i
   st = cashash_match_plan(c, h.plan, epi ? h.F : nullptr, h.moff, h.matches, mcap,
                           reinterpret_cast<cashash_stream_t>(h.comp));
   if (st != CASHASH_OK) return st;
-  CK(cudaMemcpyAsync(match_off_host, h.moff, ((uint64_t)P + 1) * sizeof(uint64_t), cudaMemcpyDeviceToHost, h.comp));
-  CK(cudaStreamSynchronize(h.comp));
+  {
+    StageTimer tm(c, CASHASH_STAGE_D2H, h.comp);
+    CK(cudaMemcpyAsync(match_off_host, h.moff, ((uint64_t)P + 1) * sizeof(uint64_t), cudaMemcpyDeviceToHost,
+                       h.comp));
+    CK(cudaStreamSynchronize(h.comp));
+    const uint64_t total = match_off_host[P];
+    const uint64_t ncopy = std::min(total, mcap);
+    if (ncopy)
+      CK(cudaMemcpyAsync(matches_host, h.matches, ncopy * 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, h.comp));
+  }
   const uint64_t total = match_off_host[P];
-  const uint64_t ncopy = std::min(total, mcap);
-  if (ncopy) CK(cudaMemcpyAsync(matches_host, h.matches, ncopy * 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, h.comp));
   st = cashash_sync_status(c, reinterpret_cast<cashash_stream_t>(h.comp));
   if (st == CASHASH_OK && total > cap) st = CASHASH_EOVERFLOW;
   return st;

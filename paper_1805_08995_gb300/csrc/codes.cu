@@ -44,10 +44,10 @@ __global__ void __launch_bounds__(256) k_colsum(const uint8_t* __restrict__ desc
   }
 }
 
-cudaError_t launch_colsum(const uint8_t* desc, uint64_t n, unsigned long long* sums, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(sums, 0, DIM * sizeof(unsigned long long), s);
+cudaError_t launch_colsum(const uint8_t* desc, uint64_t n, unsigned long long* sums, cudaStream_t s, bool add) {
+  cudaError_t e = add ? cudaSuccess : cudaMemsetAsync(sums, 0, DIM * sizeof(unsigned long long), s);
   if (e != cudaSuccess || n == 0) return e;
-  uint64_t want = (n + 32 * 64 - 1) / (32 * 64);
+  uint64_t want = (n + 32 * 8 - 1) / (32 * 8);  // about 8 rows of 16-byte loads per thread
   int grid = (int)(want < 1216 ? want : 1216);
   k_colsum<<<grid, 256, 0, s>>>(desc, n, sums);
   return cudaGetLastError();
@@ -62,46 +62,53 @@ cudaError_t launch_colsum(const uint8_t* desc, uint64_t n, unsigned long long* s
 //     alpha_b = alpha_scale * ||R_b||_2,
 //     beta_b  = 2^-23 |c_b| + 2^-40 ||R_b||_2 (||mu||_2 + 1).
 // ---------------------------------------------------------------------------
-__global__ void k_row_consts(const unsigned long long* __restrict__ sums, uint64_t n, int have_mean,
-                             double* __restrict__ mu, const double* __restrict__ R,
-                             const double* __restrict__ nrmR, uint32_t rows, float alpha_scale,
-                             RowConst* __restrict__ rc) {
+__global__ void __launch_bounds__(256) k_row_consts(const unsigned long long* __restrict__ sums, uint64_t n,
+                                                    int have_mean, double* __restrict__ mu,
+                                                    const double* __restrict__ R, const double* __restrict__ nrmR,
+                                                    uint32_t rows, float alpha_scale, RowConst* __restrict__ rc) {
   __shared__ double mu_s[DIM];
   __shared__ double nmu_s;
-  const int t = threadIdx.x;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   if (t < DIM) {
     double m;
     if (have_mean) {
       m = mu[t];
     } else {
       m = (n == 0) ? 0.0 : __ddiv_rn((double)sums[t], (double)n);
-      mu[t] = m;
     }
     mu_s[t] = m;
   }
   __syncthreads();
-  if (t == 0) {
+  if (!have_mean && blockIdx.x == 0 && t < DIM) mu[t] = mu_s[t];  // (every CTA reads the sums, one writes mu)
+  // ||mu|| and c_b = sum_j R_bj mu_j by warp reductions: only the approximation
+  // uses them and the bound covers their rounding, so the order is free
+  if (warp == 0) {
     double s = 0.0;
-    for (int j = 0; j < DIM; ++j) s += mu_s[j] * mu_s[j];
-    nmu_s = sqrt(s) * (1.0 + 0x1p-40);
+    for (int j = lane; j < DIM; j += 32) s += mu_s[j] * mu_s[j];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+    if (lane == 0) nmu_s = sqrt(s) * (1.0 + 0x1p-40);
   }
   __syncthreads();
-  if ((uint32_t)t < rows) {
+  for (uint32_t b = blockIdx.x * (blockDim.x / 32) + warp; b < rows; b += gridDim.x * (blockDim.x / 32)) {
     double c = 0.0;
-    for (int j = 0; j < DIM; ++j) c += R[(size_t)t * DIM + j] * mu_s[j];
-    RowConst r;
-    r.c32 = (float)c;
-    r.alpha = (float)(alpha_scale * nrmR[t] * (1.0 + 0x1p-20));
-    r.beta = (float)((0x1p-23 * fabs(c) + 0x1p-40 * nrmR[t] * (nmu_s + 1.0)) * (1.0 + 0x1p-20) + 0x1p-60);
-    r.pad = 0.f;
-    rc[t] = r;
+    for (int j = lane; j < DIM; j += 32) c += R[(size_t)b * DIM + j] * mu_s[j];
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
+    if (lane == 0) {
+      RowConst r;
+      r.c32 = (float)c;
+      r.alpha = (float)(alpha_scale * nrmR[b] * (1.0 + 0x1p-20));
+      r.beta = (float)((0x1p-23 * fabs(c) + 0x1p-40 * nrmR[b] * (nmu_s + 1.0)) * (1.0 + 0x1p-20) + 0x1p-60);
+      r.pad = 0.f;
+      rc[b] = r;
+    }
   }
 }
 
 cudaError_t launch_row_consts(const unsigned long long* sums, uint64_t n, int have_mean, double* mu,
                               const double* R, const double* nrmR, uint32_t rows, float alpha_scale,
                               RowConst* rc, cudaStream_t s) {
-  k_row_consts<<<1, 256, 0, s>>>(sums, n, have_mean, mu, R, nrmR, rows, alpha_scale, rc);
+  // one warp per row, the rows spread over CTAs (each CTA derives the centre itself)
+  k_row_consts<<<(rows + 7) / 8, 256, 0, s>>>(sums, n, have_mean, mu, R, nrmR, rows, alpha_scale, rc);
   return cudaGetLastError();
 }
 
@@ -267,7 +274,9 @@ __global__ void __launch_bounds__(256) k_fix_fp64(const uint8_t* __restrict__ de
   const int lane = threadIdx.x & 31;
   uint64_t nf = *nflag_feat;
   if (nf > max_feat) nf = max_feat;
-  const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  // warps numbered across CTAs first, so that a short flagged list spreads
+  // over the SMs (the FP64 pipe of one SM is narrow)
+  const uint64_t warp = (uint64_t)(threadIdx.x >> 5) * gridDim.x + blockIdx.x;
   const uint64_t nwarp = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   unsigned long long done = 0;
   for (uint64_t base = warp * 32; base < nf; base += nwarp * 32) {

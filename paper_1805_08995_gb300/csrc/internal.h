@@ -198,7 +198,9 @@ __device__ __forceinline__ bool epi_keep_fast(const EpiQ& e, float2 pc) {
 int params_ok(const cashash_params* p);
 
 // ---- launchers (return cudaError_t of the launch) ----
-cudaError_t launch_colsum(const uint8_t* desc, uint64_t n, unsigned long long* sums, cudaStream_t s);
+// Column sums of n descriptors into sums[128] (zeroed first unless add).
+cudaError_t launch_colsum(const uint8_t* desc, uint64_t n, unsigned long long* sums, cudaStream_t s,
+                          bool add = false);
 cudaError_t launch_row_consts(const unsigned long long* sums, uint64_t n, int have_mean, double* mu,
                               const double* R, const double* nrmR, uint32_t rows, float alpha_scale,
                               RowConst* rc, cudaStream_t s);

@@ -609,17 +609,22 @@ def test_host_end_to_end_matches_device_path(ch, orc):
     mu, codes, buckets = oracle_codes(orc, s.desc, s.R, po)
     eoff, emt = orc.match_pairs(s.desc, s.img_off, codes, buckets, pairs, po)
     pinned = torch.from_numpy(s.desc).pin_memory()
+    ch.cashash_set_profiling(ctx, True)
+    # 1 MiB stages: the 9,100 descriptors land in two blocks, each block's column sums taken as it lands
     for desc, stage in ((s.desc, 0), (pinned, 0), (s.desc, 1 << 20), (pinned, 1 << 20)):
         st, off, mt = ch.cashash_run_host(ctx, desc, s.img_off, pairs, cap, stage_bytes=stage)
         assert st == ch.CASHASH_OK
         assert np.array_equal(off, eoff) and np.array_equal(mt, emt)
+        ms = ch.cashash_get_stats(ctx)["ms_stage"]
+        assert ms["h2d"] > 0 and ms["d2h"] > 0 and ms["centre"] > 0 and ms["match"] > 0
+    assert np.array_equal(ch.cashash_get_mean(ctx), mu)
     st, off, mt = ch.cashash_run_host(ctx, s.desc, s.img_off, pairs, 10)
     assert st == ch.CASHASH_EOVERFLOW and np.array_equal(off, eoff) and np.array_equal(mt, emt[:10])
     ctx.close()
     # a batched context with every host-path kernel configuration
     ctx = ch.cashash_create(ch.cashash_default_params(schedule=ch.CASHASH_SCHED_PERSISTENT), s.R)
     for kernel, tile in ((ch.CASHASH_KERNEL_QUERY, 512), (ch.CASHASH_KERNEL_JOIN, 2), (ch.CASHASH_KERNEL_QUERY, 256),
-                         (0, 0)):
+                         (ch.CASHASH_KERNEL_JOIN_TC, 0), (0, 0)):
         ch.cashash_set_host_tuning(ctx, kernel, tile)
         st, off, mt = ch.cashash_run_host(ctx, pinned, s.img_off, pairs, cap)
         assert st == ch.CASHASH_OK
@@ -667,9 +672,12 @@ def test_stage_profiling_and_graph_replay(ch):
             ch.cashash_build_codes(ctx, ds)
             ch.cashash_match_plan(ctx, plan, moff, mt, cap)
             st = ch.cashash_get_stats(ctx)
-            # the per-pair schedule has no calibration or fallback stage
-            used = {k: v for k, v in st["ms_stage"].items() if sched or k not in ("calibrate", "fallback")}
+            # the per-pair schedule has no calibration or fallback stage; the copy stages
+            # belong to cashash_run_host
+            used = {k: v for k, v in st["ms_stage"].items()
+                    if (sched or k not in ("calibrate", "fallback")) and k not in ("h2d", "d2h")}
             assert all(v > 0 for v in used.values()), st["ms_stage"]
+            assert st["ms_stage"]["h2d"] == -1.0 and st["ms_stage"]["d2h"] == -1.0
             if not sched:
                 assert st["ms_stage"]["calibrate"] == -1.0 and st["ms_stage"]["fallback"] == -1.0
         assert st["n_launches"] > n0
