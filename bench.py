@@ -300,8 +300,11 @@ def roofline_of(ch, p, s, ds, stage_ms, tuning, n_sm):
     tensor_view give the integer and tensor ceilings of the Hamming step."""
     pk = peaks()
     T, m = p.n_tables, p.bits_per_table
-    entries = lookup_entries(ds.buckets_np(T), s.img_off, s.pairs, T, m)
-    queries = float(s.sizes()[s.pairs[:, 0]].sum())
+    pairs = s.pairs
+    if p.flags & 1:  # the mutual check matches every pair in both directions
+        pairs = np.concatenate([s.pairs, s.pairs[:, ::-1]])
+    entries = lookup_entries(ds.buckets_np(T), s.img_off, pairs, T, m)
+    queries = float(s.sizes()[pairs[:, 0]].sum())
     t_match = statistics.mean(stage_ms["match"]) / 1e3
     kernel = {ch.CASHASH_KERNEL_JOIN: "k_join", ch.CASHASH_KERNEL_JOIN_TC: "k_join_tc"}.get(tuning.get("kernel"),
                                                                                            "k_match")
@@ -309,6 +312,8 @@ def roofline_of(ch, p, s, ds, stage_ms, tuning, n_sm):
     achieved = touched / t_match / 1e9
     traffic = None
     prof = PROFILED_TRAFFIC.get(kernel)
+    if p.epi_px >= 0:  # the capture was taken on the join without the band
+        prof = None
     if prof and prof["sha256"] == source_sha256(prof["sources"]):
         traffic = prof["bytes_per_entry"] * entries
     sm_mhz = pk.get("sm_max_mhz", 2070.0)
