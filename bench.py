@@ -40,8 +40,8 @@ L2_FLUSH_BYTES = 256 << 20
 # summarised in profiles/ (valid only for the kernel source it was taken on).
 PROFILED_TRAFFIC = {
     "k_join": {"sources": ["paper_1805_08995_gb300/csrc/join.cu", "paper_1805_08995_gb300/csrc/join_common.cuh"],
-               "sha256": "a1dab5f155c92f817855de3c9e61a8b14c143b1e81d27147a209148ec7af7658",
-               "bytes_per_entry": (2.386088e9 + 1.099653e9) / 861951265},
+               "sha256": "806efd51cc28bb61329f1abc825a2531b56230bdadc80c275c10ef736795ffd3",
+               "bytes_per_entry": (2.351300e9 + 1.099531e9) / 861951265},
 }
 
 
@@ -557,6 +557,9 @@ def run_ours(args):
                 "config": {"workload": wdesc, "images": int(s.n_images), "features": int(s.desc.shape[0]),
                            "pairs": P_job if split_pairs else P, "precision": args.precision,
                            "schedule": args.schedule,
+                           "thresholds": ("fresh: every timed step calibrates the per-pair Hamming guesses anew"
+                                          if args.thresholds == "fresh" else
+                                          "learned: guesses carried over from earlier steps"),
                            "split": "pairs (LPT by N_A*N_B, no collective)" if split_pairs else
                                     ("independent image set per rank" if world > 1 else None),
                            "chunked": ("%d pairs per chunk, lists flushed to pinned host memory per chunk"

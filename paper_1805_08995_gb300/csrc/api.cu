@@ -947,10 +947,11 @@ int cashash_match_plan(cashash_ctx* c, cashash_plan* pl, const double* F_dev, ui
       pl->g_prof = c->profiling;
     }
     CK(cudaGraphLaunch(pl->gexec, stream));
-    if (c->profiling)  // the graph holds the stage events as external event-record nodes
+    if (c->profiling) {  // the graph holds the stage events as external event-record nodes
       c->ev_used[CASHASH_STAGE_MATCH] = c->ev_used[CASHASH_STAGE_COMPACT] = 1;
       c->ev_used[CASHASH_STAGE_FALLBACK] = 1;
       if (c->p.epi_px < 0.0) c->ev_used[CASHASH_STAGE_CALIBRATE] = 1;
+    }
   } else {
     const int st = enqueue_match(c, pl, F_dev, match_off, matches, cap, stream, false);
     if (st != CASHASH_OK) return st;
