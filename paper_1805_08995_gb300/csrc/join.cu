@@ -260,8 +260,10 @@ __global__ void __launch_bounds__(JT, 2) k_join(MatchArgs a) {
             ka &= ba;
             kb &= bb;
           }
-          if (ka | kb) {
-            // one counter update per row, then the row's survivors at consecutive slots
+          {
+            // one counter update per row, then the row's survivors at consecutive slots; the
+            // stores are predicated rather than branched (survivors are sparse and scattered
+            // over the lanes, so nearly every warp has some in every slot position)
             uint32_t pa = ka ? atomicAdd(cnt_s + qa_c, (uint32_t)__popc(ka)) : 0u;
             uint32_t pb = kb ? atomicAdd(cnt_s + qb_c, (uint32_t)__popc(kb)) : 0u;
             uint32_t* sa = seg + (size_t)qa_c * JSEG;
@@ -271,14 +273,11 @@ __global__ void __launch_bounds__(JT, 2) k_join(MatchArgs a) {
 #pragma unroll
               for (int c = 0; c < 2; ++c) {
                 const int bit = 2 * n + c;
-                if ((ka >> bit) & 1u) {
-                  if (pa < JSEG) sa[pa] = c ? key_hi(d[n][0], jc[n][1]) : key_lo(d[n][0], jc[n][0]);
-                  ++pa;
-                }
-                if ((kb >> bit) & 1u) {
-                  if (pb < JSEG) sb[pb] = c ? key_hi(d[n][1], jc[n][1]) : key_lo(d[n][1], jc[n][0]);
-                  ++pb;
-                }
+                const uint32_t oa = (ka >> bit) & 1u, ob = (kb >> bit) & 1u;
+                st_global_if(sa + pa, c ? key_hi(d[n][0], jc[n][1]) : key_lo(d[n][0], jc[n][0]), oa && pa < JSEG);
+                st_global_if(sb + pb, c ? key_hi(d[n][1], jc[n][1]) : key_lo(d[n][1], jc[n][0]), ob && pb < JSEG);
+                pa += oa;
+                pb += ob;
               }
           }
         }

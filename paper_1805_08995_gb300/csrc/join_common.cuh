@@ -12,6 +12,14 @@ namespace chx {
 
 constexpr int JT = 256;  // threads of a join CTA (one query per thread in the finalisation)
 
+// Predicated 32-bit global store (one instruction, no branch): *p = v if c.
+__device__ __forceinline__ void st_global_if(uint32_t* p, uint32_t v, bool c) {
+  asm volatile(
+      "{\n .reg .pred q;\n setp.ne.b32 q, %2, 0;\n @q st.global.u32 [%0], %1;\n}" ::"l"(__cvta_generic_to_global(p)),
+      "r"(v), "r"((uint32_t)c)
+      : "memory");
+}
+
 template <int KC>
 __device__ __forceinline__ void jt_insert(uint32_t (&top)[KC], uint32_t k) {
 #pragma unroll
@@ -112,18 +120,26 @@ __device__ __forceinline__ void join_finalise(const MatchArgs& a, const PairInfo
       pending = n > JSEG;  // survivors were dropped
       const uint4* ql = reinterpret_cast<const uint4*>(seg + (size_t)q * JSEG);
       const uint32_t m = min(n, JSEG);
-      for (uint32_t e0 = 0; e0 < m; e0 += 16) {
-        uint4 x[4];
+      // the next 16 survivors are loaded while the current 16 are inserted; a key at or above
+      // the list's last entry when its group starts cannot enter it
+      const uint4 INF4 = make_uint4(KEY_INF, KEY_INF, KEY_INF, KEY_INF);
+      uint4 x[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
-          x[i] = e0 + 4 * i < m ? ql[e0 / 4 + i] : make_uint4(KEY_INF, KEY_INF, KEY_INF, KEY_INF);
+      for (int i = 0; i < 4; ++i) x[i] = 4 * i < m ? ql[i] : INF4;
+      for (uint32_t e0 = 0; e0 < m; e0 += 16) {
+        uint4 y[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) y[i] = e0 + 16 + 4 * i < m ? ql[(e0 + 16) / 4 + i] : INF4;
+        const uint32_t lim = top[KC - 1];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           const uint32_t kk[4] = {x[i].x, x[i].y, x[i].z, x[i].w};
 #pragma unroll
           for (int u = 0; u < 4; ++u)
-            if (e0 + 4 * i + u < m && kk[u] < top[KC - 1]) jt_insert<KC>(top, kk[u]);
+            if (e0 + 4 * i + u < m && kk[u] < lim) jt_insert<KC>(top, kk[u]);
         }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) x[i] = y[i];
       }
       const uint32_t kth = jt_kth<KC>(top, K);
       if (!pending && kth == KEY_INF && cut) {
