@@ -108,6 +108,15 @@ __device__ __forceinline__ void write_feature(uint64_t f, const uint32_t* bits, 
   }
 }
 
+// Predicated 32-bit global store (one instruction, no branch): *p = v if c.
+// Survivor appends use it: their conditions are data-dependent per lane.
+__device__ __forceinline__ void st_global_if(uint32_t* p, uint32_t v, bool c) {
+  asm volatile(
+      "{\n .reg .pred q;\n setp.ne.b32 q, %2, 0;\n @q st.global.u32 [%0], %1;\n}" ::"l"(__cvta_generic_to_global(p)),
+      "r"(v), "r"((uint32_t)c)
+      : "memory");
+}
+
 // Step 4 ratio test over nv ranked candidates with the two smallest squared
 // distances d1 <= d2: den^2 d1 < num^2 d2 in 64-bit integers (strict, on
 // distances); one ranked candidate matches only with CASHASH_FLAG_ACCEPT_SINGLE.

@@ -74,9 +74,23 @@ __device__ __forceinline__ uint32_t le_mask(uint32_t d, __half2 t) {
 
 constexpr uint32_t ACC0 = 0x64806480u;  // f16 (1152, 1152): results are 1024 + 2 H
 
-// Key H << 24 | j from the low / high f16 result (bits 0x6400 + 2 H).
-__device__ __forceinline__ uint32_t key_lo(uint32_t d, uint32_t j) { return ((d & 0x3FEu) << 23) | j; }
-__device__ __forceinline__ uint32_t key_hi(uint32_t d, uint32_t j) { return ((d & 0x03FE0000u) << 7) | j; }
+// Key H << 24 | j from the low / high f16 result (bits 0x6400 + 2 H), as an integer multiply-add:
+// d * 2^23 keeps (mod 2^32) only bits 1-8 of the low f16, i.e. 2 H << 23 = H << 24, and j < 2^24
+// adds without carry.
+__device__ __forceinline__ uint32_t key_lo(uint32_t d, uint32_t j) { return d * 0x800000u + j; }
+__device__ __forceinline__ uint32_t key_hi(uint32_t d, uint32_t j) { return (d >> 16) * 0x800000u + j; }
+
+// *(base + pos) = v and ++pos when (bits & mask) != 0: one predicate for a predicated store and a
+// predicated add (survivors are sparse and scattered over the lanes, so nearly every warp has some
+// in every slot position and a branch per slot would diverge).  The stores are read only after the
+// CTA barrier that ends the scan.
+__device__ __forceinline__ void append_if(uint32_t* base, uint32_t& pos, uint32_t bits, uint32_t mask, uint32_t v) {
+  asm volatile(
+      "{\n .reg .pred q;\n .reg .b32 t;\n and.b32 t, %2, %3;\n setp.ne.b32 q, t, 0;\n"
+      " @q st.global.u32 [%1], %4;\n @q add.u32 %0, %0, 1;\n}"
+      : "+r"(pos)
+      : "l"(__cvta_generic_to_global(base + pos)), "r"(bits), "r"(mask), "r"(v));
+}
 
 // Bucket offsets of join task `task` (table task / nbk, bucket task % nbk) in
 // both images; zeros past the last task.
@@ -261,11 +275,11 @@ __global__ void __launch_bounds__(JT, 2) k_join(MatchArgs a) {
             kb &= bb;
           }
           {
-            // one counter update per row, then the row's survivors at consecutive slots; the
-            // stores are predicated rather than branched (survivors are sparse and scattered
-            // over the lanes, so nearly every warp has some in every slot position)
+            // one counter update per row, then the row's survivors at consecutive slots
             uint32_t pa = ka ? atomicAdd(cnt_s + qa_c, (uint32_t)__popc(ka)) : 0u;
             uint32_t pb = kb ? atomicAdd(cnt_s + qb_c, (uint32_t)__popc(kb)) : 0u;
+            // a row that would overflow its list stores nothing (its query is left PENDING)
+            const uint32_t sta = pa + __popc(ka) <= JSEG ? ka : 0u, stb = pb + __popc(kb) <= JSEG ? kb : 0u;
             uint32_t* sa = seg + (size_t)qa_c * JSEG;
             uint32_t* sb = seg + (size_t)qb_c * JSEG;
 #pragma unroll
@@ -273,11 +287,8 @@ __global__ void __launch_bounds__(JT, 2) k_join(MatchArgs a) {
 #pragma unroll
               for (int c = 0; c < 2; ++c) {
                 const int bit = 2 * n + c;
-                const uint32_t oa = (ka >> bit) & 1u, ob = (kb >> bit) & 1u;
-                st_global_if(sa + pa, c ? key_hi(d[n][0], jc[n][1]) : key_lo(d[n][0], jc[n][0]), oa && pa < JSEG);
-                st_global_if(sb + pb, c ? key_hi(d[n][1], jc[n][1]) : key_lo(d[n][1], jc[n][0]), ob && pb < JSEG);
-                pa += oa;
-                pb += ob;
+                append_if(sa, pa, sta, 1u << bit, c ? key_hi(d[n][0], jc[n][1]) : key_lo(d[n][0], jc[n][0]));
+                append_if(sb, pb, stb, 1u << bit, c ? key_hi(d[n][1], jc[n][1]) : key_lo(d[n][1], jc[n][0]));
               }
           }
         }

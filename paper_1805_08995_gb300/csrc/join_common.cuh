@@ -12,14 +12,6 @@ namespace chx {
 
 constexpr int JT = 256;  // threads of a join CTA (one query per thread in the finalisation)
 
-// Predicated 32-bit global store (one instruction, no branch): *p = v if c.
-__device__ __forceinline__ void st_global_if(uint32_t* p, uint32_t v, bool c) {
-  asm volatile(
-      "{\n .reg .pred q;\n setp.ne.b32 q, %2, 0;\n @q st.global.u32 [%0], %1;\n}" ::"l"(__cvta_generic_to_global(p)),
-      "r"(v), "r"((uint32_t)c)
-      : "memory");
-}
-
 template <int KC>
 __device__ __forceinline__ void jt_insert(uint32_t (&top)[KC], uint32_t k) {
 #pragma unroll

@@ -161,17 +161,17 @@ __global__ void __launch_bounds__(TPB, (TPB <= 512 ? 2 : 1)) k_match(MatchArgs a
             if (EPI && key != KEY_INF && !epi_keep_fast(eq, kp_s[jl])) key = KEY_INF;  // Sec. 7.2
             if (SPEC) {
               if (filtered && key == KEY_INF) --nlook;
-              if (key < thr) {
-                qreg[cnt] = key;
-                if (++cnt == QCAP) {  // fold a full queue into the registers, tighten the threshold
-                  for (uint32_t e = 0; e < QCAP; ++e) {
-                    const uint32_t k2 = qreg[e];
-                    if (k2 < top[KC - 1]) topk_insert<KC>(top, k2);
-                  }
-                  nflushed += QCAP;
-                  cnt = 0;
-                  thr = min(thr, top[KC - 1]);
+              const bool keep = key < thr;
+              st_global_if(qreg + cnt, key, keep);  // cnt < QCAP here
+              cnt += keep ? 1u : 0u;
+              if (cnt == QCAP) {  // fold a full queue into the registers, tighten the threshold
+                for (uint32_t e = 0; e < QCAP; ++e) {
+                  const uint32_t k2 = qreg[e];
+                  if (k2 < top[KC - 1]) topk_insert<KC>(top, k2);
                 }
+                nflushed += QCAP;
+                cnt = 0;
+                thr = min(thr, top[KC - 1]);
               }
             } else {
               // Step 3: keep the KC smallest distinct keys
