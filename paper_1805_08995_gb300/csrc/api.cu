@@ -694,7 +694,7 @@ int plan_configure(cashash_plan* pl, cashash_tuning t) {
     st = grow(pl->d_queue, pl->cap_queue, std::max<uint64_t>(q, 1));
   }
   if (st == CASHASH_OK && join && epi)
-    st = grow(pl->d_jline, pl->cap_jline, std::max<uint64_t>((uint64_t)grid * pl->na_max, 1));
+    st = grow(pl->d_jline, pl->cap_jline, std::max<uint64_t>((uint64_t)grid * jline_stride(pl->na_max), 1));
   if (st == CASHASH_OK && join && !pl->d_jhist) {
     uint64_t cap = 0;
     st = grow(pl->d_jhist, cap, std::max<uint64_t>((uint64_t)P * HBINS, 1));

@@ -55,6 +55,9 @@ __host__ __device__ inline uint64_t join_block(uint64_t n) {
   return 1040u + 4u * ((n + 3) / 4 * 4) + 16u * n;
 }
 
+// Bucket join with the band: per CTA, FP32 (a, b, c, w_lo) of each query's line, then w_hi.
+__host__ __device__ inline uint64_t jline_stride(uint64_t na_max) { return na_max + (na_max + 3) / 4; }
+
 // Per-row constants of the projection (Sec. 5.1) derived from R and the centre.
 struct RowConst {
   float c32;     // fl32(c_b), c_b = sum_j R_bj mu_j
@@ -182,6 +185,28 @@ __device__ __forceinline__ int epi_test32(float a, float b, float c, float r, fl
   return 2;
 }
 
+// Thresholds on |n|, n = fl32(a x' + b y' + c) as two FMAs (a, b, c the FP32 roundings of the
+// FP64 line), that decide epi_keep for every candidate of an image whose key-points satisfy
+// |x'| <= mx and |y'| <= my: |n| <= w_lo keeps, |n| >= w_hi drops, anything between (or NaN) is
+// left to the FP64 expression.  With u = 2^-24 and S = |a| mx + |b| my + |c|, the two FMA
+// roundings and the roundings of a, b, c give |n - num| <= 3 u S (1 + u) + 3 * 2^-53 S, num the
+// FP64 numerator; the FP64 square num^2 <= rhs holds whenever |num| <= sqrt(rhs) (1 - 2^-40) and
+// fails whenever |num| >= sqrt(rhs) (1 + 2^-40), since the roundings of the square, of the root
+// and of these bounds are all below 2^-50 relative.  The absolute 1e-30 covers FP32 underflow;
+// lines that are not finite, or so large that n could overflow, leave every candidate to FP64.
+__device__ __forceinline__ void band_thresholds(const EpiQ& e, float mx, float my, float& wlo, float& whi) {
+  wlo = -INFINITY;
+  whi = INFINITY;
+  const double t = sqrt(e.rhs);
+  const double S = fabs((double)e.a) * (double)mx + fabs((double)e.b) * (double)my + fabs((double)e.c);
+  const double en = 3.02 * 0x1p-24 * S + 1e-30;
+  const double lo = t * (1.0 - 0x1p-40) - en, hi = t * (1.0 + 0x1p-40) + en;
+  if (S < 1e30 && isfinite(lo) && isfinite(hi)) {
+    wlo = __double2float_rd(lo);
+    whi = __double2float_ru(hi);
+  }
+}
+
 // The FP64 decisions as real calls: inlined, the compiler may predicate them
 // and run them for every candidate, which makes the FP64 pipe the limit.
 static __device__ __noinline__ bool epi_keep_fp64(const EpiQ& e, float2 pc) {
@@ -257,7 +282,7 @@ struct MatchArgs {
   const uint8_t* join;       // bucket join: table buffer holding the bucket-sorted tables
   uint32_t* jqueue;          // bucket join: [grid][na_max][JSEG] survivor lists
   uint32_t* jhist;           // bucket join: [P][HBINS] k-th Hamming distances seen per pair
-  float4* jline;             // bucket join with the band: [grid][na_max] FP32 a, b, c, r per query
+  float4* jline;             // bucket join with the band: per CTA jline_stride(na_max) float4s of query lines
   uint32_t na_max;           // bucket join: largest query image of the plan
   KParams kp;
 };

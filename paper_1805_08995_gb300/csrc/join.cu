@@ -112,7 +112,7 @@ __device__ __forceinline__ void load_offsets(const uint8_t* join, const PairInfo
 template <int KC, bool TAU, int NTC, bool EPI>
 __global__ void __launch_bounds__(JT, 2) k_join(MatchArgs a) {
   extern __shared__ __align__(16) uint8_t jsm[];
-  __shared__ uint32_t s_item, s_tau, s_task;
+  __shared__ uint32_t s_item, s_tau, s_task, s_kx, s_ky;
   __shared__ uint32_t s_hist[HBINS];
   __shared__ PairInfo s_P;
   const KParams kp = a.kp;
@@ -124,7 +124,9 @@ __global__ void __launch_bounds__(JT, 2) k_join(MatchArgs a) {
   uint32_t* dist_s = key_s + KC * JT;
   uint32_t* seg = a.jqueue + (size_t)blockIdx.x * a.na_max * JSEG;
   const uint32_t h_user = TAU ? kp.tau : 128u;  // Sec. 6: keys with H > tau are no candidates
-  float4* lines = EPI ? a.jline + (size_t)blockIdx.x * a.na_max : nullptr;  // per query: FP32 a, b, c, r
+  // per query: FP32 a, b, c and the thresholds w_lo, w_hi on |a x' + b y' + c| (band_thresholds)
+  float4* lines = EPI ? a.jline + (size_t)blockIdx.x * jline_stride(a.na_max) : nullptr;
+  float* lhi = EPI ? reinterpret_cast<float*>(lines + a.na_max) : nullptr;
   const double dd = kp.epi_px * kp.epi_px;
   const float2* kpts = reinterpret_cast<const float2*>(a.kpts);
 
@@ -139,6 +141,7 @@ __global__ void __launch_bounds__(JT, 2) k_join(MatchArgs a) {
       }
       s_item = p0;
       s_task = 0;
+      s_kx = s_ky = 0u;
     }
     for (uint32_t b = tid; b < HBINS; b += JT) s_hist[b] = 0;
     __syncthreads();
@@ -150,11 +153,32 @@ __global__ void __launch_bounds__(JT, 2) k_join(MatchArgs a) {
     }
     const PairInfo P = s_P;
     const double* Fp = EPI ? a.F + 9 * (size_t)it : nullptr;
+    if constexpr (EPI) {  // max |x'|, |y'| over the candidate image (non-negative floats order as integers)
+      float mx = 0.f, my = 0.f;
+      for (uint32_t j = tid; j < P.nB; j += JT) {
+        const float2 pc = __ldg(kpts + P.b0 + j);
+        mx = fmaxf(mx, fabsf(pc.x));
+        my = fmaxf(my, fabsf(pc.y));
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        mx = fmaxf(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
+        my = fmaxf(my, __shfl_xor_sync(0xFFFFFFFFu, my, o));
+      }
+      if (lane == 0) {
+        atomicMax(&s_kx, __float_as_uint(mx));
+        atomicMax(&s_ky, __float_as_uint(my));
+      }
+      __syncthreads();
+    }
     for (uint32_t q = tid; q < P.nA; q += JT) {
       cnt_s[q] = 0;
       if constexpr (EPI) {
         const EpiQ e = epi_query(Fp, __ldg(kpts + P.a0 + q), dd);
-        lines[q] = make_float4(e.a, e.b, e.c, e.r);
+        float wlo, whi;
+        band_thresholds(e, __uint_as_float(s_kx), __uint_as_float(s_ky), wlo, whi);
+        lines[q] = make_float4(e.a, e.b, e.c, wlo);
+        lhi[q] = whi;
       }
     }
     __syncthreads();
@@ -249,9 +273,10 @@ __global__ void __launch_bounds__(JT, 2) k_join(MatchArgs a) {
           ka &= va ? jok : 0u;
           kb &= vb ? jok : 0u;
           if constexpr (EPI) {  // Sec. 7.2: only candidates inside the band
-            const float4 La = va ? lines[qa_c] : make_float4(0.f, 0.f, 0.f, 0.f);
-            const float4 Lb = vb ? lines[qb_c] : make_float4(0.f, 0.f, 0.f, 0.f);
-            uint32_t ba = 0, bb = 0;
+            const float4 La = va ? lines[qa_c] : make_float4(0.f, 0.f, 0.f, -1.f);
+            const float4 Lb = vb ? lines[qb_c] : make_float4(0.f, 0.f, 0.f, -1.f);
+            const float ha = va ? lhi[qa_c] : 0.f, hb = vb ? lhi[qb_c] : 0.f;
+            uint32_t ba = 0, bb = 0, ua = 0, ub = 0;  // inside / undecided in FP32
 #pragma unroll
             for (int n = 0; n < NTC; ++n)
 #pragma unroll
@@ -259,18 +284,29 @@ __global__ void __launch_bounds__(JT, 2) k_join(MatchArgs a) {
                 const int bit = 2 * n + c;
                 if (((ka | kb) >> bit) & 1u) {
                   const float2 pc = __ldg(kpts + P.b0 + jc[n][c]);
-                  if ((ka >> bit) & 1u) {
-                    int d = epi_test32(La.x, La.y, La.z, La.w, pc);
-                    if (d == 2) d = epi_keep_fp64_F(Fp, __ldg(kpts + P.a0 + qa_c), dd, pc) ? 1 : 0;
-                    ba |= (uint32_t)d << bit;
-                  }
-                  if ((kb >> bit) & 1u) {
-                    int d = epi_test32(Lb.x, Lb.y, Lb.z, Lb.w, pc);
-                    if (d == 2) d = epi_keep_fp64_F(Fp, __ldg(kpts + P.a0 + qb_c), dd, pc) ? 1 : 0;
-                    bb |= (uint32_t)d << bit;
-                  }
+                  const float na = fabsf(fmaf(La.x, pc.x, fmaf(La.y, pc.y, La.z)));
+                  const float nb = fabsf(fmaf(Lb.x, pc.x, fmaf(Lb.y, pc.y, Lb.z)));
+                  if (na <= La.w) ba |= 1u << bit;
+                  if (!(na <= La.w) && !(na >= ha)) ua |= 1u << bit;
+                  if (nb <= Lb.w) bb |= 1u << bit;
+                  if (!(nb <= Lb.w) && !(nb >= hb)) ub |= 1u << bit;
                 }
               }
+            ua &= ka;
+            ub &= kb;
+            if (ua | ub) {  // near the band's edge: the FP64 expression decides
+#pragma unroll
+              for (int n = 0; n < NTC; ++n)
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                  const int bit = 2 * n + c;
+                  if (((ua | ub) >> bit) & 1u) {
+                    const float2 pc = __ldg(kpts + P.b0 + jc[n][c]);
+                    if (((ua >> bit) & 1u) && epi_keep_fp64_F(Fp, __ldg(kpts + P.a0 + qa_c), dd, pc)) ba |= 1u << bit;
+                    if (((ub >> bit) & 1u) && epi_keep_fp64_F(Fp, __ldg(kpts + P.a0 + qb_c), dd, pc)) bb |= 1u << bit;
+                  }
+                }
+            }
             ka &= ba;
             kb &= bb;
           }
