@@ -517,6 +517,53 @@ def test_band_edge_decisions(ch, orc, sched):
     check_case(ch, orc, s, pairs, tuning=tuning, schedule=1 if tuning else sched, epi_px=d)
 
 
+def _band_copy_set(rng, nA, F, kA, kB, name):
+    A = synth.sift_like(rng, nA)
+    return synth.ImageSet(np.concatenate([A, A]), np.array([0, nA, 2 * nA], np.uint64),
+                          np.array([[0, 1]], np.uint32), synth.projection_matrix(616), name,
+                          F=np.ascontiguousarray(F.reshape(1, 9)), kpts=np.concatenate([kA, kB]).astype(np.float32))
+
+
+@pytest.mark.parametrize("case", ["huge_coordinates", "large_F", "infinite_point", "nan_point", "huge_F"])
+def test_band_threshold_fallbacks(ch, orc, case):
+    """Sec. 7.2 with inputs that defeat the join's FP32 thresholds on |a x' + b y' + c|: key-points
+    so far out that the FP32 numerator could overflow (no candidate stays in the band), an F scaled
+    by 1e28 (the same decisions as unscaled, every one in FP64), an infinite or NaN candidate point
+    (the image's extent becomes infinite, or the point's own test is NaN), and an F so large that
+    the FP32 line overflows (the FP64 right-hand side is infinite: every candidate is kept).  Every such decision goes to the FP64 expression, which must agree with the
+    oracle's; each candidate is a copy of its query, so it shares every bucket."""
+    rng = np.random.default_rng(616)
+    nA = 600
+    M = rng.standard_normal((3, 3))
+    U, S, Vt = np.linalg.svd(M)
+    S[2] = 0.0
+    F = (U * S) @ Vt
+    F /= np.linalg.norm(F)
+    kA = (rng.random((nA, 2)) * [1920.0, 1080.0]).astype(np.float32)
+    kB = (rng.random((nA, 2)) * [1920.0, 1080.0]).astype(np.float32)
+    # half of the candidates on the query's line (inside the band), the rest where they fall
+    for j in range(0, nA, 2):
+        x, y = float(kA[j, 0]), float(kA[j, 1])
+        a = (F[0, 0] * x + F[0, 1] * y) + F[0, 2]
+        b = (F[1, 0] * x + F[1, 1] * y) + F[1, 2]
+        c = (F[2, 0] * x + F[2, 1] * y) + F[2, 2]
+        nrm = np.hypot(a, b)
+        kB[j] = (np.array([-c * a, -c * b]) / nrm ** 2 + rng.uniform(-300, 300) * np.array([-b, a]) / nrm)
+    if case == "huge_coordinates":
+        kA = kA * np.float32(1e33)
+        kB = kB * np.float32(1e33)
+    elif case == "large_F":
+        F = F * 1e28
+    elif case == "infinite_point":
+        kB[1] = [np.inf, 5.0]
+    elif case == "nan_point":
+        kB[3] = [np.nan, 5.0]
+    else:
+        F = F * 1e300
+    s = _band_copy_set(rng, nA, F, kA, kB, "band fallbacks: " + case)
+    check_case(ch, orc, s, s.pairs, schedule=1, epi_px=4.0)
+
+
 def test_many_pairs_medium(ch, orc):
     s = synth.config1(seed=11, n_images=12, lo=1500, hi=4500)
     check_case(ch, orc, s, s.pairs, schedule=1)
