@@ -274,84 +274,70 @@ __global__ void __launch_bounds__(256) k_fix_fp64(const uint8_t* __restrict__ de
   const int lane = threadIdx.x & 31;
   uint64_t nf = *nflag_feat;
   if (nf > max_feat) nf = max_feat;
-  // warps numbered across CTAs first, so that a short flagged list spreads
-  // over the SMs (the FP64 pipe of one SM is narrow)
+  // one warp per flagged feature, warps numbered across CTAs first, so that a
+  // short flagged list spreads over the SMs (the FP64 pipe of one SM is narrow)
   const uint64_t warp = (uint64_t)(threadIdx.x >> 5) * gridDim.x + blockIdx.x;
   const uint64_t nwarp = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   unsigned long long done = 0;
-  for (uint64_t base = warp * 32; base < nf; base += nwarp * 32) {
-    // this lane's feature and its flagged rows (bit r of word k: row 32 k + r)
-    const uint64_t idx = base + lane;
-    const bool valid = idx < nf;
-    const uint32_t f = valid ? flaglist[idx] : 0u;
-    uint32_t m[6], cnt = 0;
+  for (uint64_t i = warp; i < nf; i += nwarp) {
+    const uint32_t f = flaglist[i];
+    // lane l holds columns 4 l .. 4 l + 3: t_j = x_j - mu_j exactly as the ordered sequence has it
+    const uint32_t xw = __ldg(reinterpret_cast<const uint32_t*>(desc + (uint64_t)f * DIM) + lane);
+    double t[4];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) {
-      m[k] = valid ? flagmask[(uint64_t)f * 6 + k] : 0u;
-      cnt += __popc(m[k]);
-    }
-    uint32_t incl = cnt;
+    for (int e = 0; e < 4; ++e) t[e] = __dsub_rn((double)((xw >> (8 * e)) & 0xFFu), mu_s[4 * lane + e]);
+    for (int w = 0; w < 6; ++w) {
+      uint32_t mw = flagmask[(uint64_t)f * 6 + w];  // the same word in every lane
+      while (mw) {
+        const uint32_t row = 32u * w + (uint32_t)(__ffs(mw) - 1);
+        mw &= mw - 1u;
+        const double2* Rr = reinterpret_cast<const double2*>(R + (size_t)row * DIM + 4 * lane);
+        const double2 r01 = __ldg(Rr), r23 = __ldg(Rr + 1);
+        const double p[4] = {__dmul_rn(r01.x, t[0]), __dmul_rn(r01.y, t[1]), __dmul_rn(r23.x, t[2]),
+                             __dmul_rn(r23.y, t[3])};
+        // The ordered sum s_ord = (..((p_0 + p_1) + p_2) ..) + p_127 has |s_ord - sum p| <=
+        // gamma_127 sum |p| (gamma_n = n u / (1 - n u), u = 2^-53); this warp's tree sum s (every
+        // p_j through at most 8 additions) has |s - sum p| <= gamma_8 sum |p|, and the tree sum A
+        // of the |p_j| is at least (1 - gamma_8) sum |p|.  So |s| > 1.6e-14 A (> (gamma_127 +
+        // gamma_8) A / (1 - gamma_8), roundings of the test included) fixes the sign of sum p and
+        // therefore of s_ord (which cannot be 0 then); the absolute term covers underflow.
+        // Otherwise the ordered sequence itself is evaluated.
+        double sp = __dadd_rn(__dadd_rn(__dadd_rn(p[0], p[1]), p[2]), p[3]);
+        double ap = __dadd_rn(__dadd_rn(__dadd_rn(fabs(p[0]), fabs(p[1])), fabs(p[2])), fabs(p[3]));
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const uint32_t o = __shfl_up_sync(0xFFFFFFFFu, incl, d);
-      if (lane >= d) incl += o;
-    }
-    const uint32_t excl = incl - cnt;
-    const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-    for (uint32_t r0 = 0; r0 < total; r0 += 32) {
-      const uint32_t r = r0 + lane;
-      // owner: the lane whose rows [excl, incl) hold r (incl is non-decreasing)
-      uint32_t owner = 0;
-#pragma unroll
-      for (uint32_t st = 16; st >= 1; st >>= 1) {
-        const uint32_t v = __shfl_sync(0xFFFFFFFFu, incl, owner + st - 1);
-        if (v <= r) owner += st;
-      }
-      owner = min(owner, 31u);
-      uint32_t k = r - __shfl_sync(0xFFFFFFFFu, excl, owner);
-      const uint32_t fo = __shfl_sync(0xFFFFFFFFu, f, owner);
-      uint32_t row = 0xFFFFFFFFu;
-#pragma unroll
-      for (int w = 0; w < 6; ++w) {
-        const uint32_t mw = __shfl_sync(0xFFFFFFFFu, m[w], owner);
-        const uint32_t c = __popc(mw);
-        if (row == 0xFFFFFFFFu) {
-          if (k < c) row = 32u * w + __fns(mw, 0u, (int)k + 1);
-          else k -= c;
+        for (int o = 16; o > 0; o >>= 1) {
+          sp = __dadd_rn(sp, __shfl_xor_sync(0xFFFFFFFFu, sp, o));
+          ap = __dadd_rn(ap, __shfl_xor_sync(0xFFFFFFFFu, ap, o));
         }
-      }
-      if (r >= total || row == 0xFFFFFFFFu) continue;
-      ++done;
-      const uint4* xr = reinterpret_cast<const uint4*>(desc + (uint64_t)fo * DIM);
-      const double* Rr = R + (size_t)row * DIM;
-      double s = 0.0;
-      for (int c = 0; c < 8; ++c) {  // 16 descriptor bytes per step
-        const uint4 v = __ldg(xr + c);
-        const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
-        double p[16];
-#pragma unroll
-        for (int e = 0; e < 16; ++e) {
-          const int j = 16 * c + e;
-          const double t = __dsub_rn((double)((w4[e >> 2] >> (8 * (e & 3))) & 0xFFu), mu_s[j]);
-          p[e] = __dmul_rn(__ldg(Rr + j), t);
-        }
-#pragma unroll
-        for (int e = 0; e < 16; ++e) s = __dadd_rn(s, p[e]);
-      }
-      if (s > 0.0) {
-        if (row < kp.code_bits) {
-          atomicOr(&codes[(uint64_t)fo * 4 + (row >> 5)], 1u << (row & 31));
+        bool pos;
+        if (fabs(sp) > __dadd_rn(__dmul_rn(1.6e-14, ap), 1e-290)) {  // warp-uniform
+          pos = sp > 0.0;
         } else {
-          const uint32_t rt = row - kp.code_bits;
-          const uint32_t t = rt / kp.bits_per_table, i = rt % kp.bits_per_table;
-          const uint64_t byte = (uint64_t)fo * 8 + t;
-          atomicOr(reinterpret_cast<uint32_t*>(buckets) + (byte >> 2), 1u << (8 * (byte & 3) + i));
+          double so = 0.0;
+          for (int j = 0; j < DIM; ++j) {
+            const int e = j & 3;
+            const double mine = e == 0 ? p[0] : e == 1 ? p[1] : e == 2 ? p[2] : p[3];
+            so = __dadd_rn(so, __shfl_sync(0xFFFFFFFFu, mine, j >> 2));
+          }
+          pos = so > 0.0;
+        }
+        if (lane == 0) {
+          ++done;
+          if (pos) {
+            if (row < kp.code_bits) {
+              atomicOr(&codes[(uint64_t)f * 4 + (row >> 5)], 1u << (row & 31));
+            } else {
+              const uint32_t rt = row - kp.code_bits;
+              const uint32_t tt = rt / kp.bits_per_table, bi = rt % kp.bits_per_table;
+              const uint64_t byte = (uint64_t)f * 8 + tt;
+              atomicOr(reinterpret_cast<uint32_t*>(buckets) + (byte >> 2), 1u << (8 * (byte & 3) + bi));
+            }
+          }
         }
       }
     }
   }
   // one counter update per warp
-  for (int o = 16; o > 0; o >>= 1) done += __shfl_xor_sync(0xFFFFFFFFu, done, o);
   if (lane == 0 && done) atomicAdd(n_reeval, done);
 }
 

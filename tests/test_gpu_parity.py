@@ -517,6 +517,32 @@ def test_band_edge_decisions(ch, orc, sched):
     check_case(ch, orc, s, pairs, tuning=tuning, schedule=1 if tuning else sched, epi_px=d)
 
 
+def test_reevaluation_ordered_path(ch, orc):
+    """Sec. 5.1 signs whose ordered FP64 sum is rounding noise: rows of R made orthogonal, in FP64,
+    to one feature's centred descriptor each (112 rows, 112 features).  The re-evaluation's
+    warp-parallel sign test cannot decide these and evaluates the ordered sequence itself; codes,
+    buckets and matches must equal the oracle's, and the constructed projections must indeed lie
+    inside the parallel test's undecided zone."""
+    s = synth.random_set(717, [300, 260, 280])
+    R = np.array(s.R[:176], np.float64)
+    mu = orc.mean(s.desc)
+    rows = list(range(0, 128, 2)) + list(range(128, 176))
+    for f, b in enumerate(rows):
+        t = s.desc[f].astype(np.float64) - mu
+        R[b] = R[b] - (R[b] @ t) / (t @ t) * t
+    s2 = synth.ImageSet(s.desc, s.img_off, s.pairs, R, "orthogonal rows")
+    v = orc.projections(s.desc[:len(rows)], mu, R, 176)
+    undecided = 0
+    for f, b in enumerate(rows):
+        t = s.desc[f].astype(np.float64) - mu
+        if abs(v[f, b]) <= 1.6e-14 * np.abs(R[b] * t).sum():
+            undecided += 1
+    assert undecided >= len(rows) // 2
+    for prec in (0, 1):
+        ds, codes, buckets, stats = check_case(ch, orc, s2, s2.pairs, precision=prec)
+        assert stats["n_reevaluated"] >= len(rows)
+
+
 def _band_copy_set(rng, nA, F, kA, kB, name):
     A = synth.sift_like(rng, nA)
     return synth.ImageSet(np.concatenate([A, A]), np.array([0, nA, 2 * nA], np.uint64),
