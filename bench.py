@@ -305,9 +305,10 @@ def roofline_of(ch, p, s, ds, stage_ms, tuning, n_sm):
         pairs = np.concatenate([s.pairs, s.pairs[:, ::-1]])
     entries = lookup_entries(ds.buckets_np(T), s.img_off, pairs, T, m)
     queries = float(s.sizes()[pairs[:, 0]].sum())
-    t_match = statistics.mean(stage_ms["match"]) / 1e3
-    kernel = {ch.CASHASH_KERNEL_JOIN: "k_join", ch.CASHASH_KERNEL_JOIN_TC: "k_join_tc"}.get(tuning.get("kernel"),
-                                                                                           "k_match")
+    warp_only = tuning.get("kernel") == ch.CASHASH_KERNEL_WARP  # the exact warp-per-query kernel alone
+    t_match = statistics.mean(stage_ms["fallback" if warp_only else "match"]) / 1e3
+    kernel = {ch.CASHASH_KERNEL_JOIN: "k_join", ch.CASHASH_KERNEL_JOIN_TC: "k_join_tc",
+              ch.CASHASH_KERNEL_WARP: "k_match_fallback"}.get(tuning.get("kernel"), "k_match")
     touched = 20.0 * entries + queries * (p.top_k * 128 + 128 + 16 + 8 + 48)
     achieved = touched / t_match / 1e9
     traffic = None
@@ -414,7 +415,8 @@ def run_ours(args):
 
     F_dev = torch.from_numpy(np.ascontiguousarray(s.F)).to(dev) if band else None
     if args.kernel != "auto" and sched == ch.CASHASH_SCHED_PERSISTENT:
-        kid = {"join": ch.CASHASH_KERNEL_JOIN, "join_tc": ch.CASHASH_KERNEL_JOIN_TC, "query": ch.CASHASH_KERNEL_QUERY}
+        kid = {"join": ch.CASHASH_KERNEL_JOIN, "join_tc": ch.CASHASH_KERNEL_JOIN_TC, "query": ch.CASHASH_KERNEL_QUERY,
+               "warp": ch.CASHASH_KERNEL_WARP}
         ch.cashash_plan_set_tuning(plan, kid[args.kernel], 4 if args.kernel == "join" else 512, 0)
     tuning = ch.cashash_plan_get_tuning(plan)
     if sched == ch.CASHASH_SCHED_PERSISTENT and not args.no_autotune and args.kernel == "auto":
@@ -569,7 +571,7 @@ def run_ours(args):
                                      (", tau %d" % args.tau if args.tau is not None else "") +
                                      (", mutual check" if args.mutual else "") +
                                      (", single candidates accepted" if args.accept_single else ""),
-                           "kernel_tuning": {"kernel": {1: "join", 2: "query", 3: "join_tc"}.get(tuning["kernel"], "per_pair"),
+                           "kernel_tuning": {"kernel": {1: "join", 2: "query", 3: "join_tc", 4: "warp"}.get(tuning["kernel"], "per_pair"),
                                              "tile": tuning["tile"], "ctas_per_sm": tuning["ctas_per_sm"],
                                              "autotuned": tuning["ms_sample"] > 0},
                            "matches_per_step": int(chunk_matches[0] if args.chunk_pairs else stats["n_matches"]),
@@ -633,7 +635,7 @@ def config3_forms(ch, torch, dev):
         out[name] = {"pairs_per_s": P / (statistics.mean(ms) / 1e3), "ms_per_step": statistics.mean(ms),
                      "steps": steps, "warmup": warm, "matches": int(moff[P].item())}
         if tuning:
-            out[name]["kernel_tuning"] = {"kernel": {1: "join", 2: "query", 3: "join_tc"}.get(tuning["kernel"]),
+            out[name]["kernel_tuning"] = {"kernel": {1: "join", 2: "query", 3: "join_tc", 4: "warp"}.get(tuning["kernel"]),
                                           "tile": tuning["tile"], "ctas_per_sm": tuning["ctas_per_sm"]}
         plan.close()
         ctx.close()
@@ -704,7 +706,7 @@ def run_tau_sweep(args):
         rows.append({"tau": tau, "pairs_per_s": P / (statistics.mean(ms) / 1e3), "ms_per_step": statistics.mean(ms),
                      "matches": n, "planted_found": hit, "planted": int(len(pk_keys)),
                      "recall": hit / max(1, len(pk_keys)), "precision_vs_planted": hit / max(1, n),
-                     "kernel_tuning": {"kernel": {1: "join", 2: "query", 3: "join_tc"}.get(tuning["kernel"]),
+                     "kernel_tuning": {"kernel": {1: "join", 2: "query", 3: "join_tc", 4: "warp"}.get(tuning["kernel"]),
                                        "tile": tuning["tile"], "ctas_per_sm": tuning["ctas_per_sm"]},
                      "parity": {"pairs_checked": par["pairs_checked"], "mismatches": par["mismatches"]}})
         plan.close()
@@ -938,7 +940,7 @@ def main():
     ap.add_argument("--thresholds", default="learned", choices=["learned", "fresh"],
                     help="fresh: clear the learned per-pair Hamming thresholds before every timed step")
     ap.add_argument("--no-autotune", action="store_true", help="keep the plan's default kernel configuration")
-    ap.add_argument("--kernel", default="auto", choices=["auto", "join", "join_tc", "query"],
+    ap.add_argument("--kernel", default="auto", choices=["auto", "join", "join_tc", "query", "warp"],
                     help="batched matching kernel: autotuned (auto) or forced")
     ap.add_argument("--mutual", action="store_true", help="mutual check (every pair matched in both directions)")
     ap.add_argument("--chunk-pairs", type=int, default=0,

@@ -220,19 +220,22 @@ int cashash_plan_set_threshold_hint(cashash_plan* plan, uint32_t hamming, int fi
 /* Kernel configuration of a batched (persistent) plan.  Every configuration
  * gives the same, exact results; they differ in speed only.  The paper has no
  * counterpart (it runs one kernel shape). */
-enum { CASHASH_KERNEL_JOIN = 1, CASHASH_KERNEL_QUERY = 2, CASHASH_KERNEL_JOIN_TC = 3 };
+enum { CASHASH_KERNEL_JOIN = 1, CASHASH_KERNEL_QUERY = 2, CASHASH_KERNEL_JOIN_TC = 3, CASHASH_KERNEL_WARP = 4 };
 typedef struct {
   uint32_t kernel;       /* CASHASH_KERNEL_JOIN: bucket join with warp-level (mma.sync) tensor-core
                             Hamming distances (query images that fit its shared-memory counters);
                             CASHASH_KERNEL_JOIN_TC: the same join with tcgen05 MMAs into tensor
                             memory, 128 query rows per tile (same limit);
                             CASHASH_KERNEL_QUERY: per-query speculative kernel over shared-memory
-                            staged table chunks */
+                            staged table chunks;
+                            CASHASH_KERNEL_WARP: one warp per query, exact without a threshold guess
+                            (no calibration; the fit for a few pairs, where the other kernels leave
+                            most SMs idle) */
   uint32_t tile;         /* JOIN: candidate tiles of 8 columns held in registers (2 or 4; 4 with
-                            the band); JOIN_TC: ignored (0);
+                            the band); JOIN_TC, WARP: ignored (0);
                             QUERY: queries per CTA (256, or 512 when top_k <= 16) */
   uint32_t ctas_per_sm;  /* JOIN, JOIN_TC: resident CTAs per SM, 0 = as many as fit (JOIN_TC: at most
-                            2); QUERY: ignored */
+                            2); QUERY, WARP: ignored */
   uint32_t reserved;
   double ms_sample;      /* set by cashash_plan_autotune: matching time (ms) of its sample with
                             this configuration; -1 otherwise */

@@ -23,7 +23,7 @@ CASHASH_EOVERFLOW, CASHASH_EDEVICE, CASHASH_ETIMEOUT, CASHASH_ENOTSUP = 4, 5, 6,
 CASHASH_FP32, CASHASH_BF16 = 0, 1
 CASHASH_SCHED_PER_PAIR, CASHASH_SCHED_PERSISTENT = 0, 1
 CASHASH_NOALLOC_MAX_QUERIES = 65536
-CASHASH_KERNEL_JOIN, CASHASH_KERNEL_QUERY, CASHASH_KERNEL_JOIN_TC = 1, 2, 3
+CASHASH_KERNEL_JOIN, CASHASH_KERNEL_QUERY, CASHASH_KERNEL_JOIN_TC, CASHASH_KERNEL_WARP = 1, 2, 3, 4
 CASHASH_FLAG_MUTUAL, CASHASH_FLAG_ACCEPT_SINGLE = 1, 2
 
 

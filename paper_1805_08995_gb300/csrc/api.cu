@@ -685,6 +685,9 @@ int plan_configure(cashash_plan* pl, cashash_tuning t) {
     for (uint32_t i : order)
       for (uint32_t q0 = 0; q0 < info[i].nA; q0 += t.tile) items.push_back(make_uint2(i, q0));
     grid = match_grid(c->p.top_k, 1, epi, c->p.n_tables, (uint32_t)items.size(), t.tile);
+  } else if (t.kernel == CASHASH_KERNEL_WARP) {
+    t.tile = 0;  // no work items: the exact warp-per-query kernel walks the result array
+    t.ctas_per_sm = 0;
   } else {
     return CASHASH_EINVAL;
   }
@@ -853,6 +856,8 @@ int enqueue_match(cashash_ctx* c, cashash_plan* pl, const double* F_dev, uint64_
   a.queue = pl->d_queue;
   a.tau_pair = pl->d_tau;
   a.tau_fixed = pl->tau_fixed;
+  const bool warp_only = pl->persistent && pl->tune.kernel == CASHASH_KERNEL_WARP;
+  a.all_queries = warp_only ? 1u : 0u;
   a.join = pl->tables;
   a.jqueue = pl->d_queue;
   a.jhist = pl->d_jhist;
@@ -864,11 +869,11 @@ int enqueue_match(cashash_ctx* c, cashash_plan* pl, const double* F_dev, uint64_
     a.items = pl->d_items;
     a.n_items = pl->n_items;
     a.item_ctr = pl->d_item_ctr + P;
-    if (c->p.epi_px < 0.0) {  // threshold guesses for pairs without one (either kernel)
+    if (c->p.epi_px < 0.0 && !warp_only) {  // threshold guesses for pairs without one (either kernel)
       StageTimer tm(c, CASHASH_STAGE_CALIBRATE, stream, capturing);
       CK(launch_join_calibrate(a, stream));
     }
-    {
+    if (!warp_only) {
       StageTimer tm(c, CASHASH_STAGE_MATCH, stream, capturing);
       if (pl->join && pl->tune.kernel == CASHASH_KERNEL_JOIN_TC) CK(launch_join_tc(a, pl->grid, stream));
       else if (pl->join) CK(launch_join(a, pl->grid, pl->tune.tile, stream));
@@ -948,9 +953,10 @@ int cashash_match_plan(cashash_ctx* c, cashash_plan* pl, const double* F_dev, ui
     }
     CK(cudaGraphLaunch(pl->gexec, stream));
     if (c->profiling) {  // the graph holds the stage events as external event-record nodes
-      c->ev_used[CASHASH_STAGE_MATCH] = c->ev_used[CASHASH_STAGE_COMPACT] = 1;
-      c->ev_used[CASHASH_STAGE_FALLBACK] = 1;
-      if (c->p.epi_px < 0.0) c->ev_used[CASHASH_STAGE_CALIBRATE] = 1;
+      const bool warp_only = pl->tune.kernel == CASHASH_KERNEL_WARP;  // the fallback kernel alone
+      c->ev_used[CASHASH_STAGE_COMPACT] = c->ev_used[CASHASH_STAGE_FALLBACK] = 1;
+      if (!warp_only) c->ev_used[CASHASH_STAGE_MATCH] = 1;
+      if (c->p.epi_px < 0.0 && !warp_only) c->ev_used[CASHASH_STAGE_CALIBRATE] = 1;
     }
   } else {
     const int st = enqueue_match(c, pl, F_dev, match_off, matches, cap, stream, false);
@@ -1069,6 +1075,11 @@ int cashash_plan_autotune(cashash_ctx* c, cashash_plan* pl, const double* F_dev,
     cashash_tuning t{};
     t.kernel = CASHASH_KERNEL_QUERY;
     t.tile = tile;
+    cand.push_back(t);
+  }
+  {
+    cashash_tuning t{};
+    t.kernel = CASHASH_KERNEL_WARP;
     cand.push_back(t);
   }
   // Two interleaved rounds (so that clock and cache drift hit every candidate),
@@ -1205,7 +1216,7 @@ int cashash_get_stats(cashash_ctx* c, cashash_stats* out) {
 int cashash_set_host_tuning(cashash_ctx* c, const cashash_tuning* t) {
   if (!c) return CASHASH_EINVAL;
   if (t && t->kernel != CASHASH_KERNEL_JOIN && t->kernel != CASHASH_KERNEL_JOIN_TC &&
-      t->kernel != CASHASH_KERNEL_QUERY)
+      t->kernel != CASHASH_KERNEL_QUERY && t->kernel != CASHASH_KERNEL_WARP)
     return CASHASH_EINVAL;
   HostWS& h = c->hw;
   h.has_tune = t != nullptr;

@@ -279,6 +279,7 @@ struct MatchArgs {
   uint32_t* tau_pair;        // speculative form, per pair: 0 = no guess yet, else (threshold + 1);
                              // learned as the largest k-th Hamming distance seen, kept across launches
   uint32_t tau_fixed;        // speculative form: do not learn (keep the values set by the host)
+  uint32_t all_queries;      // exact warp-per-query kernel: every query, not only the PENDING ones
   const uint8_t* join;       // bucket join: table buffer holding the bucket-sorted tables
   uint32_t* jqueue;          // bucket join: [grid][na_max][JSEG] survivor lists
   uint32_t* jhist;           // bucket join: [P][HBINS] k-th Hamming distances seen per pair

@@ -282,15 +282,121 @@ __global__ void __launch_bounds__(TPB, (TPB <= 512 ? 2 : 1)) k_match(MatchArgs a
 // counts once), k lanes compute the exact distances and lane 0 applies the
 // ratio test.
 // ---------------------------------------------------------------------------
+// One query g of the per-query result array, by one warp (exact): the pair
+// holding g, the query's buckets walked with the lanes side by side, the
+// merge of the lanes' k smallest distinct keys, distances and the ratio test.
+template <int KC, bool EPI>
+__device__ __forceinline__ void fallback_query(const MatchArgs& a, uint64_t g, int lane, uint32_t thr_user,
+                                               double dd) {
+  const KParams& kp = a.kp;
+  const uint32_t T = kp.n_tables, K = kp.top_k;
+  // pair: the last with qbase <= g.  32-way search; invariant: pairs[lo].qbase <= g
+  // and the answer lies in [lo, hi].  Lane l probes lo + 1 + l * span / 32.
+  uint32_t lo = 0, hi = a.n_pairs - 1;
+  while (lo < hi) {
+    const uint32_t lo0 = lo, span = hi - lo;
+    const uint32_t piv = lo0 + 1u + (uint32_t)(((uint64_t)lane * span) / 32u);  // in [lo + 1, hi]
+    const uint32_t m = __ballot_sync(0xFFFFFFFFu, a.pairs[piv].qbase <= g);  // a prefix of the lanes
+    if (m == 0u) {
+      hi = lo0;
+    } else {
+      const int l = 31 - __clz(m);  // lane l + 1 probes a later pair, past g
+      lo = lo0 + 1u + (uint32_t)(((uint64_t)l * span) / 32u);
+      if (l < 31) hi = lo0 + (uint32_t)(((uint64_t)(l + 1) * span) / 32u);
+    }
+  }
+  const PairInfo P = a.pairs[lo];
+  const uint32_t q = (uint32_t)(g - P.qbase);
+  const uint4 qc = __ldg(reinterpret_cast<const uint4*>(a.codes) + P.a0 + q);
+  const uint2 qb = __ldg(reinterpret_cast<const uint2*>(a.buckets) + P.a0 + q);
+  EpiQ eq{};
+  if (EPI) eq = epi_query(a.F + 9 * (size_t)lo, __ldg(reinterpret_cast<const float2*>(a.kpts) + P.a0 + q), dd);
+  uint32_t top[KC];
+#pragma unroll
+  for (int s = 0; s < KC; ++s) top[s] = KEY_INF;
+  const uint32_t nch = (P.nB + JC - 1) / JC;
+  for (uint32_t c = 0; c < nch; ++c) {
+    const uint16_t* blk =
+        reinterpret_cast<const uint16_t*>(a.tables + (uint64_t)(P.bchunk0 + c) * chunk_bytes(T));
+    const uint4* gc = reinterpret_cast<const uint4*>(a.codes) + P.b0 + (uint64_t)c * JC;
+    for (uint32_t t = 0; t < T; ++t) {
+      const uint32_t v = (t < 4 ? (qb.x >> (8 * t)) : (qb.y >> (8 * (t - 4)))) & 0xFFu;
+      const uint32_t s0 = blk[t * OFF_STRIDE + v], s1 = blk[t * OFF_STRIDE + v + 1];
+      const uint16_t* il = blk + T * OFF_STRIDE + t * JC;
+      for (uint32_t pos = s0 + lane; pos < s1; pos += 32) {
+        const uint32_t jl = il[pos];
+        const uint32_t key = (hamming128(__ldg(gc + jl), qc) << 24) | (c * JC + jl);
+        if (key >= thr_user) continue;
+        if (EPI && !epi_keep_fast(eq, __ldg(reinterpret_cast<const float2*>(a.kpts) + P.b0 + (uint64_t)c * JC + jl)))
+          continue;
+        if (key < top[KC - 1]) topk_insert<KC>(top, key);
+      }
+    }
+  }
+  // merge: round r leaves the r-th smallest distinct key in lane r
+  uint32_t mine = KEY_INF;
+  for (uint32_t r = 0; r < K; ++r) {
+    uint32_t m = top[0];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
+    if (m == KEY_INF) break;  // warp-uniform
+    if ((uint32_t)lane == r) mine = m;
+    if (top[0] == m) {
+#pragma unroll
+      for (int s = 0; s + 1 < KC; ++s) top[s] = top[s + 1];
+      top[KC - 1] = KEY_INF;
+    }
+  }
+  // exact distances of the k ranked candidates (Step 4), ratio test
+  const uint64_t fa = P.a0 + q;
+  uint64_t dj = ~0ull;  // (d << 32) | j
+  if (mine != KEY_INF) {
+    const uint32_t j = mine & 0xFFFFFFu;
+    const uint64_t fb = P.b0 + j;
+    const uint4* arow = reinterpret_cast<const uint4*>(a.desc + fa * DIM);
+    const uint4* brow = reinterpret_cast<const uint4*>(a.desc + fb * DIM);
+    uint32_t dot = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+      const uint4 av = __ldg(arow + w), bv = __ldg(brow + w);
+      dot = __dp4a(av.x, bv.x, dot);
+      dot = __dp4a(av.y, bv.y, dot);
+      dot = __dp4a(av.z, bv.z, dot);
+      dot = __dp4a(av.w, bv.w, dot);
+    }
+    const uint32_t d = __ldg(a.sqnorm + fa) + __ldg(a.sqnorm + fb) - 2u * dot;
+    dj = ((uint64_t)d << 32) | j;
+  }
+  const uint32_t nv = __popc(__ballot_sync(0xFFFFFFFFu, mine != KEY_INF));
+  uint64_t best = dj;  // smallest (d, j)
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(0xFFFFFFFFu, best, o));
+  uint64_t second = dj == best ? ~0ull : dj;  // keys are distinct, so exactly one lane holds best
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) second = min(second, __shfl_xor_sync(0xFFFFFFFFu, second, o));
+  if (lane == 0) {
+    const uint32_t d1 = (uint32_t)(best >> 32), j1 = (uint32_t)best, d2 = (uint32_t)(second >> 32);
+    const bool matched = ratio_ok(kp, nv, d1, d2);
+    a.res[g] = matched ? j1 : NO_MATCH;
+    if (matched) atomicAdd(a.pair_cnt + lo, 1ull);
+  }
+}
+
 template <int KC, bool EPI>
 __global__ void __launch_bounds__(128) k_match_fallback(MatchArgs a) {
   const KParams kp = a.kp;
-  const uint32_t T = kp.n_tables, K = kp.top_k;
   const uint32_t thr_user = kp.tau < kp.code_bits ? ((kp.tau + 1u) << 24) : KEY_INF;
   const double dd = kp.epi_px * kp.epi_px;
   const int lane = threadIdx.x & 31;
   const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint64_t nwarp = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  if (a.all_queries) {  // every query, one warp each (the exact warp-per-query configuration)
+    for (uint64_t g = warp; g < a.n_res; g += nwarp) {
+      fallback_query<KC, EPI>(a, g, lane, thr_user, dd);
+      __syncwarp();
+    }
+    return;
+  }
   for (uint64_t g0 = warp * 128; g0 < a.n_res; g0 += nwarp * 128) {
     uint32_t pend[4];
 #pragma unroll
@@ -303,97 +409,7 @@ __global__ void __launch_bounds__(128) k_match_fallback(MatchArgs a) {
       while (pend[i]) {
         const int b = __ffs(pend[i]) - 1;
         pend[i] &= pend[i] - 1u;
-        const uint64_t g = g0 + 32 * i + b;
-        // pair: the last with qbase <= g.  32-way search; invariant: pairs[lo].qbase <= g
-        // and the answer lies in [lo, hi].  Lane l probes lo + 1 + l * span / 32.
-        uint32_t lo = 0, hi = a.n_pairs - 1;
-        while (lo < hi) {
-          const uint32_t lo0 = lo, span = hi - lo;
-          const uint32_t piv = lo0 + 1u + (uint32_t)(((uint64_t)lane * span) / 32u);  // in [lo + 1, hi]
-          const uint32_t m = __ballot_sync(0xFFFFFFFFu, a.pairs[piv].qbase <= g);  // a prefix of the lanes
-          if (m == 0u) {
-            hi = lo0;
-          } else {
-            const int l = 31 - __clz(m);  // lane l + 1 probes a later pair, past g
-            lo = lo0 + 1u + (uint32_t)(((uint64_t)l * span) / 32u);
-            if (l < 31) hi = lo0 + (uint32_t)(((uint64_t)(l + 1) * span) / 32u);
-          }
-        }
-        const PairInfo P = a.pairs[lo];
-        const uint32_t q = (uint32_t)(g - P.qbase);
-        const uint4 qc = __ldg(reinterpret_cast<const uint4*>(a.codes) + P.a0 + q);
-        const uint2 qb = __ldg(reinterpret_cast<const uint2*>(a.buckets) + P.a0 + q);
-        EpiQ eq{};
-        if (EPI) eq = epi_query(a.F + 9 * (size_t)lo, __ldg(reinterpret_cast<const float2*>(a.kpts) + P.a0 + q), dd);
-        uint32_t top[KC];
-#pragma unroll
-        for (int s = 0; s < KC; ++s) top[s] = KEY_INF;
-        const uint32_t nch = (P.nB + JC - 1) / JC;
-        for (uint32_t c = 0; c < nch; ++c) {
-          const uint16_t* blk =
-              reinterpret_cast<const uint16_t*>(a.tables + (uint64_t)(P.bchunk0 + c) * chunk_bytes(T));
-          const uint4* gc = reinterpret_cast<const uint4*>(a.codes) + P.b0 + (uint64_t)c * JC;
-          for (uint32_t t = 0; t < T; ++t) {
-            const uint32_t v = (t < 4 ? (qb.x >> (8 * t)) : (qb.y >> (8 * (t - 4)))) & 0xFFu;
-            const uint32_t s0 = blk[t * OFF_STRIDE + v], s1 = blk[t * OFF_STRIDE + v + 1];
-            const uint16_t* il = blk + T * OFF_STRIDE + t * JC;
-            for (uint32_t pos = s0 + lane; pos < s1; pos += 32) {
-              const uint32_t jl = il[pos];
-              const uint32_t key = (hamming128(__ldg(gc + jl), qc) << 24) | (c * JC + jl);
-              if (key >= thr_user) continue;
-              if (EPI && !epi_keep_fast(eq, __ldg(reinterpret_cast<const float2*>(a.kpts) + P.b0 + (uint64_t)c * JC + jl)))
-                continue;
-              if (key < top[KC - 1]) topk_insert<KC>(top, key);
-            }
-          }
-        }
-        // merge: round r leaves the r-th smallest distinct key in lane r
-        uint32_t mine = KEY_INF;
-        for (uint32_t r = 0; r < K; ++r) {
-          uint32_t m = top[0];
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
-          if (m == KEY_INF) break;  // warp-uniform
-          if ((uint32_t)lane == r) mine = m;
-          if (top[0] == m) {
-#pragma unroll
-            for (int s = 0; s + 1 < KC; ++s) top[s] = top[s + 1];
-            top[KC - 1] = KEY_INF;
-          }
-        }
-        // exact distances of the k ranked candidates (Step 4), ratio test
-        const uint64_t fa = P.a0 + q;
-        uint64_t dj = ~0ull;  // (d << 32) | j
-        if (mine != KEY_INF) {
-          const uint32_t j = mine & 0xFFFFFFu;
-          const uint64_t fb = P.b0 + j;
-          const uint4* arow = reinterpret_cast<const uint4*>(a.desc + fa * DIM);
-          const uint4* brow = reinterpret_cast<const uint4*>(a.desc + fb * DIM);
-          uint32_t dot = 0;
-#pragma unroll
-          for (int w = 0; w < 8; ++w) {
-            const uint4 av = __ldg(arow + w), bv = __ldg(brow + w);
-            dot = __dp4a(av.x, bv.x, dot);
-            dot = __dp4a(av.y, bv.y, dot);
-            dot = __dp4a(av.z, bv.z, dot);
-            dot = __dp4a(av.w, bv.w, dot);
-          }
-          const uint32_t d = __ldg(a.sqnorm + fa) + __ldg(a.sqnorm + fb) - 2u * dot;
-          dj = ((uint64_t)d << 32) | j;
-        }
-        const uint32_t nv = __popc(__ballot_sync(0xFFFFFFFFu, mine != KEY_INF));
-        uint64_t best = dj;  // smallest (d, j)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(0xFFFFFFFFu, best, o));
-        uint64_t second = dj == best ? ~0ull : dj;  // keys are distinct, so exactly one lane holds best
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) second = min(second, __shfl_xor_sync(0xFFFFFFFFu, second, o));
-        if (lane == 0) {
-          const uint32_t d1 = (uint32_t)(best >> 32), j1 = (uint32_t)best, d2 = (uint32_t)(second >> 32);
-          const bool matched = ratio_ok(kp, nv, d1, d2);
-          a.res[g] = matched ? j1 : NO_MATCH;
-          if (matched) atomicAdd(a.pair_cnt + lo, 1ull);
-        }
+        fallback_query<KC, EPI>(a, g0 + 32 * i + b, lane, thr_user, dd);
         __syncwarp();
       }
     }
@@ -495,7 +511,7 @@ cudaError_t launch_match_fallback(const MatchArgs& a, cudaStream_t s) {
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const uint64_t want = (a.n_res + 127) / 128;
+  const uint64_t want = a.all_queries ? (a.n_res + 3) / 4 : (a.n_res + 127) / 128;  // 4 warps per CTA
   const unsigned grid = (unsigned)(want < (uint64_t)nsm * 16 ? want : (uint64_t)nsm * 16);
   const bool epi = a.kp.epi_px >= 0.0;
   const uint32_t k = a.kp.top_k;

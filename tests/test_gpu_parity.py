@@ -262,15 +262,15 @@ def test_every_tuning_and_the_autotuner(ch, orc):
             assert np.array_equal(off, eoff)
             assert np.array_equal(mt[:int(off[-1])].cpu().numpy().view(np.uint32), emt)
 
-    J, Q = ch.CASHASH_KERNEL_JOIN, ch.CASHASH_KERNEL_QUERY
-    for kern, tile, ctas in [(J, 4, 0), (J, 2, 0), (J, 4, 1), (J, 2, 1), (Q, 512, 0), (Q, 256, 0)]:
+    J, Q, W = ch.CASHASH_KERNEL_JOIN, ch.CASHASH_KERNEL_QUERY, ch.CASHASH_KERNEL_WARP
+    for kern, tile, ctas in [(J, 4, 0), (J, 2, 0), (J, 4, 1), (J, 2, 1), (Q, 512, 0), (Q, 256, 0), (W, 0, 0)]:
         ch.cashash_plan_set_tuning(plan, kern, tile, ctas)
         t = ch.cashash_plan_get_tuning(plan)
         assert (t["kernel"], t["tile"], t["ctas_per_sm"]) == (kern, tile, ctas)
         check()
     for mp in (5, 0):  # a sample, then the plan itself
         t = ch.cashash_plan_autotune(ctx, plan, max_pairs=mp)
-        assert t["kernel"] in (J, Q) and t["ms_sample"] > 0
+        assert t["kernel"] in (J, Q, ch.CASHASH_KERNEL_JOIN_TC, W) and t["ms_sample"] > 0
         check()
     plan.close()
     ctx.close()
@@ -310,13 +310,14 @@ def test_band_kernels_and_the_autotuner(ch, orc):
             assert np.array_equal(off, eoff)
             assert np.array_equal(mt[:int(off[-1])].cpu().numpy().view(np.uint32), emt)
 
-    for kern, tile, want in [(J, 2, 4), (J, 4, 4), (Q, 512, 512), (Q, 256, 256)]:
+    W = ch.CASHASH_KERNEL_WARP
+    for kern, tile, want in [(J, 2, 4), (J, 4, 4), (Q, 512, 512), (Q, 256, 256), (W, 0, 0)]:
         ch.cashash_plan_set_tuning(plan, kern, tile, 0)
         t = ch.cashash_plan_get_tuning(plan)
         assert (t["kernel"], t["tile"]) == (kern, want)
         check()
     t = ch.cashash_plan_autotune(ctx, plan, F=F, max_pairs=0)
-    assert t["kernel"] in (J, Q) and t["ms_sample"] > 0
+    assert t["kernel"] in (J, Q, ch.CASHASH_KERNEL_JOIN_TC, W) and t["ms_sample"] > 0
     check()
     plan.close()
     ctx.close()
@@ -617,6 +618,21 @@ PARAM_VARIANTS = [
 ]
 
 
+@pytest.mark.parametrize("pk", [dict(), dict(precision=1), dict(epi_px=4.0)] + PARAM_VARIANTS)
+def test_warp_kernel_parameter_variants(ch, orc, pk):
+    """The exact warp-per-query configuration (CASHASH_KERNEL_WARP: every query by the fallback
+    kernel, no threshold guess) with every parameter variant, the band included, on ragged image
+    sizes with an empty image."""
+    sizes = [700, 1300, 0, 260, 4500]
+    s = synth.random_set(203, sizes)
+    pairs = _pairs(sizes)
+    if pk.get("epi_px", -1.0) >= 0:
+        import math
+        s = synth.epipolar_set(45, n_views=5, n_points=9000, arc=2 * math.pi * 5 / 250, z_max=0.355)
+        pairs = s.pairs
+    check_case(ch, orc, s, pairs, tuning=(ch.CASHASH_KERNEL_WARP, 0, 0), schedule=1, **pk)
+
+
 @pytest.mark.parametrize("pk", [dict(), dict(precision=1)] + PARAM_VARIANTS)
 def test_join_tc_parameter_variants(ch, orc, pk):
     """The tcgen05 bucket join (FP8 +-1 rows in shared memory, 128-row tiles,
@@ -697,7 +713,7 @@ def test_host_end_to_end_matches_device_path(ch, orc):
     # a batched context with every host-path kernel configuration
     ctx = ch.cashash_create(ch.cashash_default_params(schedule=ch.CASHASH_SCHED_PERSISTENT), s.R)
     for kernel, tile in ((ch.CASHASH_KERNEL_QUERY, 512), (ch.CASHASH_KERNEL_JOIN, 2), (ch.CASHASH_KERNEL_QUERY, 256),
-                         (ch.CASHASH_KERNEL_JOIN_TC, 0), (0, 0)):
+                         (ch.CASHASH_KERNEL_JOIN_TC, 0), (ch.CASHASH_KERNEL_WARP, 0), (0, 0)):
         ch.cashash_set_host_tuning(ctx, kernel, tile)
         st, off, mt = ch.cashash_run_host(ctx, pinned, s.img_off, pairs, cap)
         assert st == ch.CASHASH_OK
