@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(JT, 2) k_join(MatchArgs a) {
 #pragma unroll
               for (int c = 0; c < 2; ++c) {
                 const int bit = 2 * n + c;
-                if (((ka | kb) >> bit) & 1u) {
+                {  // every slot, without a branch (a column past the run reads feature 0 of B; masked below)
                   const float2 pc = __ldg(kpts + P.b0 + jc[n][c]);
                   const float na = fabsf(fmaf(La.x, pc.x, fmaf(La.y, pc.y, La.z)));
                   const float nb = fabsf(fmaf(Lb.x, pc.x, fmaf(Lb.y, pc.y, Lb.z)));
