@@ -310,7 +310,9 @@ __global__ void __launch_bounds__(JT, 2) k_join(MatchArgs a) {
             ka &= ba;
             kb &= bb;
           }
-          {
+          // with tau or the band survivors are sparse, and a warp whose lanes have none skips the
+          // appends (without them nearly every warp has some, and the vote would only cost)
+          if (!(TAU || EPI) || __any_sync(0xFFFFFFFFu, (ka | kb) != 0u)) {
             // one counter update per row, then the row's survivors at consecutive slots
             uint32_t pa = ka ? atomicAdd(cnt_s + qa_c, (uint32_t)__popc(ka)) : 0u;
             uint32_t pb = kb ? atomicAdd(cnt_s + qb_c, (uint32_t)__popc(kb)) : 0u;
