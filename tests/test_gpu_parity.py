@@ -323,12 +323,13 @@ def test_band_kernels_and_the_autotuner(ch, orc):
     ctx.close()
 
 
-@pytest.mark.parametrize("case", ["plain_persistent", "plain_per_pair", "band", "tuned_query"])
+@pytest.mark.parametrize("case", ["plain_persistent", "plain_per_pair", "band", "tuned_query", "tuned_warp"])
 def test_chunked_matching_resumes(ch, orc, case):
     """A long pair list matched in chunks: the callback stops the run after two
     chunks, a second call resumes at the returned cursor, and the chunks
-    joined equal the oracle's lists for the whole list.  tuned_query: the
-    chunks' plans take the per-query kernel set by cashash_set_host_tuning."""
+    joined equal the oracle's lists for the whole list.  tuned_query /
+    tuned_warp: the chunks' plans take the per-query kernel or the
+    warp-per-query configuration set by cashash_set_host_tuning."""
     import math
     pk = dict(schedule=0 if case == "plain_per_pair" else 1)
     if case == "band":
@@ -348,6 +349,9 @@ def test_chunked_matching_resumes(ch, orc, case):
     if case == "tuned_query":
         ch.cashash_set_host_tuning(ctx, ch.CASHASH_KERNEL_QUERY, 256)
         assert ch.cashash_get_host_tuning(ctx) == {"kernel": ch.CASHASH_KERNEL_QUERY, "tile": 256, "ctas_per_sm": 0}
+    if case == "tuned_warp":
+        ch.cashash_set_host_tuning(ctx, ch.CASHASH_KERNEL_WARP)
+        assert ch.cashash_get_host_tuning(ctx)["kernel"] == ch.CASHASH_KERNEL_WARP
     F = torch.from_numpy(np.ascontiguousarray(s.F)).cuda() if s.F is not None else None
     got = {}
     seen = []
