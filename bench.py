@@ -424,7 +424,9 @@ def run_ours(args):
         tuning = ch.cashash_plan_autotune(ctx, plan, F=F_dev, max_pairs=0, stream=stream)
         if args.chunk_pairs:  # the chunks' plans take the tuned configuration
             ch.cashash_set_host_tuning(ctx, tuning["kernel"], tuning["tile"], tuning["ctas_per_sm"])
-    ch.cashash_set_profiling(ctx, True)
+    # The timed steps run without the library's stage events; the stage times come from a short
+    # pass with them after the timed region (the events add a few microseconds per stage).
+    ch.cashash_set_profiling(ctx, False)
     for _ in range(args.warmup):
         flush.zero_()
         step()
@@ -453,10 +455,6 @@ def run_ours(args):
         e1.record(stream)
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
-        st = ch.cashash_get_stats(ctx)
-        for k, v in st["ms_stage"].items():
-            if v >= 0:
-                stage_ms[k].append(v)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -474,10 +472,6 @@ def run_ours(args):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_max = float(tt.item())
     value = (P_job if split_pairs else P * world) * args.steps / t_max
-    rf = roofline_of(ch, p, s, ds, stage_ms, tuning, torch.cuda.get_device_properties(dev).multi_processor_count)
-
-    # stage timers and counters of the chunked path cover the last chunk only: no kernel roofline
-    roofline = None if args.chunk_pairs else rf
     # parity: the GPU lists of the last timed step, before anything else writes them
     smp = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -485,6 +479,23 @@ def run_ours(args):
     parity = None
     if smp is not None and not args.chunk_pairs:
         parity = parity_check(smp, moff, mt)
+    # stage times (CUDA events inside the library's launch sequence), outside the timed region
+    ch.cashash_set_profiling(ctx, True)
+    for i in range(1 + min(args.steps, 5)):
+        flush.zero_()
+        if args.thresholds == "fresh":
+            ch.cashash_plan_set_threshold_hint(plan, p.code_bits, False)
+        step()
+        torch.cuda.synchronize()
+        if i == 0:
+            continue  # captures the graphs that record the events
+        st = ch.cashash_get_stats(ctx)
+        for k, v in st["ms_stage"].items():
+            if v >= 0:
+                stage_ms[k].append(v)
+    rf = roofline_of(ch, p, s, ds, stage_ms, tuning, torch.cuda.get_device_properties(dev).multi_processor_count)
+    # stage timers and counters of the chunked path cover the last chunk only: no kernel roofline
+    roofline = None if args.chunk_pairs else rf
 
     # end-to-end through the C-ABI with host buffers (pinned descriptors)
     e2e = None
@@ -495,7 +506,7 @@ def run_ours(args):
         mo_h = torch.zeros(P + 1, dtype=torch.int64).pin_memory().numpy().view(np.uint64)
         mt_h = torch.zeros((cap, 2), dtype=torch.int32).pin_memory().numpy().view(np.uint32)
         ctx2 = ch.cashash_create(p, s.R)
-        ch.cashash_set_profiling(ctx2, True)  # per-call copy and device stage times (events)
+        ch.cashash_set_profiling(ctx2, False)  # the timed calls run without the stage events
         if tuning.get("kernel"):  # the host path matches with the same configuration as the timed plan
             ch.cashash_set_host_tuning(ctx2, tuning["kernel"], tuning["tile"], tuning["ctas_per_sm"])
         for _ in range(max(1, args.warmup)):
@@ -511,9 +522,21 @@ def run_ours(args):
                                                matches=mt_h, kpts=kp_pin, F=s.F if band else None)
             ts.append(time.perf_counter() - t0)
             assert st == ch.CASHASH_OK
+        # per-call copy and device stage times from a few more calls with the stage events on
+        ch.cashash_set_profiling(ctx2, True)
+        for i in range(1 + min(args.steps, 5)):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st, off, mth = ch.cashash_run_host(ctx2, pinned, s.img_off, s.pairs, cap, match_off=mo_h,
+                                               matches=mt_h, kpts=kp_pin, F=s.F if band else None)
+            tb = time.perf_counter() - t0
+            assert st == ch.CASHASH_OK
+            if i == 0:
+                continue
             ms = ch.cashash_get_stats(ctx2)["ms_stage"]
             dev_ms = sum(max(ms[k], 0.0) for k in dev_stages)
-            parts.append((ms["h2d"], dev_ms, ms["d2h"], ts[-1] * 1e3 - ms["h2d"] - dev_ms - ms["d2h"]))
+            parts.append((ms["h2d"], dev_ms, ms["d2h"], tb * 1e3 - ms["h2d"] - dev_ms - ms["d2h"]))
         t_e2e = statistics.mean(ts)
         if dist:
             tt = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
@@ -528,8 +551,9 @@ def run_ours(args):
                "breakdown_ms_each": {"h2d": [round(x[0], 3) for x in parts], "device": [round(x[1], 3) for x in parts],
                                      "d2h": [round(x[2], 3) for x in parts],
                                      "host_other": [round(x[3], 3) for x in parts]},
-               "breakdown_note": "device = the stages on the compute stream after the last copy (the column "
-                                 "sums overlap the copy); host_other = wall - h2d - device - d2h"}
+               "breakdown_note": "from separate calls with the library's stage events on: device = the stages "
+                                 "on the compute stream after the last copy (the column sums overlap the copy); "
+                                 "host_other = wall - h2d - device - d2h"}
         if parity is not None:  # the host path's lists of the sampled pairs too
             e2e["parity_mismatches"] = parity_check(smp, torch.from_numpy(mo_h.view(np.int64)),
                                                     torch.from_numpy(mt_h.view(np.int32)))["mismatches"]
