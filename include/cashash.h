@@ -149,7 +149,11 @@ void cashash_destroy(cashash_ctx* ctx);
  * mean over every descriptor of the set (computed exactly from integer
  * column sums, one correctly rounded division).  Writes set->codes,
  * set->buckets, set->sqnorm and set->tables.  Asynchronous on `stream`.
- * Errors: EINVAL (null pointer, bad offsets), ENOMEM, ECUDA. */
+ * With mean_host NULL, a second and later call for the same set (the same
+ * struct contents and image offsets) under the same profiling setting
+ * replays the launch sequence as one CUDA graph captured on that second
+ * call; it reads the buffers' current contents.  Calls on one context must
+ * not overlap.  Errors: EINVAL (null pointer, bad offsets), ENOMEM, ECUDA. */
 int cashash_build_codes(cashash_ctx* ctx, const cashash_set* set, const double* mean_host,
                         cashash_stream_t stream);
 
