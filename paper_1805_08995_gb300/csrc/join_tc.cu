@@ -426,7 +426,7 @@ cudaError_t run_join_tc(const MatchArgs* a, uint32_t grid, cudaStream_t s, uint3
     e = cudaFuncGetAttributes(&fa, k_join_tc<KC, TAU, EPI>);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     if (e != cudaSuccess) return e;
-    const size_t per_cta = smem + fa.sharedSizeBytes + 1024;  // + the driver's reserve per CTA
+    const size_t per_cta = smem + fa.sharedSizeBytes + 1024;  // + the 1 KB the system reserves per CTA
     const uint32_t by_smem = (uint32_t)((size_t)sm_smem / per_cta);
     const uint32_t by_regs = (uint32_t)(65536 / ((size_t)(fa.numRegs > 0 ? fa.numRegs : 1) * JT));
     uint32_t nb = by_smem < by_regs ? by_smem : by_regs;
