@@ -81,12 +81,16 @@ __global__ void __launch_bounds__(256) k_row_consts(const unsigned long long* __
   __syncthreads();
   if (!have_mean && blockIdx.x == 0 && t < DIM) mu[t] = mu_s[t];  // (every CTA reads the sums, one writes mu)
   // ||mu|| and c_b = sum_j R_bj mu_j by warp reductions: only the approximation
-  // uses them and the bound covers their rounding, so the order is free
+  // uses them and the bound covers their rounding, so the order is free.  ||mu||
+  // enters the bound only, as an upper bound: FP32 with every step rounded up.
   if (warp == 0) {
-    double s = 0.0;
-    for (int j = lane; j < DIM; j += 32) s += mu_s[j] * mu_s[j];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
-    if (lane == 0) nmu_s = sqrt(s) * (1.0 + 0x1p-40);
+    float s = 0.f;
+    for (int j = lane; j < DIM; j += 32) {
+      const float m = __double2float_ru(fabs(mu_s[j]));
+      s = __fmaf_ru(m, m, s);
+    }
+    for (int o = 16; o > 0; o >>= 1) s = __fadd_ru(s, __shfl_xor_sync(0xFFFFFFFFu, s, o));
+    if (lane == 0) nmu_s = (double)__fsqrt_ru(s);
   }
   __syncthreads();
   for (uint32_t b = blockIdx.x * (blockDim.x / 32) + warp; b < rows; b += gridDim.x * (blockDim.x / 32)) {

@@ -573,16 +573,18 @@ __global__ void __launch_bounds__(1024) k_scan_counts(const unsigned long long* 
   }
 }
 
-__global__ void __launch_bounds__(256) k_compact(const PairInfo* __restrict__ pairs, const uint32_t* __restrict__ res,
-                                                 const uint64_t* __restrict__ off, uint32_t* __restrict__ matches,
-                                                 uint64_t cap) {
-  __shared__ uint32_t wsum[8];
+template <int NT>
+__global__ void __launch_bounds__(NT) k_compact(const PairInfo* __restrict__ pairs, const uint32_t* __restrict__ res,
+                                                const uint64_t* __restrict__ off, uint32_t* __restrict__ matches,
+                                                uint64_t cap) {
+  constexpr int NW = NT / 32;
+  __shared__ uint32_t wsum[NW];
   const uint32_t p = blockIdx.x;
   const PairInfo pi = pairs[p];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const uint64_t base = off[p];
   uint64_t run = 0;
-  for (uint32_t q0 = 0; q0 < pi.nA; q0 += 256) {
+  for (uint32_t q0 = 0; q0 < pi.nA; q0 += NT) {
     const uint32_t q = q0 + tid;
     const uint32_t r = q < pi.nA ? res[pi.qbase + q] : NO_MATCH;
     const bool f = r < PENDING;
@@ -591,7 +593,7 @@ __global__ void __launch_bounds__(256) k_compact(const PairInfo* __restrict__ pa
     __syncthreads();
     uint32_t woff = 0, tot = 0;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
+    for (int k = 0; k < NW; ++k) {
       const uint32_t x = wsum[k];
       if (k < w) woff += x;
       tot += x;
@@ -617,7 +619,12 @@ cudaError_t launch_scan_counts(const unsigned long long* pair_cnt, uint32_t P, u
 cudaError_t launch_compact(const PairInfo* pairs, uint32_t P, const uint32_t* res, const uint64_t* match_off,
                            uint32_t* matches, uint64_t cap, cudaStream_t s) {
   if (P == 0) return cudaSuccess;
-  k_compact<<<P, 256, 0, s>>>(pairs, res, match_off, matches, cap);
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  // one CTA per pair; a list of fewer pairs than SMs takes CTAs of 1024 threads (fewer steps each)
+  if (P < (uint32_t)nsm) k_compact<1024><<<P, 1024, 0, s>>>(pairs, res, match_off, matches, cap);
+  else k_compact<256><<<P, 256, 0, s>>>(pairs, res, match_off, matches, cap);
   return cudaGetLastError();
 }
 
