@@ -44,6 +44,24 @@ def test_binding_names_match_header():
     assert sorted(ch.exported_symbols()) == sorted(n for n in declared_functions())
 
 
+def test_binding_constants_match_header_enums():
+    """Every CASHASH_ enum value the header defines that the binding also names has the same value
+    there (kernel configurations, schedules, precisions, flags, stages, status codes)."""
+    import paper_1805_08995_gb300 as ch
+    txt = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    found = {}
+    for body in re.findall(r"enum\s*\w*\s*\{([^}]*)\}", txt):
+        for name, val in re.findall(r"(CASHASH_\w+)\s*=\s*(-?\w+)", body):
+            found[name] = int(val, 0)
+    for name, val in re.findall(r"#define\s+(CASHASH_\w+)\s+\(?(-?\d+)u?\)?", txt):
+        found.setdefault(name, int(val))
+    assert found.get("CASHASH_KERNEL_WARP") == 4 and found.get("CASHASH_KERNEL_JOIN_TC") == 3
+    shared = [n for n in found if hasattr(ch, n)]
+    assert len(shared) >= 10
+    for n in shared:
+        assert getattr(ch, n) == found[n], n
+
+
 def test_strerror_and_defaults_without_device(lib):
     import paper_1805_08995_gb300 as ch
     assert ch.cashash_strerror(0) == "ok"
