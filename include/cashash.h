@@ -26,9 +26,11 @@
  *   - bit b of a feature is [v_b > 0] where v_b is the projection
  *     sum_j R[b][j] * (x_j - mu_j) evaluated in IEEE double, j ascending,
  *     each difference, product and sum rounded to nearest (no fused
- *     multiply-add); the GPU computes a cheaper bounded approximation and
- *     re-evaluates exactly that double sequence whenever the approximation
- *     is within its rounding bound of zero;
+ *     multiply-add); the GPU computes a cheaper bounded approximation and,
+ *     whenever the approximation is within its rounding bound of zero,
+ *     decides the sign of exactly that double sequence (from a tree sum of
+ *     the same rounded products with a bound on its distance from the
+ *     sequence, or from the sequence itself inside that bound);
  *   - the candidate set of a query is the set of points of the other image
  *     that share its bucket in at least one table (each point once);
  *   - ranking orders candidates by (Hamming distance, candidate index);

@@ -254,15 +254,15 @@ cudaError_t launch_project_fp32(const uint8_t* desc, uint64_t n, const float* R3
 }
 
 // ---------------------------------------------------------------------------
-// Exact re-evaluation of flagged (feature, row) projections: the double
-// sequence t = x_j - mu_j, p = R_bj * t, s = s + p for j = 0..127, each
-// rounded to nearest (explicit _rn intrinsics, so no contraction).  A warp
-// takes 32 flagged features and evaluates their flagged rows 32 at a time,
-// one (feature, row) per lane, so every FP64 instruction runs with full lanes
-// (a feature has one to a few flagged rows; an FP64 instruction costs the
-// pipe the same with 6 active lanes as with 32).  Within a chain the products
-// are formed ahead of the (ordered) additions.  Bits that come out 1 are ORed
-// into the codes / bucket bytes (they were written as 0).
+// Exact re-evaluation of flagged (feature, row) projections: the sign of the
+// double sequence t = x_j - mu_j, p = R_bj * t, s = s + p for j = 0..127, each
+// rounded to nearest (explicit _rn intrinsics, so no contraction).  One warp
+// per flagged feature: the lanes form the t_j and p_j of four columns each and
+// the warp sums them as a tree, which fixes the sign of the ordered sum unless
+// the tree sum lies within a bound of zero (then the warp runs the ordered
+// additions themselves).  The 128 dependent additions of the ordered sum, slow
+// on the narrow FP64 pipe, run only for such rounding-noise projections.  Bits
+// that come out 1 are ORed into the codes / bucket bytes (they were written as 0).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_fix_fp64(const uint8_t* __restrict__ desc, const double* __restrict__ mu,
                                                   const double* __restrict__ R, KParams kp,
